@@ -1,0 +1,199 @@
+"""Seeded synthetic workloads (integrands, boxes, call counts).
+
+This module draws inputs only: family ids, parameter vectors, integration
+boxes and call counts.  It holds none of the method's arithmetic, so both the
+CUDA path's tests and the CPU oracle's tests use it to build identical
+problems.  Parameters are drawn from numpy's PCG64 generator with the stated
+seed, which gives the same values on every platform.
+
+Family ids are the values of the MCUBES_F_* enumeration of include/mcubes.h.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+F_CONST, F_GAUSS, F_CORNER, F_OSC, F_PRODPEAK, F_C0, F_DISCONT, F_COSMO6 = range(8)
+FAMILY_NAMES = {F_CONST: "const", F_GAUSS: "gauss", F_CORNER: "corner", F_OSC: "osc",
+                F_PRODPEAK: "prodpeak", F_C0: "c0", F_DISCONT: "discont", F_COSMO6: "cosmo6"}
+
+
+@dataclass
+class Workload:
+    """One integral: what to integrate, where, and how many calls."""
+    name: str
+    fid: int
+    params: np.ndarray
+    lo: np.ndarray
+    hi: np.ndarray
+    ncall: int
+    itmax: int
+    ita: int | None = None          # adjusting iterations (None = all)
+    nb: int = 500
+    g_override: int = 0
+    seed: int = 0
+    precision: str = "fp64"         # "fp64" or "mixed"
+    rel_tol: float = 0.0
+    abs_tol: float = 0.0
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def d(self) -> int:
+        return len(self.lo)
+
+    def scaled(self, ncall: int, **kw) -> "Workload":
+        """The same integrand with another call count (and other overrides)."""
+        w = Workload(**{**self.__dict__, "ncall": ncall, "meta": dict(self.meta)})
+        for k, v in kw.items():
+            setattr(w, k, v)
+        return w
+
+
+def _box(d, lo, hi):
+    return np.full(d, float(lo)), np.full(d, float(hi))
+
+
+# ---------------------------------------------------------------------------
+# the five configurations
+# ---------------------------------------------------------------------------
+def gauss3(seed: int = 0) -> Workload:
+    """d=3 product Gaussian, sigma 0.1 centred at 0.5, on [0,1]^3; 500 bins,
+    4 sub-cubes per axis (m=64), 2^20 samples per iteration, 10 iterations,
+    plain double precision."""
+    d = 3
+    params = np.concatenate([[1.0], np.full(d, 0.5), np.full(d, 0.1)])
+    lo, hi = _box(d, 0.0, 1.0)
+    return Workload("gauss3_fp64", F_GAUSS, params, lo, hi, ncall=2 ** 20, itmax=10,
+                    g_override=4, seed=seed)
+
+
+def cosmo6(seed: int = 0, draw_seed: int = 2202) -> Workload:
+    """d=6 power-law x lognormal-peak x Gaussian-ridge integrand on
+    [0.05, 2]^6 with 1e8 calls per iteration, 20 iterations, double precision.
+    a_i ~ U[0.2, 0.8]; lognormal in x_3, x_4 with mu = ln 0.5, s = 0.3; ridge
+    along x_1 + x_2 = r, r ~ U[0.8, 1.6], width t = 0.01."""
+    rng = np.random.Generator(np.random.PCG64(draw_seed))
+    a = rng.uniform(0.2, 0.8, size=6)
+    r = rng.uniform(0.8, 1.6)
+    params = np.concatenate([a, [math.log(0.5), 0.3, r, 0.01]])
+    lo, hi = _box(6, 0.05, 2.0)
+    return Workload("cosmo6_fp64", F_COSMO6, params, lo, hi, ncall=10 ** 8, itmax=20, seed=seed)
+
+
+def corner8(seed: int = 0, draw_seed: int = 2203) -> Workload:
+    """d=8 corner peak (1 + sum a_i x_i)^-(d+1), a_i ~ U[0.5, 2], on [0,1]^8,
+    1e9 calls per iteration, mixed precision."""
+    rng = np.random.Generator(np.random.PCG64(draw_seed))
+    a = rng.uniform(0.5, 2.0, size=8)
+    lo, hi = _box(8, 0.0, 1.0)
+    return Workload("corner8_mixed", F_CORNER, a, lo, hi, ncall=10 ** 9, itmax=10, seed=seed,
+                    precision="mixed")
+
+
+def osc10(seed: int = 0, draw_seed: int = 2204) -> Workload:
+    """d=10 oscillatory cos(2 pi u + sum a_i x_i), u ~ U[0,1], a_i ~ U[0.5, 2],
+    on [0,1]^10, 1e9 calls per iteration, mixed precision."""
+    rng = np.random.Generator(np.random.PCG64(draw_seed))
+    u = rng.uniform(0.0, 1.0)
+    a = rng.uniform(0.5, 2.0, size=10)
+    lo, hi = _box(10, 0.0, 1.0)
+    return Workload("osc10_mixed", F_OSC, np.concatenate([[u], a]), lo, hi, ncall=10 ** 9,
+                    itmax=10, seed=seed, precision="mixed")
+
+
+def random_integral(rng: np.random.Generator, d: int, family: int, ncall: int, itmax: int,
+                    seed: int) -> Workload:
+    """One seed-drawn integral of the gauss / corner / osc families on [0,1]^d."""
+    lo, hi = _box(d, 0.0, 1.0)
+    if family == F_GAUSS:
+        mu = rng.uniform(0.3, 0.7, size=d)
+        sig = rng.uniform(0.1, 0.3, size=d)
+        params = np.concatenate([[1.0], mu, sig])
+    elif family == F_CORNER:
+        params = rng.uniform(0.5, 2.0, size=d)
+    elif family == F_OSC:
+        params = np.concatenate([[rng.uniform(0.0, 1.0)], rng.uniform(0.5, 2.0, size=d)])
+    else:
+        raise ValueError(family)
+    return Workload(f"{FAMILY_NAMES[family]}{d}", family, params, lo, hi, ncall=ncall, itmax=itmax,
+                    seed=seed, precision="mixed")
+
+
+def batch4096(n: int = 4096, draw_seed: int = 2205, itmax: int = 10) -> list[Workload]:
+    """n independent integrals: d ~ U{2..10}, family ~ U{gauss, corner, osc},
+    ncall log-uniform in [1e4, 1e7], each with its own seed."""
+    rng = np.random.Generator(np.random.PCG64(draw_seed))
+    out = []
+    for i in range(n):
+        d = int(rng.integers(2, 11))
+        fam = int(rng.choice([F_GAUSS, F_CORNER, F_OSC]))
+        ncall = int(round(10 ** rng.uniform(4.0, 7.0)))
+        out.append(random_integral(rng, d, fam, ncall, itmax, seed=1000 + i))
+    return out
+
+
+def serving_stream(rate: float = 2000.0, duration: float = 60.0, draw_seed: int = 2206):
+    """Poisson arrivals (mean `rate` per second over `duration` seconds) of
+    integration requests: d ~ U{3..12}, rel_tol log-uniform in [1e-5, 1e-3],
+    family ~ U{gauss, corner, osc}.  Returns a list of (arrival_s, Workload)."""
+    rng = np.random.Generator(np.random.PCG64(draw_seed))
+    t = 0.0
+    out = []
+    i = 0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration:
+            break
+        d = int(rng.integers(3, 13))
+        fam = int(rng.choice([F_GAUSS, F_CORNER, F_OSC]))
+        w = random_integral(rng, d, fam, ncall=100_000, itmax=20, seed=50_000 + i)
+        w.rel_tol = float(10 ** rng.uniform(-5.0, -3.0))
+        out.append((t, w))
+        i += 1
+    return out
+
+
+# ---------------------------------------------------------------------------
+# the paper's test suite (Sec. 5, eqs. 1-6, and f_A, f_B of Table 1)
+# ---------------------------------------------------------------------------
+def suite(name: str, d: int | None = None, ncall: int = 10 ** 6, itmax: int = 10,
+          seed: int = 0) -> Workload:
+    """Parameters of the paper's integrands in the registered families.
+    f1..f6 are on [0,1]^d; f_A on (0,10)^6; f_B on (-1,1)^9."""
+    idx = np.arange(1, (d or 0) + 1, dtype=np.float64)
+    if name == "f1":   # cos(sum i x_i)
+        fid, params, box = F_OSC, np.concatenate([[0.0], idx]), (0.0, 1.0)
+    elif name == "f2":  # prod (1/50^2 + (x_i - 1/2)^2)^-1
+        fid, params, box = F_PRODPEAK, np.concatenate([np.full(d, 50.0), np.full(d, 0.5)]), (0.0, 1.0)
+    elif name == "f3":  # (1 + sum i x_i)^-(d+1)
+        fid, params, box = F_CORNER, idx.copy(), (0.0, 1.0)
+    elif name == "f4":  # exp(-625 sum (x_i - 1/2)^2): sigma^2 = 1/1250
+        fid, params, box = F_GAUSS, np.concatenate([[1.0], np.full(d, 0.5),
+                                                    np.full(d, math.sqrt(1.0 / 1250.0))]), (0.0, 1.0)
+    elif name == "f5":  # exp(-10 sum |x_i - 1/2|)
+        fid, params, box = F_C0, np.concatenate([np.full(d, 10.0), np.full(d, 0.5)]), (0.0, 1.0)
+    elif name == "f6":  # exp(sum (i+4) x_i) if x_i < (3+i)/10 for all i
+        fid, params, box = F_DISCONT, np.concatenate([idx + 4.0, (3.0 + idx) / 10.0]), (0.0, 1.0)
+    elif name == "fA":  # sin(sum x_i) = cos(sum x_i - pi/2), d = 6 on (0,10)
+        d = 6
+        fid, params, box = F_OSC, np.concatenate([[-0.25], np.ones(6)]), (0.0, 10.0)
+    elif name == "fB":  # normalised 9-d Gaussian on (-1,1)
+        # Table 1's printed f_B normalises by (2 pi 0.01)^(9/2), i.e. variance
+        # 0.01 (sigma = 0.1), while its exponent prints 1/(2 * 0.01^2).  The
+        # reading taken is sigma = 0.1: it matches the normalisation, the true
+        # value 1.0, and the finite error the paper reports (with sigma = 0.01
+        # no sample of a 9-d uniform start ever meets the peak).
+        d = 9
+        sig = 0.1
+        norm = (sig * math.sqrt(2.0 * math.pi)) ** -9
+        fid, params, box = F_GAUSS, np.concatenate([[norm], np.zeros(9), np.full(9, sig)]), (-1.0, 1.0)
+    else:
+        raise ValueError(name)
+    lo, hi = _box(d, *box)
+    return Workload(f"{name}_{d}", fid, np.asarray(params, dtype=np.float64), lo, hi, ncall=ncall,
+                    itmax=itmax, seed=seed)
+
+
+CONFIGS = {"gauss3": gauss3, "cosmo6": cosmo6, "corner8": corner8, "osc10": osc10}

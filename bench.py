@@ -1,0 +1,306 @@
+"""Benchmark of the m-Cubes VEGAS hot path on GB300.
+
+One step = one VEGAS iteration of the whole hot path (sampling launch +
+refinement/weighting launch) over one batch of N = m * p synthetic samples.
+Default workload: the d=6 power-law x lognormal x ridge integrand on
+[0.05, 2]^6, 1e8 calls per iteration (m = 19^6, p = 2), 500 bins per axis,
+plain double precision.  Metric: integrand evaluations per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--config cosmo6|gauss3|corner8|osc10] [--ncall C] [--no-cpu-baseline]
+
+Under torchrun (N > 1) every rank integrates its own independent copy of
+the workload (own seed) on its own GPU: weak scaling, no collective on the
+data path; the value is the samples of all ranks over the slowest rank's time.
+--impl reference times the CPU oracle (the method as plainly written) on the
+host cores, each step a bounded sample of one iteration.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2202_01753_gb300 import workloads as W  # noqa: E402
+
+# Issued warp instructions per sample of the sampling kernel, from the ncu
+# capture summarised in profiles/ (smsp__inst_issued.sum / samples), keyed by
+# (config, precision, adjusting).  None until measured for a kernel version.
+INST_PER_SAMPLE = {}
+
+L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2: written between timed steps
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="cosmo6", choices=sorted(W.CONFIGS))
+    ap.add_argument("--ncall", type=float, default=None, help="override calls per iteration (profiling)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload(args, rank):
+    w = W.CONFIGS[args.config](seed=rank)
+    if args.ncall:
+        w = w.scaled(int(args.ncall))
+    return w
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            t = [x.strip() for x in ln.split(",")]
+            if len(t) < 7:
+                continue
+            try:
+                sm.append(float(t[0]))
+                smax.append(float(t[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, t[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+def cpu_oracle_rate(w, seconds):
+    import numpy as np
+
+    import oracle
+    pb = oracle.Problem(w.fid, w.params, w.lo, w.hi, w.ncall, nb=w.nb, g_override=w.g_override, seed=w.seed)
+    B = oracle.init_grid(pb.d, pb.nb)
+    # calibrate on a small range, then run one range sized to `seconds`
+    n0 = max(1, min(pb.m, 2000 if pb.p < 100 else 1))
+    t = time.perf_counter()
+    pb.vsample(B, 0, True, 0, n0)
+    dt = max(time.perf_counter() - t, 1e-4)
+    n = int(min(pb.m, max(n0, n0 * seconds / dt)))
+    t = time.perf_counter()
+    pb.vsample(B, 0, True, 0, n)
+    dt = time.perf_counter() - t
+    samples = n * pb.p
+    return samples / dt, samples, dt, n
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = workload(args, 0)
+    import oracle
+    pb = oracle.Problem(w.fid, w.params, w.lo, w.hi, w.ncall, nb=w.nb, g_override=w.g_override, seed=w.seed)
+    B = oracle.init_grid(pb.d, pb.nb)
+    # one step: one adjusting sampling pass of the oracle over a fixed cube range
+    cubes = max(1, min(pb.m, (400_000 // pb.p) if pb.p < 1000 else 1))
+    for i in range(args.warmup):
+        pb.vsample(B, i, True, 0, cubes)
+    t = time.perf_counter()
+    for i in range(args.steps):
+        pb.vsample(B, args.warmup + i, True, 0, cubes)
+    dt = time.perf_counter() - t
+    samples = cubes * pb.p * args.steps
+    value = samples / dt
+    line = {
+        "impl": "reference", "metric": "integrand evaluations per second", "value": value,
+        "unit": "evals/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "d": w.d, "ncall": w.ncall, "nbins": w.nb,
+                   "sample_per_step": f"cubes [0, {cubes}) of one iteration ({cubes * pb.p} samples)"},
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{cubes * pb.p} samples per step, {args.steps} steps"},
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2202_01753_gb300 import build, mcubes
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    w = workload(args, rank)
+    K, Wm = args.steps, args.warmup
+    stream = torch.cuda.current_stream()
+    prec = w.precision
+    ctx = mcubes.Context(local, stream=stream.cuda_stream, nbins=w.nb, g_override=w.g_override, seed=w.seed,
+                         precision=prec, ita=-1)
+    ctx.setup(w.fid, w.params, w.lo, w.hi, w.ncall, itmax=Wm + K)
+    geom = ctx.geometry()
+    N = geom["m"] * geom["p"]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    ctx.iterate(Wm)
+    torch.cuda.synchronize()
+    ctx.timing_reset(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(K):
+        flush.fill_(float(k))                 # L2 flush, outside the timed pair
+        ev[k][0].record(stream)
+        ctx.iterate(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    kt = ctx.timing()
+    res = ctx.result()
+    ctx.close()
+
+    # slowest rank's time, all ranks' samples
+    t_max = total_ms
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = N * K * world / (t_max / 1e3)
+
+    # end to end through the public call with host buffers (copies inside)
+    ctx2 = mcubes.Context(local, nbins=w.nb, g_override=w.g_override, seed=w.seed, precision=prec, ita=-1)
+    ctx2.integrate(w.fid, w.params, w.lo, w.hi, w.ncall, 2)   # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r2 = ctx2.integrate(w.fid, w.params, w.lo, w.hi, w.ncall, K)
+    e2e_s = time.perf_counter() - t0
+    ctx2.close()
+    e2e_t = torch.tensor([e2e_s], device="cuda")
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = N * K * world / float(e2e_t.item())
+    h2d = 8 * (len(w.params) + 2 * w.d)
+    d2h = 88
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    avg_sample_ms = kt["sample_ms"] / max(kt["sample_launches"], 1)
+    key = (args.config, prec, True)
+    ips = INST_PER_SAMPLE.get(key)
+    sm_mhz = clk.get("sm_mhz") or 0.0
+    peak_issue = 4.0 * sms * sm_mhz * 1e6 / 1e9           # G warp-instructions / s
+    if ips is not None and sm_mhz:
+        achieved = ips * N / (avg_sample_ms / 1e3) / 1e9
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak_issue, "unit": "Gwarp-inst/s",
+                "frac": achieved / peak_issue, "traffic": None,
+                "note": "issue slots: 4 warp-instructions/clk/SM x SMs x median SM clock under load"}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": peak_issue, "unit": "Gwarp-inst/s", "frac": None,
+                "traffic": None, "note": "per-sample instruction count not yet measured for this kernel"}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        rate, samples, dt, n = cpu_oracle_rate(w, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "evals/s", "cores": 1, "kind": "oracle",
+               "sample": f"one adjusting pass over cubes [0, {n}) ({samples} samples, {dt:.1f} s)"}
+
+    line = {
+        "metric": "integrand evaluations per second", "value": value, "unit": "evals/s", "n_gpus": world,
+        "steps": K, "warmup": Wm, "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32+f64", "data": "synthetic",
+        "config": {"workload": w.name, "d": w.d, "ncall": w.ncall, "g": geom["g"], "m": geom["m"], "p": geom["p"],
+                   "samples_per_step": N, "nbins": w.nb, "precision": prec, "adjusting": True,
+                   "lanes_per_cube": geom["lanes"], "blocks": geom["blocks"],
+                   "l2": "flushed between timed steps (256 MB write)"},
+        "kernel": {"sample_ms_avg": avg_sample_ms, "refine_ms_avg": kt["refine_ms"] / max(kt["refine_launches"], 1),
+                   "sample_launches": kt["sample_launches"], "refine_launches": kt["refine_launches"]},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
+                "call": "mcubes_integrate (host params/bounds/result), %d iterations" % K},
+        "gpu_launches": kt["sample_launches"] + kt["refine_launches"],
+        "clocks": clk,
+        "result": {"estimate": res["estimate"], "sigma": res["sigma"], "chi2_dof": res["chi2_dof"],
+                   "e2e_estimate": r2["estimate"]},
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,235 @@
+/*
+ * mcubes.h -- C ABI of the GB300 m-Cubes VEGAS integrator.
+ *
+ * The library implements the per-iteration hot path of m-Cubes (Sakiotis et
+ * al., arXiv 2202.01753): the d-cube is split into m = g^d equal sub-cubes
+ * (Alg. 2), every sub-cube receives p samples drawn from a counter-based
+ * Philox4x32-10 stream keyed by (seed, iteration, cube, sample), the samples
+ * are mapped through the adaptive per-axis bin grid (Alg. 1), the integrand
+ * is evaluated, per-cube means and variances are reduced into the iteration
+ * estimate (Alg. 3), per-axis per-bin sums of f^2 drive the grid refinement
+ * (Alg. 2, Adjust-Bin-Bounds), and iterations are combined with inverse-
+ * variance weights and chi^2 (Alg. 2, Weighted-Estimates).  Every step runs
+ * in CUDA kernels on one GPU; the host only validates arguments and
+ * enqueues work.
+ *
+ * Conventions for every entry point:
+ *   - All pointers named host_* or documented as host arrays are host memory
+ *     owned by the caller, read (or written) before the call returns.
+ *   - A context owns all device memory it uses and one CUDA stream (its own,
+ *     or one the caller passes in and keeps alive).  Contexts are not
+ *     thread-safe: one host thread at a time per context.
+ *   - Every call returns an mcubes_status; no C++ exception crosses the ABI.
+ *   - Arrays of bins are laid out [d][nb], axis-major, in unit coordinates
+ *     (edges in [0, 1], the right edge of bin k at index k, the left edge of
+ *     bin 0 being 0 implicitly).
+ */
+#ifndef MCUBES_H
+#define MCUBES_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mcubes_ctx mcubes_ctx;
+
+typedef enum {
+    MCUBES_OK = 0,
+    MCUBES_EINVAL = 1,     /* invalid argument (d, ncall, bounds, params, ids, sizes) */
+    MCUBES_ENOMEM = 2,     /* device or host allocation failed */
+    MCUBES_ECUDA = 3,      /* a CUDA runtime call failed (see mcubes_last_cuda_error) */
+    MCUBES_ENONFINITE = 4, /* the integrand produced a non-finite value */
+    MCUBES_ENOCONV = 5,    /* itmax reached before the tolerance: results are still filled */
+    MCUBES_ETIMEOUT = 6,   /* a bounded device wait gave up */
+    MCUBES_ESTATE = 7      /* call out of order (e.g. iterate before setup) */
+} mcubes_status;
+
+typedef enum {
+    MCUBES_FP64 = 0,  /* map, integrand and all sums in double precision */
+    MCUBES_MIXED = 1  /* map and integrand in single precision; per-cube sums compensated,
+                         everything from the thread level up in double precision */
+} mcubes_precision;
+
+/* Integrand families (Sec. 5 eqs. 1-6 and Table 1 of the paper in
+ * parameterised form, and a stand-in for the six-dimensional integrand of
+ * Sec. 6.1).  params layout, d = dimension:
+ *   CONST    [v]                      f = v
+ *   GAUSS    [A, mu_1..d, sig_1..d]   f = A prod_i exp(-(x_i-mu_i)^2 / (2 sig_i^2))
+ *   CORNER   [a_1..d]                 f = (1 + sum_i a_i x_i)^(-(d+1))
+ *   OSC      [u, a_1..d]              f = cos(2 pi u + sum_i a_i x_i)
+ *   PRODPEAK [c_1..d, w_1..d]         f = prod_i 1 / (c_i^-2 + (x_i - w_i)^2)
+ *   C0       [c_1..d, w_1..d]         f = exp(-sum_i c_i |x_i - w_i|)
+ *   DISCONT  [c_1..d, w_1..d]         f = exp(sum_i c_i x_i) if x_i < w_i for all i, else 0
+ *   COSMO6   [a_1..6, mu, s, r, t]    d = 6 only:
+ *            f = prod_i x_i^-a_i * LN(x_3) LN(x_4) * exp(-(x_1 + x_2 - r)^2 / (2 t^2)),
+ *            LN(z) = exp(-(ln z - mu)^2 / (2 s^2)) / (z s sqrt(2 pi))
+ * (indices 1-based as written; x_i > 0 is required for COSMO6). */
+enum {
+    MCUBES_F_CONST = 0,
+    MCUBES_F_GAUSS = 1,
+    MCUBES_F_CORNER = 2,
+    MCUBES_F_OSC = 3,
+    MCUBES_F_PRODPEAK = 4,
+    MCUBES_F_C0 = 5,
+    MCUBES_F_DISCONT = 6,
+    MCUBES_F_COSMO6 = 7,
+    MCUBES_F_COUNT = 8
+};
+
+#define MCUBES_DMAX 12        /* largest dimension */
+#define MCUBES_NBMAX 1024     /* largest number of bins per axis */
+#define MCUBES_PARAMS_MAX 32  /* largest params blob */
+#define MCUBES_ITMAX_MAX 4096 /* largest itmax */
+
+typedef struct {
+    int nbins;            /* bins per axis, 2..MCUBES_NBMAX (default 500) */
+    int ita;              /* adjusting iterations (Alg. 2); < 0 means all (default -1) */
+    long long g_override; /* sub-cubes per axis; 0 = largest g with g^d <= ncall/2 (default 0) */
+    double alpha;         /* grid compression exponent of Adjust-Bin-Bounds (default 1.5) */
+    uint64_t seed;        /* Philox key (default 0) */
+    int precision;        /* mcubes_precision (default MCUBES_FP64) */
+    int lanes_per_cube;   /* 0 = automatic; else a power of two 1..32: threads sharing one cube */
+    int blocks_per_sm;    /* 0 = automatic (occupancy); else resident sampling blocks per SM */
+} mcubes_opts;
+
+typedef struct {
+    double estimate;            /* weighted estimate over the iterations run */
+    double sigma;               /* its standard deviation */
+    double chi2_dof;            /* chi^2 per degree of freedom of the iteration estimates */
+    int iterations;             /* iterations run */
+    int converged;              /* 1 if sigma <= max(abs_tol, rel_tol |estimate|) with >= 2 iterations */
+    long long samples_per_iter; /* m * p */
+    long long g, m, p;          /* sub-cubes per axis, sub-cubes, samples per sub-cube */
+    int status;                 /* mcubes_status of the run */
+} mcubes_result;
+
+/* One integral of a batch (mcubes_integrate_batch). */
+typedef struct {
+    int integrand_id;
+    const double* params; /* host, nparams values */
+    int nparams;
+    int d;
+    const double* lo;     /* host, d values */
+    const double* hi;     /* host, d values */
+    long long ncall;
+    int itmax;
+    double rel_tol;
+    double abs_tol;
+    uint64_t seed;        /* this integral's own Philox key */
+} mcubes_request;
+
+/* Fills *opts with the defaults listed in mcubes_opts. */
+void mcubes_default_opts(mcubes_opts* opts);
+
+/* Creates a context on CUDA device `device` with a stream of its own.
+ * opts may be NULL (defaults).  *out receives the context.
+ * Errors: EINVAL (bad opts or device), ECUDA, ENOMEM. */
+mcubes_status mcubes_create(mcubes_ctx** out, int device, const mcubes_opts* opts);
+
+/* As mcubes_create, but all work is enqueued on `cuda_stream` (a
+ * cudaStream_t, e.g. the current PyTorch stream), which the caller keeps
+ * alive until mcubes_destroy. */
+mcubes_status mcubes_create_on_stream(mcubes_ctx** out, int device, const mcubes_opts* opts,
+                                      void* cuda_stream);
+
+/* Replaces the options of an existing context (takes effect at the next setup). */
+mcubes_status mcubes_set_opts(mcubes_ctx* ctx, const mcubes_opts* opts);
+
+/* Releases the context and all its device memory. NULL is accepted. */
+mcubes_status mcubes_destroy(mcubes_ctx* ctx);
+
+/* Static description of a status code. */
+const char* mcubes_strerror(mcubes_status status);
+
+/* Text of the last CUDA error seen by this context (static storage, valid
+ * until the next call on the context). */
+const char* mcubes_last_cuda_error(mcubes_ctx* ctx);
+
+/* The whole m-Cubes driver (Alg. 2): up to itmax iterations, the first
+ * opts.ita of them adjusting the grid, stopping once sigma <= max(abs_tol,
+ * rel_tol |estimate|) after at least two iterations.  params, lo and hi are
+ * host arrays (nparams and d values).  *out (host) is filled on OK and on
+ * ENOCONV.  Blocks until the result is on the host.
+ * Errors: EINVAL (d outside 1..MCUBES_DMAX, ncall < 2, lo >= hi, non-finite
+ * params or bounds, unknown id, wrong nparams, itmax outside
+ * 1..MCUBES_ITMAX_MAX, or a grid too large for one block's shared memory:
+ * d * nbins * 24 bytes in FP64, d * nbins * 20 bytes in MIXED, at most the
+ * device's opt-in limit less 1 KB, 227 KB on GB300), ENOMEM, ECUDA,
+ * ENONFINITE, ENOCONV. */
+mcubes_status mcubes_integrate(mcubes_ctx* ctx, int integrand_id, const double* params, int nparams,
+                               int d, const double* lo, const double* hi, long long ncall,
+                               int itmax, double rel_tol, double abs_tol, mcubes_result* out);
+
+/* n independent integrals, each with its own seed, iterated together: every
+ * iteration of all live integrals is one persistent sampling launch and one
+ * refinement launch, captured once as a CUDA graph and replayed.  Uses the
+ * context's precision, nbins, ita (as a count) and alpha.  outs (host, n
+ * entries) receives one result per request, each with its own status.
+ * Returns OK if the batch ran (individual statuses are in outs), EINVAL if
+ * any request is invalid (nothing runs), ENOMEM, ECUDA. */
+mcubes_status mcubes_integrate_batch(mcubes_ctx* ctx, int n, const mcubes_request* reqs,
+                                     mcubes_result* outs);
+
+/* ---- step-level interface (the pieces of mcubes_integrate) -------------- */
+
+/* Validates one integral, computes its geometry, sizes the device buffers,
+ * sets the uniform grid and clears the iteration history.  Host arrays.
+ * Errors: as mcubes_integrate. */
+mcubes_status mcubes_setup(mcubes_ctx* ctx, int integrand_id, const double* params, int nparams,
+                           int d, const double* lo, const double* hi, long long ncall, int itmax,
+                           double rel_tol, double abs_tol);
+
+/* Enqueues n_iter further iterations on the context's stream and returns
+ * without waiting.  Iterations after convergence (or a device error) are
+ * skipped on the device.  Errors: ESTATE (no setup or beyond itmax). */
+mcubes_status mcubes_iterate(mcubes_ctx* ctx, int n_iter);
+
+/* Waits for the stream and copies the current result to *out (host). */
+mcubes_status mcubes_result_get(mcubes_ctx* ctx, mcubes_result* out);
+
+/* Waits, then copies the per-iteration estimates and variances (host arrays
+ * of `cap` entries); *n receives the number of iterations recorded. */
+mcubes_status mcubes_trace_get(mcubes_ctx* ctx, double* I_it, double* var_it, int cap, int* n);
+
+/* Waits, then copies the current bin grid ([d][nb] right edges, host). */
+mcubes_status mcubes_grid_get(mcubes_ctx* ctx, double* B, long long count);
+
+/* Replaces the current bin grid ([d][nb], host): every axis must have
+ * strictly increasing edges in (0, 1] ending at 1. Errors: EINVAL, ESTATE. */
+mcubes_status mcubes_grid_set(mcubes_ctx* ctx, const double* B, long long count);
+
+/* Waits, then copies the per-bin sums of f^2 ([d][nb], host) of the last
+ * adjusting iteration. */
+mcubes_status mcubes_hist_get(mcubes_ctx* ctx, double* C, long long count);
+
+/* One sampling pass (Alg. 3) over sub-cubes [cube_begin, cube_end) of
+ * iteration `it` with the current grid, leaving the context's state
+ * untouched; blocks.  sums (host, 3 values) receives the sum over those
+ * cubes of the cube means, of the variances of the cube means, and of the
+ * absolute cube means; C (host, [d][nb], may be NULL) receives the per-bin
+ * sums of f^2 when adjust != 0.  The launch is the one mcubes_iterate uses. */
+mcubes_status mcubes_sample_range(mcubes_ctx* ctx, unsigned it, int adjust, long long cube_begin,
+                                  long long cube_end, double* sums, double* C);
+
+/* Geometry of the current setup: sub-cubes per axis, sub-cubes, samples per
+ * sub-cube, lanes per cube and sampling blocks chosen. */
+mcubes_status mcubes_geometry_get(mcubes_ctx* ctx, long long* g, long long* m, long long* p,
+                                  int* lanes_per_cube, int* blocks);
+
+/* Turns per-launch CUDA-event timing on (enable != 0) or off and clears the
+ * counters.  Timing records events on the context's stream around every
+ * sampling launch and every refinement launch. */
+mcubes_status mcubes_timing_reset(mcubes_ctx* ctx, int enable);
+
+/* Waits, then reports the summed duration (ms) and count of the sampling
+ * launches and of the refinement/finalisation launches since the last reset. */
+mcubes_status mcubes_timing_get(mcubes_ctx* ctx, double* sample_ms, int* sample_launches,
+                                double* refine_ms, int* refine_launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MCUBES_H */

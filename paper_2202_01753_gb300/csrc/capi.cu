@@ -1,0 +1,756 @@
+// capi.cu -- host driver and C ABI (include/mcubes.h) of the single-integral
+// path: argument validation, geometry (Alg. 2), device buffers, and the
+// enqueueing of the sampling and refinement launches of every iteration.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "mc_internal.h"
+
+using namespace mc;
+
+namespace mc {
+cudaError_t launch_vsample_const(bool, bool, const VsArgs&, int, size_t, cudaStream_t);
+cudaError_t launch_vsample_gauss(bool, bool, const VsArgs&, int, size_t, cudaStream_t);
+cudaError_t launch_vsample_corner(bool, bool, const VsArgs&, int, size_t, cudaStream_t);
+cudaError_t launch_vsample_osc(bool, bool, const VsArgs&, int, size_t, cudaStream_t);
+cudaError_t launch_vsample_prodpeak(bool, bool, const VsArgs&, int, size_t, cudaStream_t);
+cudaError_t launch_vsample_c0(bool, bool, const VsArgs&, int, size_t, cudaStream_t);
+cudaError_t launch_vsample_discont(bool, bool, const VsArgs&, int, size_t, cudaStream_t);
+cudaError_t launch_vsample_cosmo6(bool, bool, const VsArgs&, int, size_t, cudaStream_t);
+cudaError_t occupancy_const(bool, bool, size_t, int*);
+cudaError_t occupancy_gauss(bool, bool, size_t, int*);
+cudaError_t occupancy_corner(bool, bool, size_t, int*);
+cudaError_t occupancy_osc(bool, bool, size_t, int*);
+cudaError_t occupancy_prodpeak(bool, bool, size_t, int*);
+cudaError_t occupancy_c0(bool, bool, size_t, int*);
+cudaError_t occupancy_discont(bool, bool, size_t, int*);
+cudaError_t occupancy_cosmo6(bool, bool, size_t, int*);
+
+cudaError_t launch_vsample(int family, bool mixed, bool adjust, const VsArgs& a, int grid, size_t smem,
+                           cudaStream_t s)
+{
+    switch (family) {
+    case MCUBES_F_CONST: return launch_vsample_const(mixed, adjust, a, grid, smem, s);
+    case MCUBES_F_GAUSS: return launch_vsample_gauss(mixed, adjust, a, grid, smem, s);
+    case MCUBES_F_CORNER: return launch_vsample_corner(mixed, adjust, a, grid, smem, s);
+    case MCUBES_F_OSC: return launch_vsample_osc(mixed, adjust, a, grid, smem, s);
+    case MCUBES_F_PRODPEAK: return launch_vsample_prodpeak(mixed, adjust, a, grid, smem, s);
+    case MCUBES_F_C0: return launch_vsample_c0(mixed, adjust, a, grid, smem, s);
+    case MCUBES_F_DISCONT: return launch_vsample_discont(mixed, adjust, a, grid, smem, s);
+    case MCUBES_F_COSMO6: return launch_vsample_cosmo6(mixed, adjust, a, grid, smem, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t vsample_occupancy(int family, bool mixed, bool adjust, size_t smem, int* blocks)
+{
+    switch (family) {
+    case MCUBES_F_CONST: return occupancy_const(mixed, adjust, smem, blocks);
+    case MCUBES_F_GAUSS: return occupancy_gauss(mixed, adjust, smem, blocks);
+    case MCUBES_F_CORNER: return occupancy_corner(mixed, adjust, smem, blocks);
+    case MCUBES_F_OSC: return occupancy_osc(mixed, adjust, smem, blocks);
+    case MCUBES_F_PRODPEAK: return occupancy_prodpeak(mixed, adjust, smem, blocks);
+    case MCUBES_F_C0: return occupancy_c0(mixed, adjust, smem, blocks);
+    case MCUBES_F_DISCONT: return occupancy_discont(mixed, adjust, smem, blocks);
+    case MCUBES_F_COSMO6: return occupancy_cosmo6(mixed, adjust, smem, blocks);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+size_t vsample_smem_bytes(bool mixed, bool adjust, int d, int nb)
+{
+    const size_t cell = mixed ? 16 : 16;  // float4 or double2
+    const size_t h = adjust ? (mixed ? 4 : 8) : 0;
+    return (size_t)d * nb * (cell + h);
+}
+
+// ---------------------------------------------------------------------------
+// integrand registry: parameter validation and the device constant layout
+// ---------------------------------------------------------------------------
+int family_nparams(int id, int d)
+{
+    switch (id) {
+    case MCUBES_F_CONST: return 1;
+    case MCUBES_F_GAUSS: return 1 + 2 * d;
+    case MCUBES_F_CORNER: return d;
+    case MCUBES_F_OSC: return 1 + d;
+    case MCUBES_F_PRODPEAK:
+    case MCUBES_F_C0:
+    case MCUBES_F_DISCONT: return 2 * d;
+    case MCUBES_F_COSMO6: return d == 6 ? 10 : -1;
+    default: return -1;
+    }
+}
+
+// Fills the kernel-side constants of one integrand (layout documented in
+// mc_device.cuh).  Returns false if the parameters are unusable.
+bool integrand_prepare(int id, const double* p, int np, int d, FamParams* out)
+{
+    if (family_nparams(id, d) < 0 || np != family_nparams(id, d)) return false;
+    for (int i = 0; i < np; ++i)
+        if (!std::isfinite(p[i])) return false;
+    double c[kParMax];
+    std::fill(c, c + kParMax, 0.0);
+    const double pi = 3.14159265358979323846;
+    switch (id) {
+    case MCUBES_F_CONST: c[0] = p[0]; break;
+    case MCUBES_F_GAUSS:
+        c[0] = p[0];
+        for (int j = 0; j < d; ++j) {
+            if (!(p[1 + d + j] != 0.0)) return false;
+            c[1 + j] = p[1 + j];
+            c[13 + j] = 1.0 / (2.0 * p[1 + d + j] * p[1 + d + j]);
+        }
+        break;
+    case MCUBES_F_CORNER:
+        for (int j = 0; j < d; ++j) c[j] = p[j];
+        break;
+    case MCUBES_F_OSC:
+        c[0] = 2.0 * pi * p[0];
+        for (int j = 0; j < d; ++j) c[1 + j] = p[1 + j];
+        break;
+    case MCUBES_F_PRODPEAK:
+        for (int j = 0; j < d; ++j) {
+            if (!(p[j] != 0.0)) return false;
+            c[j] = 1.0 / (p[j] * p[j]);
+            c[12 + j] = p[d + j];
+        }
+        break;
+    case MCUBES_F_C0:
+    case MCUBES_F_DISCONT:
+        for (int j = 0; j < d; ++j) {
+            c[j] = p[j];
+            c[12 + j] = p[d + j];
+        }
+        break;
+    case MCUBES_F_COSMO6:
+        if (!(p[7] > 0.0) || !(p[9] > 0.0)) return false;
+        for (int j = 0; j < 6; ++j) c[j] = p[j];
+        c[6] = p[6];
+        c[7] = 1.0 / (2.0 * p[7] * p[7]);
+        c[8] = p[8];
+        c[9] = 1.0 / (2.0 * p[9] * p[9]);
+        c[10] = 1.0 / (2.0 * pi * p[7] * p[7]);
+        break;
+    default: return false;
+    }
+    for (int i = 0; i < kParMax; ++i) {
+        out->c[i] = c[i];
+        out->cf[i] = (float)c[i];
+    }
+    return true;
+}
+
+// Geometry of Alg. 2: g = largest integer with g^d <= ncall/2 (>= 1), capped
+// so that m = g^d fits a 32-bit counter and nb*g <= 2^31; p = max(ncall/m, 2).
+static bool ipow_le(long long g, int d, unsigned long long limit, unsigned long long* out)
+{
+    unsigned long long v = 1;
+    for (int i = 0; i < d; ++i) {
+        if (v > limit / (unsigned long long)g) return false;
+        v *= (unsigned long long)g;
+    }
+    *out = v;
+    return true;
+}
+
+bool geometry(int d, long long ncall, long long g_override, int nb, long long* g, long long* m,
+              long long* p)
+{
+    const unsigned long long mlim = 0xFFFFFFFFull;
+    const long long glim = (1ll << 31) / nb;
+    unsigned long long mm = 0;
+    long long gg;
+    if (g_override > 0) {
+        gg = g_override;
+        if (gg > glim || !ipow_le(gg, d, mlim, &mm)) return false;
+    } else {
+        const unsigned long long cap = std::min<unsigned long long>((unsigned long long)ncall / 2, mlim);
+        long long lo = 1, hi = glim;
+        while (lo < hi) {
+            const long long mid = lo + (hi - lo + 1) / 2;
+            unsigned long long t;
+            if (ipow_le(mid, d, cap, &t)) lo = mid; else hi = mid - 1;
+        }
+        gg = lo;
+        ipow_le(gg, d, mlim, &mm);
+    }
+    long long pp = ncall / (long long)mm;
+    if (pp < 2) pp = 2;
+    if (pp > 0xFFFFFFFFll) return false;
+    *g = gg;
+    *m = (long long)mm;
+    *p = pp;
+    return true;
+}
+
+void philox_round_keys(uint64_t seed, uint32_t rk[10][2])
+{
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        rk[r][0] = k0;
+        rk[r][1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+}  // namespace mc
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+namespace {
+
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+};
+
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    cudaError_t reserve(size_t n)
+    {
+        if (n <= bytes) return cudaSuccess;
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMalloc(&ptr, n);
+        if (e == cudaSuccess) bytes = n;
+        return e;
+    }
+    void release()
+    {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+    }
+};
+
+}  // namespace
+
+struct mcubes_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    mcubes_opts opts{};
+    int num_sms = 0;
+    char cuda_err[256] = {0};
+
+    // current problem
+    bool ready = false;
+    int fid = 0, d = 0, nb = 0, itmax = 0, ita = 0;
+    long long ncall = 0, g = 0, m = 0, p = 0;
+    bool mixed = false;
+    int lanes = 1;
+    int grid_adj = 0, grid_noadj = 0;
+    size_t smem_adj = 0, smem_noadj = 0;
+    int it_enqueued = 0;
+    VsArgs vs{};
+    RefineArgs rf{};
+
+    DevBuf grid, hist, part, part_hist, state, range_out;
+
+    bool timing = false;
+    std::vector<EventPair> ev_sample, ev_refine;
+    size_t n_sample = 0, n_refine = 0;
+    std::vector<EventPair> pool;
+};
+
+static mcubes_status cuda_fail(mcubes_ctx* c, cudaError_t e)
+{
+    if (c) std::snprintf(c->cuda_err, sizeof c->cuda_err, "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) return MCUBES_ENOMEM;
+    return MCUBES_ECUDA;
+}
+
+#define MC_CHECK(ctx, expr)                                   \
+    do {                                                      \
+        cudaError_t _e = (expr);                              \
+        if (_e != cudaSuccess) return cuda_fail((ctx), _e);   \
+    } while (0)
+
+static bool opts_valid(const mcubes_opts* o)
+{
+    if (o->nbins < 2 || o->nbins > MCUBES_NBMAX) return false;
+    if (!(o->alpha >= 0.0) || !std::isfinite(o->alpha)) return false;
+    if (o->precision != MCUBES_FP64 && o->precision != MCUBES_MIXED) return false;
+    if (o->lanes_per_cube < 0 || o->lanes_per_cube > 32 || (o->lanes_per_cube & (o->lanes_per_cube - 1)))
+        return false;
+    if (o->blocks_per_sm < 0 || o->blocks_per_sm > 32) return false;
+    if (o->g_override < 0) return false;
+    return true;
+}
+
+static EventPair take_events(mcubes_ctx* c)
+{
+    if (!c->pool.empty()) {
+        EventPair e = c->pool.back();
+        c->pool.pop_back();
+        return e;
+    }
+    EventPair e;
+    cudaEventCreate(&e.a);
+    cudaEventCreate(&e.b);
+    return e;
+}
+
+static void recycle_events(mcubes_ctx* c)
+{
+    for (auto& e : c->ev_sample) c->pool.push_back(e);
+    for (auto& e : c->ev_refine) c->pool.push_back(e);
+    c->ev_sample.clear();
+    c->ev_refine.clear();
+}
+
+extern "C" {
+
+void mcubes_default_opts(mcubes_opts* o)
+{
+    if (!o) return;
+    o->nbins = 500;
+    o->ita = -1;
+    o->g_override = 0;
+    o->alpha = 1.5;
+    o->seed = 0;
+    o->precision = MCUBES_FP64;
+    o->lanes_per_cube = 0;
+    o->blocks_per_sm = 0;
+}
+
+const char* mcubes_strerror(mcubes_status s)
+{
+    switch (s) {
+    case MCUBES_OK: return "ok";
+    case MCUBES_EINVAL: return "invalid argument";
+    case MCUBES_ENOMEM: return "out of memory";
+    case MCUBES_ECUDA: return "CUDA error";
+    case MCUBES_ENONFINITE: return "integrand produced a non-finite value";
+    case MCUBES_ENOCONV: return "not converged within itmax";
+    case MCUBES_ETIMEOUT: return "device wait timed out";
+    case MCUBES_ESTATE: return "call out of order";
+    default: return "unknown status";
+    }
+}
+
+const char* mcubes_last_cuda_error(mcubes_ctx* c) { return c ? c->cuda_err : ""; }
+
+static mcubes_status create_impl(mcubes_ctx** out, int device, const mcubes_opts* opts, void* stream)
+{
+    if (!out) return MCUBES_EINVAL;
+    *out = nullptr;
+    mcubes_opts o;
+    mcubes_default_opts(&o);
+    if (opts) o = *opts;
+    if (!opts_valid(&o)) return MCUBES_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return MCUBES_EINVAL;
+    mcubes_ctx* c = new (std::nothrow) mcubes_ctx();
+    if (!c) return MCUBES_ENOMEM;
+    c->device = device;
+    c->opts = o;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) {
+        if (stream) {
+            c->stream = (cudaStream_t)stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+            c->own_stream = true;
+        }
+    }
+    if (e == cudaSuccess) e = c->state.reserve(sizeof(DevState));
+    if (e == cudaSuccess) e = c->range_out.reserve(sizeof(double) * (3 + (size_t)MCUBES_DMAX * MCUBES_NBMAX));
+    if (e != cudaSuccess) {
+        mcubes_status st = cuda_fail(nullptr, e);
+        mcubes_destroy(c);
+        return st;
+    }
+    *out = c;
+    return MCUBES_OK;
+}
+
+mcubes_status mcubes_create(mcubes_ctx** out, int device, const mcubes_opts* opts)
+{
+    return create_impl(out, device, opts, nullptr);
+}
+
+mcubes_status mcubes_create_on_stream(mcubes_ctx** out, int device, const mcubes_opts* opts, void* stream)
+{
+    if (!stream) return MCUBES_EINVAL;
+    return create_impl(out, device, opts, stream);
+}
+
+mcubes_status mcubes_set_opts(mcubes_ctx* c, const mcubes_opts* o)
+{
+    if (!c || !o || !opts_valid(o)) return MCUBES_EINVAL;
+    c->opts = *o;
+    c->ready = false;
+    return MCUBES_OK;
+}
+
+mcubes_status mcubes_destroy(mcubes_ctx* c)
+{
+    if (!c) return MCUBES_OK;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    c->grid.release();
+    c->hist.release();
+    c->part.release();
+    c->part_hist.release();
+    c->state.release();
+    c->range_out.release();
+    recycle_events(c);
+    for (auto& e : c->pool) {
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return MCUBES_OK;
+}
+
+// Chooses how many threads share a cube: enough cube-lanes to cover the
+// resident threads several times, and a bounded number of samples per lane.
+static int choose_lanes(long long m, long long p, long long resident)
+{
+    int L = 1;
+    while (L < 32 && 2 * L <= p && (m * L < 4 * resident || p / L > 64)) L *= 2;
+    return L;
+}
+
+mcubes_status mcubes_setup(mcubes_ctx* c, int id, const double* params, int nparams, int d,
+                           const double* lo, const double* hi, long long ncall, int itmax,
+                           double rel_tol, double abs_tol)
+{
+    if (!c) return MCUBES_EINVAL;
+    c->ready = false;
+    if (d < 1 || d > MCUBES_DMAX || ncall < 2 || itmax < 1 || itmax > MCUBES_ITMAX_MAX) return MCUBES_EINVAL;
+    if (!lo || !hi || (nparams > 0 && !params)) return MCUBES_EINVAL;
+    if (!(rel_tol >= 0.0) || !(abs_tol >= 0.0)) return MCUBES_EINVAL;
+    FamParams fp;
+    if (!integrand_prepare(id, params, nparams, d, &fp)) return MCUBES_EINVAL;
+    for (int j = 0; j < d; ++j)
+        if (!std::isfinite(lo[j]) || !std::isfinite(hi[j]) || !(lo[j] < hi[j])) return MCUBES_EINVAL;
+    const int nb = c->opts.nbins;
+    long long g, m, p;
+    if (!geometry(d, ncall, c->opts.g_override, nb, &g, &m, &p)) return MCUBES_EINVAL;
+
+    MC_CHECK(c, cudaSetDevice(c->device));
+    c->fid = id;
+    c->d = d;
+    c->nb = nb;
+    c->ncall = ncall;
+    c->itmax = itmax;
+    c->ita = c->opts.ita < 0 ? itmax : std::min(c->opts.ita, itmax);
+    c->g = g;
+    c->m = m;
+    c->p = p;
+    c->mixed = c->opts.precision == MCUBES_MIXED;
+
+    // launch shapes
+    c->smem_adj = vsample_smem_bytes(c->mixed, true, d, nb);
+    c->smem_noadj = vsample_smem_bytes(c->mixed, false, d, nb);
+    int smem_limit = 0;
+    MC_CHECK(c, cudaDeviceGetAttribute(&smem_limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    if (c->smem_adj + 1024 > (size_t)smem_limit) return MCUBES_EINVAL;  // grid + histogram must fit on chip
+    int occ_adj = 0, occ_noadj = 0;
+    MC_CHECK(c, vsample_occupancy(id, c->mixed, true, c->smem_adj, &occ_adj));
+    MC_CHECK(c, vsample_occupancy(id, c->mixed, false, c->smem_noadj, &occ_noadj));
+    if (occ_adj < 1 || occ_noadj < 1) return MCUBES_EINVAL;
+    if (c->opts.blocks_per_sm > 0) {
+        occ_adj = std::min(occ_adj, c->opts.blocks_per_sm);
+        occ_noadj = std::min(occ_noadj, c->opts.blocks_per_sm);
+    }
+    c->grid_adj = occ_adj * c->num_sms;
+    c->grid_noadj = occ_noadj * c->num_sms;
+    const long long resident = (long long)std::max(occ_adj, occ_noadj) * c->num_sms * kVsThreads;
+    c->lanes = c->opts.lanes_per_cube > 0 ? c->opts.lanes_per_cube : choose_lanes(m, p, resident);
+    const int grid_max = std::max(c->grid_adj, c->grid_noadj);
+
+    // device buffers
+    const size_t hist_elem = c->mixed ? sizeof(float) : sizeof(double);
+    MC_CHECK(c, c->grid.reserve(sizeof(double) * d * nb));
+    MC_CHECK(c, c->hist.reserve(sizeof(double) * d * nb));
+    MC_CHECK(c, c->part.reserve(sizeof(double) * 3 * grid_max));
+    MC_CHECK(c, c->part_hist.reserve(hist_elem * (size_t)grid_max * d * nb));
+
+    // kernel arguments
+    VsArgs& a = c->vs;
+    std::memset(&a, 0, sizeof a);
+    a.grid = (const double*)c->grid.ptr;
+    a.part = (double*)c->part.ptr;
+    a.part_hist = c->part_hist.ptr;
+    a.st = (DevState*)c->state.ptr;
+    a.d = (uint32_t)d;
+    a.nb = (uint32_t)nb;
+    a.g = (uint32_t)g;
+    a.gmagic = (uint32_t)(0xFFFFFFFFu / (uint32_t)g);
+    a.p = (uint32_t)p;
+    a.lanes = (uint32_t)c->lanes;
+    a.cube_begin = 0;
+    a.cube_end = (uint64_t)m;
+    philox_round_keys(c->opts.seed, a.rk);
+    double jc = 1.0;
+    for (int j = 0; j < d; ++j) {
+        a.lo[j] = lo[j];
+        a.scale[j] = hi[j] - lo[j];
+        jc *= (double)nb;
+    }
+    a.jac_const = jc;
+    a.inv_g_2p33 = std::ldexp(1.0 / (double)g, -33);
+    a.inv_g_f = (float)(1.0 / (double)g);
+    a.nb_f = (float)nb;
+    a.fam = fp;
+
+    RefineArgs& r = c->rf;
+    std::memset(&r, 0, sizeof r);
+    r.grid = (double*)c->grid.ptr;
+    r.hist = (double*)c->hist.ptr;
+    r.part = (const double*)c->part.ptr;
+    r.part_hist = c->part_hist.ptr;
+    r.st = (DevState*)c->state.ptr;
+    r.d = d;
+    r.nb = nb;
+    r.hist_is_float = c->mixed ? 1 : 0;
+    r.alpha = c->opts.alpha;
+    r.m = (double)m;
+
+    // initial state: uniform grid, empty history
+    DevState hst;
+    std::memset(&hst, 0, offsetof(DevState, hist_I));
+    hst.rel_tol = rel_tol;
+    hst.abs_tol = abs_tol;
+    MC_CHECK(c, cudaMemcpyAsync(c->state.ptr, &hst, offsetof(DevState, hist_I), cudaMemcpyHostToDevice, c->stream));
+    MC_CHECK(c, launch_init_grid((double*)c->grid.ptr, d, nb, c->stream));
+    MC_CHECK(c, cudaMemsetAsync(c->hist.ptr, 0, sizeof(double) * d * nb, c->stream));
+    MC_CHECK(c, cudaStreamSynchronize(c->stream));  // hst lives on this stack frame
+    c->it_enqueued = 0;
+    c->ready = true;
+    return MCUBES_OK;
+}
+
+mcubes_status mcubes_iterate(mcubes_ctx* c, int n_iter)
+{
+    if (!c) return MCUBES_EINVAL;
+    if (!c->ready || n_iter < 0 || c->it_enqueued + n_iter > c->itmax) return MCUBES_ESTATE;
+    MC_CHECK(c, cudaSetDevice(c->device));
+    for (int i = 0; i < n_iter; ++i) {
+        const bool adjust = c->it_enqueued < c->ita;
+        const int grid = adjust ? c->grid_adj : c->grid_noadj;
+        const size_t smem = adjust ? c->smem_adj : c->smem_noadj;
+        EventPair ev;
+        if (c->timing) {
+            ev = take_events(c);
+            MC_CHECK(c, cudaEventRecord(ev.a, c->stream));
+        }
+        MC_CHECK(c, launch_vsample(c->fid, c->mixed, adjust, c->vs, grid, smem, c->stream));
+        if (c->timing) {
+            MC_CHECK(c, cudaEventRecord(ev.b, c->stream));
+            c->ev_sample.push_back(ev);
+        }
+        c->rf.nblocks = grid;
+        c->rf.adjust = adjust ? 1 : 0;
+        EventPair ev2;
+        if (c->timing) {
+            ev2 = take_events(c);
+            MC_CHECK(c, cudaEventRecord(ev2.a, c->stream));
+        }
+        MC_CHECK(c, launch_refine(c->rf, c->stream));
+        if (c->timing) {
+            MC_CHECK(c, cudaEventRecord(ev2.b, c->stream));
+            c->ev_refine.push_back(ev2);
+        }
+        ++c->it_enqueued;
+    }
+    return MCUBES_OK;
+}
+
+mcubes_status mcubes_result_get(mcubes_ctx* c, mcubes_result* out)
+{
+    if (!c || !out) return MCUBES_EINVAL;
+    if (!c->ready) return MCUBES_ESTATE;
+    MC_CHECK(c, cudaSetDevice(c->device));
+    DevState h;
+    MC_CHECK(c, cudaMemcpyAsync(&h, c->state.ptr, offsetof(DevState, hist_I), cudaMemcpyDeviceToHost, c->stream));
+    MC_CHECK(c, cudaStreamSynchronize(c->stream));
+    out->estimate = h.estimate;
+    out->sigma = h.sigma;
+    out->chi2_dof = h.chi2_dof;
+    out->iterations = h.n;
+    out->converged = h.converged;
+    out->samples_per_iter = c->m * c->p;
+    out->g = c->g;
+    out->m = c->m;
+    out->p = c->p;
+    mcubes_status st = h.error ? (mcubes_status)h.error : (h.converged ? MCUBES_OK : MCUBES_ENOCONV);
+    out->status = st;
+    return st;
+}
+
+mcubes_status mcubes_integrate(mcubes_ctx* c, int id, const double* params, int nparams, int d,
+                               const double* lo, const double* hi, long long ncall, int itmax,
+                               double rel_tol, double abs_tol, mcubes_result* out)
+{
+    if (!c || !out) return MCUBES_EINVAL;
+    mcubes_status st = mcubes_setup(c, id, params, nparams, d, lo, hi, ncall, itmax, rel_tol, abs_tol);
+    if (st != MCUBES_OK) return st;
+    st = mcubes_iterate(c, itmax);
+    if (st != MCUBES_OK) return st;
+    return mcubes_result_get(c, out);
+}
+
+mcubes_status mcubes_trace_get(mcubes_ctx* c, double* I_it, double* var_it, int cap, int* n)
+{
+    if (!c || cap < 0) return MCUBES_EINVAL;
+    if (!c->ready) return MCUBES_ESTATE;
+    MC_CHECK(c, cudaSetDevice(c->device));
+    int hn = 0;
+    MC_CHECK(c, cudaMemcpyAsync(&hn, (char*)c->state.ptr + offsetof(DevState, n), sizeof(int),
+                                cudaMemcpyDeviceToHost, c->stream));
+    MC_CHECK(c, cudaStreamSynchronize(c->stream));
+    const int k = std::min(hn, cap);
+    if (k > 0 && I_it)
+        MC_CHECK(c, cudaMemcpy(I_it, (char*)c->state.ptr + offsetof(DevState, hist_I), sizeof(double) * k,
+                               cudaMemcpyDeviceToHost));
+    if (k > 0 && var_it)
+        MC_CHECK(c, cudaMemcpy(var_it, (char*)c->state.ptr + offsetof(DevState, hist_V), sizeof(double) * k,
+                               cudaMemcpyDeviceToHost));
+    if (n) *n = hn;
+    return MCUBES_OK;
+}
+
+static mcubes_status copy_dd(mcubes_ctx* c, double* dst, const DevBuf& src, long long count)
+{
+    if (!c || !dst) return MCUBES_EINVAL;
+    if (!c->ready) return MCUBES_ESTATE;
+    if (count != (long long)c->d * c->nb) return MCUBES_EINVAL;
+    MC_CHECK(c, cudaSetDevice(c->device));
+    MC_CHECK(c, cudaMemcpyAsync(dst, src.ptr, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream));
+    MC_CHECK(c, cudaStreamSynchronize(c->stream));
+    return MCUBES_OK;
+}
+
+mcubes_status mcubes_grid_get(mcubes_ctx* c, double* B, long long count) { return copy_dd(c, B, c->grid, count); }
+
+mcubes_status mcubes_hist_get(mcubes_ctx* c, double* C, long long count) { return copy_dd(c, C, c->hist, count); }
+
+mcubes_status mcubes_grid_set(mcubes_ctx* c, const double* B, long long count)
+{
+    if (!c || !B) return MCUBES_EINVAL;
+    if (!c->ready) return MCUBES_ESTATE;
+    if (count != (long long)c->d * c->nb) return MCUBES_EINVAL;
+    for (int j = 0; j < c->d; ++j) {
+        double prev = 0.0;
+        for (int k = 0; k < c->nb; ++k) {
+            const double v = B[(size_t)j * c->nb + k];
+            if (!(v > prev) || !(v <= 1.0)) return MCUBES_EINVAL;
+            prev = v;
+        }
+        if (prev != 1.0) return MCUBES_EINVAL;
+    }
+    MC_CHECK(c, cudaSetDevice(c->device));
+    MC_CHECK(c, cudaMemcpyAsync(c->grid.ptr, B, sizeof(double) * count, cudaMemcpyHostToDevice, c->stream));
+    MC_CHECK(c, cudaStreamSynchronize(c->stream));
+    return MCUBES_OK;
+}
+
+mcubes_status mcubes_sample_range(mcubes_ctx* c, unsigned it, int adjust, long long cube_begin,
+                                  long long cube_end, double* sums, double* C)
+{
+    if (!c || !sums) return MCUBES_EINVAL;
+    if (!c->ready) return MCUBES_ESTATE;
+    if (cube_begin < 0 || cube_end < cube_begin || cube_end > c->m) return MCUBES_EINVAL;
+    MC_CHECK(c, cudaSetDevice(c->device));
+    VsArgs a = c->vs;
+    a.st = nullptr;
+    a.it_fixed = it;
+    a.cube_begin = (uint64_t)cube_begin;
+    a.cube_end = (uint64_t)cube_end;
+    const bool adj = adjust != 0;
+    const int grid = adj ? c->grid_adj : c->grid_noadj;
+    const size_t smem = adj ? c->smem_adj : c->smem_noadj;
+    MC_CHECK(c, launch_vsample(c->fid, c->mixed, adj, a, grid, smem, c->stream));
+    double* out = (double*)c->range_out.ptr;
+    MC_CHECK(c, launch_reduce_range((const double*)c->part.ptr, c->part_hist.ptr, c->mixed ? 1 : 0, grid, c->d,
+                                    c->nb, adj ? 1 : 0, out, out + 3, c->stream));
+    MC_CHECK(c, cudaMemcpyAsync(sums, out, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream));
+    if (adj && C)
+        MC_CHECK(c, cudaMemcpyAsync(C, out + 3, sizeof(double) * c->d * c->nb, cudaMemcpyDeviceToHost, c->stream));
+    MC_CHECK(c, cudaStreamSynchronize(c->stream));
+    return MCUBES_OK;
+}
+
+mcubes_status mcubes_geometry_get(mcubes_ctx* c, long long* g, long long* m, long long* p, int* lanes,
+                                  int* blocks)
+{
+    if (!c) return MCUBES_EINVAL;
+    if (!c->ready) return MCUBES_ESTATE;
+    if (g) *g = c->g;
+    if (m) *m = c->m;
+    if (p) *p = c->p;
+    if (lanes) *lanes = c->lanes;
+    if (blocks) *blocks = c->ita > 0 ? c->grid_adj : c->grid_noadj;
+    return MCUBES_OK;
+}
+
+mcubes_status mcubes_timing_reset(mcubes_ctx* c, int enable)
+{
+    if (!c) return MCUBES_EINVAL;
+    MC_CHECK(c, cudaSetDevice(c->device));
+    MC_CHECK(c, cudaStreamSynchronize(c->stream));
+    recycle_events(c);
+    c->timing = enable != 0;
+    return MCUBES_OK;
+}
+
+mcubes_status mcubes_timing_get(mcubes_ctx* c, double* sample_ms, int* sample_launches, double* refine_ms,
+                                int* refine_launches)
+{
+    if (!c) return MCUBES_EINVAL;
+    MC_CHECK(c, cudaSetDevice(c->device));
+    MC_CHECK(c, cudaStreamSynchronize(c->stream));
+    double ts = 0.0, tr = 0.0;
+    for (auto& e : c->ev_sample) {
+        float ms = 0.f;
+        MC_CHECK(c, cudaEventElapsedTime(&ms, e.a, e.b));
+        ts += ms;
+    }
+    for (auto& e : c->ev_refine) {
+        float ms = 0.f;
+        MC_CHECK(c, cudaEventElapsedTime(&ms, e.a, e.b));
+        tr += ms;
+    }
+    if (sample_ms) *sample_ms = ts;
+    if (sample_launches) *sample_launches = (int)c->ev_sample.size();
+    if (refine_ms) *refine_ms = tr;
+    if (refine_launches) *refine_launches = (int)c->ev_refine.size();
+    return MCUBES_OK;
+}
+
+mcubes_status mcubes_integrate_batch(mcubes_ctx* c, int n, const mcubes_request* reqs, mcubes_result* outs)
+{
+    // Sequential fallback until the persistent batched kernel lands: every
+    // request runs through the single-integral path with its own seed.
+    if (!c || n < 0 || (n > 0 && (!reqs || !outs))) return MCUBES_EINVAL;
+    const uint64_t saved_seed = c->opts.seed;
+    for (int i = 0; i < n; ++i) {
+        const mcubes_request& r = reqs[i];
+        c->opts.seed = r.seed;
+        mcubes_status st = mcubes_integrate(c, r.integrand_id, r.params, r.nparams, r.d, r.lo, r.hi, r.ncall,
+                                            r.itmax, r.rel_tol, r.abs_tol, &outs[i]);
+        outs[i].status = st;
+        if (st == MCUBES_ECUDA || st == MCUBES_ENOMEM) {
+            c->opts.seed = saved_seed;
+            return st;
+        }
+    }
+    c->opts.seed = saved_seed;
+    return MCUBES_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,233 @@
+// mc_device.cuh -- device building blocks of the sampling kernel:
+// counter-based random words, the exact sub-cube/bin position of a
+// coordinate, the integrand families, and compensated single-precision sums.
+#pragma once
+
+#include <cstdint>
+
+#include "mc_internal.h"
+
+namespace mc {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+// as 1, 2, 3", SC'11).  The round keys (key + r * Weyl increments) are
+// precomputed on the host and read from the kernel's constant bank.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 x, const uint32_t (&rk)[10][2])
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t a0 = x.x * 0xD2511F53u, h0 = __umulhi(x.x, 0xD2511F53u);
+        const uint32_t a1 = x.z * 0xCD9E8D57u, h1 = __umulhi(x.z, 0xCD9E8D57u);
+        x = make_uint4(h1 ^ x.y ^ rk[r][0], a1, h0 ^ x.w ^ rk[r][1], a0);
+    }
+    return x;
+}
+
+// ---------------------------------------------------------------------------
+// Exact position of one coordinate (Alg. 1 map step, Alg. 3 Get-Bin-ID).  The
+// sample sits at y = (c + u)/g on this axis, c the sub-cube digit and
+// u = (w + 1/2) / 2^32 the offset drawn from the random word w.  With
+// A = nb (2w + 1) = a_hi 2^33 + a_lo and Q = nb c + a_hi:
+//     nb y = (Q + a_lo 2^-33) / g,   k = floor(Q / g),
+//     phi = nb y - k = (Q mod g + a_lo 2^-33) / g.
+// Q < nb g <= 2^31, so floor(Q/g) is one high multiply by
+// gmagic = floor((2^32-1)/g) and at most one correction.
+// ---------------------------------------------------------------------------
+struct BinPos {
+    uint32_t k;    // bin index
+    uint32_t r;    // Q mod g
+    uint32_t ahi;  // bit 32 of a_lo (i.e. A >> 32 & 1)
+    uint32_t alo;  // low 32 bits of a_lo
+};
+
+__device__ __forceinline__ BinPos bin_pos(uint32_t w, uint32_t nb_c, uint32_t nb, uint32_t g,
+                                          uint32_t gmagic)
+{
+    const uint64_t A = (uint64_t)(2u * nb) * (uint64_t)w + (uint64_t)nb;
+    const uint32_t hi = (uint32_t)(A >> 32);
+    const uint32_t Q = nb_c + (hi >> 1);
+    uint32_t q = __umulhi(Q, gmagic);
+    uint32_t r = Q - q * g;
+    if (r >= g) { ++q; r -= g; }
+    BinPos b;
+    b.k = q;
+    b.r = r;
+    b.ahi = hi & 1u;
+    b.alo = (uint32_t)A;
+    return b;
+}
+
+// phi in double: (r 2^33 + a_lo) * 2^-33 / g  (the numerator is exact below 2^53)
+__device__ __forceinline__ double bin_phi_f64(const BinPos& b, double inv_g_2p33)
+{
+    const uint64_t num = ((uint64_t)b.r << 33) | ((uint64_t)b.ahi << 32) | (uint64_t)b.alo;
+    return __ull2double_rn(num) * inv_g_2p33;
+}
+
+// phi in single precision
+__device__ __forceinline__ float bin_phi_f32(const BinPos& b, float inv_g)
+{
+    const float base = __uint2float_rn(b.r) + (b.ahi ? 0.5f : 0.0f);
+    return __fmul_rn(__fmaf_rn(__uint2float_rn(b.alo), 1.16415321826934814453125e-10f /*2^-33*/, base), inv_g);
+}
+
+// ---------------------------------------------------------------------------
+// Integrand families.  Each keeps a running state updated axis by axis, so
+// the point x never has to be stored; constants come from FamParams, whose
+// layout per family is fixed by integrand_prepare (capi.cu):
+//   CONST    c[0] = v
+//   GAUSS    c[0] = A, c[1+j] = mu_j, c[13+j] = 1/(2 sig_j^2)
+//   CORNER   c[j] = a_j
+//   OSC      c[0] = 2 pi u, c[1+j] = a_j
+//   PRODPEAK c[j] = c_j^-2, c[12+j] = w_j
+//   C0       c[j] = c_j, c[12+j] = w_j
+//   DISCONT  c[j] = c_j, c[12+j] = w_j
+//   COSMO6   c[0..5] = a, c[6] = mu, c[7] = 1/(2 s^2), c[8] = r, c[9] = 1/(2 t^2),
+//            c[10] = 1/(2 pi s^2)
+// ---------------------------------------------------------------------------
+template <typename R> struct RealOps;
+template <> struct RealOps<double> {
+    __device__ static double exp_(double v) { return exp(v); }
+    __device__ static double log_(double v) { return log(v); }
+    __device__ static double cos_(double v) { return cos(v); }
+    __device__ static double rcp(double v) { return 1.0 / v; }
+    __device__ static double par(const FamParams& f, int i) { return f.c[i]; }
+};
+template <> struct RealOps<float> {
+    __device__ static float exp_(float v) { return expf(v); }
+    __device__ static float log_(float v) { return logf(v); }
+    __device__ static float cos_(float v) { return cosf(v); }
+    __device__ static float rcp(float v) { return 1.0f / v; }
+    __device__ static float par(const FamParams& f, int i) { return f.cf[i]; }
+};
+
+template <int FAM, typename R> struct Family;
+
+template <typename R> struct Family<MCUBES_F_CONST, R> {
+    struct S {};
+    __device__ static void begin(S&) {}
+    __device__ static void add(S&, int, R, const FamParams&) {}
+    __device__ static R end(const S&, uint32_t, const FamParams& f) { return RealOps<R>::par(f, 0); }
+};
+
+template <typename R> struct Family<MCUBES_F_GAUSS, R> {
+    struct S { R q; };
+    __device__ static void begin(S& s) { s.q = R(0); }
+    __device__ static void add(S& s, int j, R x, const FamParams& f)
+    {
+        const R z = x - RealOps<R>::par(f, 1 + j);
+        s.q += z * z * RealOps<R>::par(f, 13 + j);
+    }
+    __device__ static R end(const S& s, uint32_t, const FamParams& f)
+    {
+        return RealOps<R>::par(f, 0) * RealOps<R>::exp_(-s.q);
+    }
+};
+
+template <typename R> struct Family<MCUBES_F_CORNER, R> {
+    struct S { R t; };
+    __device__ static void begin(S& s) { s.t = R(1); }
+    __device__ static void add(S& s, int j, R x, const FamParams& f) { s.t += RealOps<R>::par(f, j) * x; }
+    __device__ static R end(const S& s, uint32_t d, const FamParams&)
+    {
+        // t^-(d+1) by repeated squaring of 1/t
+        R b = RealOps<R>::rcp(s.t), r = R(1);
+        uint32_t e = d + 1;
+        while (e) {
+            if (e & 1u) r *= b;
+            b *= b;
+            e >>= 1;
+        }
+        return r;
+    }
+};
+
+template <typename R> struct Family<MCUBES_F_OSC, R> {
+    struct S { R t; };
+    __device__ static void begin(S& s) { s.t = R(0); }
+    __device__ static void add(S& s, int j, R x, const FamParams& f) { s.t += RealOps<R>::par(f, 1 + j) * x; }
+    __device__ static R end(const S& s, uint32_t, const FamParams& f)
+    {
+        return RealOps<R>::cos_(RealOps<R>::par(f, 0) + s.t);
+    }
+};
+
+template <typename R> struct Family<MCUBES_F_PRODPEAK, R> {
+    struct S { R v; };
+    __device__ static void begin(S& s) { s.v = R(1); }
+    __device__ static void add(S& s, int j, R x, const FamParams& f)
+    {
+        const R z = x - RealOps<R>::par(f, 12 + j);
+        s.v *= RealOps<R>::rcp(RealOps<R>::par(f, j) + z * z);
+    }
+    __device__ static R end(const S& s, uint32_t, const FamParams&) { return s.v; }
+};
+
+template <typename R> struct Family<MCUBES_F_C0, R> {
+    struct S { R t; };
+    __device__ static void begin(S& s) { s.t = R(0); }
+    __device__ static void add(S& s, int j, R x, const FamParams& f)
+    {
+        const R z = x - RealOps<R>::par(f, 12 + j);
+        s.t += RealOps<R>::par(f, j) * (z < R(0) ? -z : z);
+    }
+    __device__ static R end(const S& s, uint32_t, const FamParams&) { return RealOps<R>::exp_(-s.t); }
+};
+
+template <typename R> struct Family<MCUBES_F_DISCONT, R> {
+    struct S { R t; bool out; };
+    __device__ static void begin(S& s) { s.t = R(0); s.out = false; }
+    __device__ static void add(S& s, int j, R x, const FamParams& f)
+    {
+        s.out |= !(x < RealOps<R>::par(f, 12 + j));
+        s.t += RealOps<R>::par(f, j) * x;
+    }
+    __device__ static R end(const S& s, uint32_t, const FamParams&)
+    {
+        return s.out ? R(0) : RealOps<R>::exp_(s.t);
+    }
+};
+
+template <typename R> struct Family<MCUBES_F_COSMO6, R> {
+    // f = c10 exp(-sum a_i L_i - L_3 - L_4 - (L_3-mu)^2 h - (L_4-mu)^2 h - (x_1+x_2-r)^2 ht)
+    // with L_i = ln x_i (the 1/(x_3 x_4) of the lognormals folded into the exponent)
+    struct S { R e; R x12; };
+    __device__ static void begin(S& s) { s.e = R(0); s.x12 = R(0); }
+    __device__ static void add(S& s, int j, R x, const FamParams& f)
+    {
+        const R L = RealOps<R>::log_(x);
+        s.e += RealOps<R>::par(f, j) * L;
+        if (j == 2 || j == 3) {
+            const R z = L - RealOps<R>::par(f, 6);
+            s.e += L + z * z * RealOps<R>::par(f, 7);
+        }
+        if (j < 2) s.x12 += x;
+    }
+    __device__ static R end(const S& s, uint32_t, const FamParams& f)
+    {
+        const R z = s.x12 - RealOps<R>::par(f, 8);
+        return RealOps<R>::par(f, 10) * RealOps<R>::exp_(-(s.e + z * z * RealOps<R>::par(f, 9)));
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Compensated single-precision accumulator (Knuth's TwoSum; the pair holds
+// about 48 significant bits).  Used for the per-thread sums over cubes of the
+// mixed-precision path, which must not issue FP64 work per sample.
+// ---------------------------------------------------------------------------
+struct DFloat {
+    float hi, lo;
+    __device__ void add(float v)
+    {
+        const float s = __fadd_rn(hi, v);
+        const float bp = __fsub_rn(s, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(v, bp));
+        hi = s;
+        lo = __fadd_rn(lo, err);
+    }
+    __device__ double value() const { return (double)hi + (double)lo; }
+};
+
+}  // namespace mc

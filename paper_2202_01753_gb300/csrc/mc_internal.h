@@ -1,0 +1,89 @@
+// mc_internal.h -- structures shared by the host driver and the kernels of
+// the GB300 m-Cubes library.  Not part of the public ABI (include/mcubes.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "mcubes.h"
+
+namespace mc {
+
+constexpr int kDMax = MCUBES_DMAX;
+constexpr int kNbMax = MCUBES_NBMAX;
+constexpr int kParMax = MCUBES_PARAMS_MAX;
+constexpr int kItMax = MCUBES_ITMAX_MAX;
+constexpr int kVsThreads = 256;    // sampling block size (8 warps)
+constexpr int kRefineThreads = 512;
+
+// Per-integral state kept on the device across iterations, so that the whole
+// iteration loop (sample -> refine -> weight -> converge) runs without the
+// host.  One instance per single-integral context.
+struct DevState {
+    uint32_t it;        // iteration index of the next sampling pass
+    int done;           // converged or failed: further iterations are skipped
+    int active;         // set by the sampling launch: this iteration ran
+    int error;          // mcubes_status of a failure seen on the device
+    int n;              // iterations recorded
+    int converged;
+    double estimate, sigma, chi2_dof;
+    double rel_tol, abs_tol;
+    double hist_I[kItMax];
+    double hist_V[kItMax];
+};
+
+// Integrand constants in the form the kernels use (derived on the host from
+// the public params blob, see integrand_prepare in capi.cu).
+struct FamParams {
+    double c[kParMax];
+    float cf[kParMax];
+};
+
+// Arguments of one sampling launch (Alg. 3).  Passed by value as a
+// __grid_constant__ kernel parameter: indices known at compile time become
+// constant-bank operands.
+struct VsArgs {
+    const double* grid;       // [d][nb] right edges, unit coordinates
+    double* part;             // [gridDim][3]: sum of cube means, of their variances, of |means|
+    void* part_hist;          // [gridDim][d][nb] per-block sums of F^2 (double or float)
+    DevState* st;             // iteration state; nullptr -> use it_fixed and always run
+    uint32_t it_fixed;
+    uint32_t d, nb, g, gmagic;  // gmagic = floor((2^32-1)/g)
+    uint32_t p, lanes;          // samples per cube, threads per cube (power of two <= 32)
+    uint64_t cube_begin, cube_end;
+    uint32_t rk[10][2];       // Philox round keys (key + r * Weyl constants)
+    double lo[kDMax];
+    double scale[kDMax];      // hi - lo
+    double jac_const;         // nb^d
+    double inv_g_2p33;        // 2^-33 / g
+    float inv_g_f;            // 1/g
+    float nb_f;
+    FamParams fam;
+};
+
+struct RefineArgs {
+    double* grid;             // [d][nb], updated in place by the rebin blocks
+    double* hist;             // [d][nb] reduced histogram (written for read-back)
+    const double* part;       // [nblocks][3]
+    const void* part_hist;    // [nblocks][d][nb]
+    DevState* st;
+    int nblocks, d, nb, adjust, hist_is_float;
+    double alpha;
+    double m;                 // number of cubes
+};
+
+// Launchers (one per integrand family translation unit).
+cudaError_t launch_vsample(int family, bool mixed, bool adjust, const VsArgs& a, int grid,
+                           size_t smem, cudaStream_t s);
+size_t vsample_smem_bytes(bool mixed, bool adjust, int d, int nb);
+cudaError_t vsample_occupancy(int family, bool mixed, bool adjust, size_t smem, int* blocks_per_sm);
+
+cudaError_t launch_refine(const RefineArgs& a, cudaStream_t s);
+cudaError_t launch_reduce_range(const double* part, const void* part_hist, int hist_is_float,
+                                int nblocks, int d, int nb, int adjust, double* out_sums,
+                                double* out_hist, cudaStream_t s);
+cudaError_t launch_init_grid(double* grid, int d, int nb, cudaStream_t s);
+
+}  // namespace mc

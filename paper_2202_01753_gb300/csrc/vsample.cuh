@@ -1,0 +1,281 @@
+// vsample.cuh -- the sampling kernel (V-Sample / V-Sample-No-Adjust of
+// Alg. 3 in the paper), instantiated once per integrand family by the
+// vsample_<family>.cu translation units.
+//
+// Work layout.  A run of `lanes` consecutive threads of a warp owns one
+// sub-cube; lane l of the run draws samples l, l + lanes, ... of it.  With
+// lanes == 1 (the common case: p is 2 or 3 at 1e8-1e9 calls) a thread owns
+// whole cubes and its cube moments need no communication; larger p spreads a
+// cube over up to 32 lanes whose moments are merged by XOR shuffles.  Blocks
+// walk the cube range with a grid stride.  The bin grid of all axes is staged
+// in shared memory once per block as (left edge, width[, Jacobian factor])
+// cells in the integration box's coordinates.  In adjusting iterations every
+// sample adds F^2 to a per-block shared-memory histogram [d][nb], flushed to
+// global memory once at the end of the block: no per-sample global atomics.
+// Each block writes three double partials (sum of cube means, of their
+// variances, of |means|) which the refinement launch reduces in fixed order.
+#pragma once
+
+#include "mc_device.cuh"
+
+namespace mc {
+
+template <bool MIXED> struct Prec;
+template <> struct Prec<false> {
+    using R = double;
+    using Cell = double2;  // (x left, x width); Jacobian factor = width, times nb^d at the end
+    using H = double;
+};
+template <> struct Prec<true> {
+    using R = float;
+    using Cell = float4;   // (x left, x width, nb * x width, unused)
+    using H = float;
+};
+
+// One sample: random words -> exact bin position -> map -> integrand.
+// Returns F = f(x) * J and leaves the flat histogram index of every axis in idx.
+template <int FAM, bool MIXED>
+__device__ __forceinline__ typename Prec<MIXED>::R
+sample_point(const VsArgs& a, const typename Prec<MIXED>::Cell* cells, uint32_t c, uint32_t s,
+             uint32_t it, const uint32_t (&nbc)[kDMax], uint32_t (&idx)[kDMax])
+{
+    using R = typename Prec<MIXED>::R;
+    using Fam = Family<FAM, R>;
+    const uint32_t d = a.d, nb = a.nb;
+    uint32_t w[kDMax];
+#pragma unroll
+    for (int b = 0; b < kDMax / 4; ++b) {
+        if (4 * b < (int)d) {
+            const uint4 r = philox4x32_10(make_uint4(s, c, it, (uint32_t)b), a.rk);
+            w[4 * b + 0] = r.x;
+            w[4 * b + 1] = r.y;
+            w[4 * b + 2] = r.z;
+            w[4 * b + 3] = r.w;
+        }
+    }
+    typename Fam::S fs;
+    Fam::begin(fs);
+    R jac = R(1);
+#pragma unroll
+    for (int j = 0; j < kDMax; ++j) {
+        if (j < (int)d) {
+            const BinPos bp = bin_pos(w[j], nbc[j], nb, a.g, a.gmagic);
+            const uint32_t flat = (uint32_t)j * nb + bp.k;
+            const auto cell = cells[flat];
+            R x;
+            if constexpr (MIXED) {
+                const float phi = bin_phi_f32(bp, a.inv_g_f);
+                x = fmaf(cell.y, phi, cell.x);
+                jac *= cell.z;
+            } else {
+                const double phi = bin_phi_f64(bp, a.inv_g_2p33);
+                x = fma(cell.y, phi, cell.x);
+                jac *= cell.y;
+            }
+            Fam::add(fs, j, x, a.fam);
+            idx[j] = flat;
+        }
+    }
+    R F = Fam::end(fs, d, a.fam) * jac;
+    if constexpr (!MIXED) F *= a.jac_const;
+    return F;
+}
+
+template <int FAM, bool MIXED, bool ADJ>
+__global__ void __launch_bounds__(kVsThreads)
+vsample_kernel(const __grid_constant__ VsArgs a)
+{
+    using R = typename Prec<MIXED>::R;
+    using Cell = typename Prec<MIXED>::Cell;
+    using HT = typename Prec<MIXED>::H;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double red[3][kVsThreads / 32];
+
+    const uint32_t d = a.d, nb = a.nb;
+    uint32_t it = a.it_fixed;
+    if (a.st != nullptr) {
+        const int done = *(volatile const int*)&a.st->done;
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.st->active = done ? 0 : 1;
+        if (done) return;
+        it = *(volatile const uint32_t*)&a.st->it;
+    }
+
+    Cell* cells = reinterpret_cast<Cell*>(smem);
+    HT* hist = reinterpret_cast<HT*>(smem + sizeof(Cell) * d * nb);
+    for (uint32_t i = threadIdx.x; i < d * nb; i += blockDim.x) {
+        const uint32_t j = i / nb, k = i - j * nb;
+        const double right = a.grid[i];
+        const double left = k ? a.grid[i - 1] : 0.0;
+        const double xl = a.lo[j] + a.scale[j] * left;
+        const double xw = a.scale[j] * (right - left);
+        if constexpr (MIXED) cells[i] = make_float4((float)xl, (float)xw, (float)(xw * (double)nb), 0.0f);
+        else cells[i] = make_double2(xl, xw);
+        if constexpr (ADJ) hist[i] = HT(0);
+    }
+    __syncthreads();
+
+    const uint32_t L = a.lanes;
+    const uint32_t seg_lane = threadIdx.x & (L - 1u);
+    const uint32_t cubes_per_round = blockDim.x / L;
+    const uint64_t ncubes = a.cube_end - a.cube_begin;
+    const uint64_t stride = (uint64_t)gridDim.x * cubes_per_round;
+
+    double accI = 0.0, accV = 0.0, accA = 0.0;
+    DFloat dfI{0.f, 0.f}, dfV{0.f, 0.f}, dfA{0.f, 0.f};
+
+    for (uint64_t base = (uint64_t)blockIdx.x * cubes_per_round; base < ncubes; base += stride) {
+        const uint64_t ci = base + threadIdx.x / L;
+        const bool valid = ci < ncubes;
+        const uint32_t c = (uint32_t)(a.cube_begin + (valid ? ci : 0));
+        // sub-cube digits (axis 0 fastest), kept as nb * digit
+        uint32_t nbc[kDMax];
+        {
+            uint32_t rest = c;
+#pragma unroll
+            for (int j = 0; j < kDMax; ++j) {
+                if (j < (int)d) {
+                    uint32_t q = __umulhi(rest, a.gmagic);
+                    uint32_t r = rest - q * a.g;
+                    if (r >= a.g) { ++q; r -= a.g; }
+                    if (r >= a.g) { ++q; r -= a.g; }
+                    nbc[j] = r * nb;
+                    rest = q;
+                }
+            }
+        }
+        // this lane's samples of the cube, shifted by its first value
+        R K = R(0), S1 = R(0), S2 = R(0);
+        uint32_t n = 0;
+        if (valid) {
+            for (uint32_t s = seg_lane; s < a.p; s += L) {
+                uint32_t idx[kDMax];
+                const R F = sample_point<FAM, MIXED>(a, cells, c, s, it, nbc, idx);
+                if (n == 0) K = F;
+                const R z = F - K;
+                S1 += z;
+                S2 += z * z;
+                ++n;
+                if constexpr (ADJ) {
+                    const HT F2 = (HT)(F * F);
+#pragma unroll
+                    for (int j = 0; j < kDMax; ++j)
+                        if (j < (int)d) atomicAdd(&hist[idx[j]], F2);
+                }
+            }
+        }
+        if (L == 1u) {
+            if (valid) {
+                // UpdateVariance (Alg. 3): cube mean and the variance of that mean
+                const R pf = R(a.p);
+                const R mean = K + S1 / pf;
+                const R var = (S2 - S1 * S1 / pf) / (pf * (pf - R(1)));
+                if constexpr (MIXED) {
+                    dfI.add(mean);
+                    dfV.add(var);
+                    dfA.add(fabsf(mean));
+                } else {
+                    accI += mean;
+                    accV += var;
+                    accA += fabs(mean);
+                }
+            }
+        } else {
+            // merge (count, mean, M2) across the cube's lanes (Chan et al.)
+            double cnt = (double)n;
+            double mean = n ? (double)K + (double)S1 / cnt : 0.0;
+            double M2 = n ? (double)S2 - (double)S1 * (double)S1 / cnt : 0.0;
+            for (uint32_t off = 1; off < L; off <<= 1) {
+                const double cnt_o = __shfl_xor_sync(0xffffffffu, cnt, off);
+                const double mean_o = __shfl_xor_sync(0xffffffffu, mean, off);
+                const double M2_o = __shfl_xor_sync(0xffffffffu, M2, off);
+                const double tot = cnt + cnt_o;
+                if (tot > 0.0) {
+                    const double delta = mean_o - mean;
+                    mean += delta * (cnt_o / tot);
+                    M2 += M2_o + delta * delta * (cnt * cnt_o / tot);
+                }
+                cnt = tot;
+            }
+            if (valid && seg_lane == 0) {
+                const double var = M2 / (cnt * (cnt - 1.0));
+                accI += mean;
+                accV += var;
+                accA += fabs(mean);
+            }
+        }
+    }
+
+    // block partials, reduced in a fixed order
+    double v0 = accI + dfI.value(), v1 = accV + dfV.value(), v2 = accA + dfA.value();
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        v0 += __shfl_down_sync(0xffffffffu, v0, off);
+        v1 += __shfl_down_sync(0xffffffffu, v1, off);
+        v2 += __shfl_down_sync(0xffffffffu, v2, off);
+    }
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red[0][warp] = v0;
+        red[1][warp] = v1;
+        red[2][warp] = v2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            s0 += red[0][w];
+            s1 += red[1][w];
+            s2 += red[2][w];
+        }
+        a.part[3 * (size_t)blockIdx.x + 0] = s0;
+        a.part[3 * (size_t)blockIdx.x + 1] = s1;
+        a.part[3 * (size_t)blockIdx.x + 2] = s2;
+    }
+    if constexpr (ADJ) {
+        HT* out = reinterpret_cast<HT*>(a.part_hist) + (size_t)blockIdx.x * d * nb;
+        for (uint32_t i = threadIdx.x; i < d * nb; i += blockDim.x) out[i] = hist[i];
+    }
+}
+
+template <int FAM>
+inline auto vsample_kernel_ptr(bool mixed, bool adjust)
+{
+    using K = void (*)(VsArgs);
+    if (mixed) return adjust ? (K)vsample_kernel<FAM, true, true> : (K)vsample_kernel<FAM, true, false>;
+    return adjust ? (K)vsample_kernel<FAM, false, true> : (K)vsample_kernel<FAM, false, false>;
+}
+
+template <int FAM>
+cudaError_t launch_vsample_family(bool mixed, bool adjust, const VsArgs& a, int grid, size_t smem,
+                                  cudaStream_t s)
+{
+    auto k = vsample_kernel_ptr<FAM>(mixed, adjust);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, kVsThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int FAM>
+cudaError_t occupancy_family(bool mixed, bool adjust, size_t smem, int* blocks)
+{
+    auto k = vsample_kernel_ptr<FAM>(mixed, adjust);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, kVsThreads, smem);
+}
+
+}  // namespace mc
+
+#define MC_INSTANTIATE_FAMILY(FAM, NAME)                                                          \
+    namespace mc {                                                                                \
+    cudaError_t launch_vsample_##NAME(bool mixed, bool adjust, const VsArgs& a, int grid,         \
+                                      size_t smem, cudaStream_t s)                                \
+    {                                                                                             \
+        return launch_vsample_family<FAM>(mixed, adjust, a, grid, smem, s);                       \
+    }                                                                                             \
+    cudaError_t occupancy_##NAME(bool mixed, bool adjust, size_t smem, int* blocks)               \
+    {                                                                                             \
+        return occupancy_family<FAM>(mixed, adjust, smem, blocks);                                \
+    }                                                                                             \
+    }

@@ -1,0 +1,271 @@
+"""Thin ctypes binding of the C ABI in include/mcubes.h.
+
+Argument marshalling only: every step of an integration runs in the CUDA
+kernels of libmcubes.  Functions keep the C names.  Loading fails loudly if
+the library has not been built (``python -m paper_2202_01753_gb300.build``);
+there is no other implementation to fall back to.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ENOCONV, ETIMEOUT, ESTATE = range(8)
+FP64, MIXED = 0, 1
+DMAX, NBMAX, PARAMS_MAX, ITMAX_MAX = 12, 1024, 32, 4096
+
+EXPORTED = [
+    "mcubes_default_opts", "mcubes_create", "mcubes_create_on_stream", "mcubes_set_opts",
+    "mcubes_destroy", "mcubes_strerror", "mcubes_last_cuda_error", "mcubes_integrate",
+    "mcubes_integrate_batch", "mcubes_setup", "mcubes_iterate", "mcubes_result_get",
+    "mcubes_trace_get", "mcubes_grid_get", "mcubes_grid_set", "mcubes_hist_get",
+    "mcubes_sample_range", "mcubes_geometry_get", "mcubes_timing_reset", "mcubes_timing_get",
+]
+
+
+class mcubes_opts(ctypes.Structure):
+    _fields_ = [("nbins", ctypes.c_int), ("ita", ctypes.c_int), ("g_override", ctypes.c_longlong),
+                ("alpha", ctypes.c_double), ("seed", ctypes.c_uint64), ("precision", ctypes.c_int),
+                ("lanes_per_cube", ctypes.c_int), ("blocks_per_sm", ctypes.c_int)]
+
+
+class mcubes_result(ctypes.Structure):
+    _fields_ = [("estimate", ctypes.c_double), ("sigma", ctypes.c_double), ("chi2_dof", ctypes.c_double),
+                ("iterations", ctypes.c_int), ("converged", ctypes.c_int),
+                ("samples_per_iter", ctypes.c_longlong), ("g", ctypes.c_longlong),
+                ("m", ctypes.c_longlong), ("p", ctypes.c_longlong), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class mcubes_request(ctypes.Structure):
+    _fields_ = [("integrand_id", ctypes.c_int), ("params", ctypes.POINTER(ctypes.c_double)),
+                ("nparams", ctypes.c_int), ("d", ctypes.c_int), ("lo", ctypes.POINTER(ctypes.c_double)),
+                ("hi", ctypes.POINTER(ctypes.c_double)), ("ncall", ctypes.c_longlong),
+                ("itmax", ctypes.c_int), ("rel_tol", ctypes.c_double), ("abs_tol", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.lib_path()
+
+
+def lib():
+    """The loaded libmcubes (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"libmcubes is not built ({path} missing): run "
+                                   "`python -m paper_2202_01753_gb300.build` on a machine with nvcc")
+            h = ctypes.CDLL(path)
+            P = ctypes.POINTER
+            dp = P(ctypes.c_double)
+            ctx = ctypes.c_void_p
+            ll = ctypes.c_longlong
+            sig = {
+                "mcubes_default_opts": (None, [P(mcubes_opts)]),
+                "mcubes_create": (ctypes.c_int, [P(ctx), ctypes.c_int, P(mcubes_opts)]),
+                "mcubes_create_on_stream": (ctypes.c_int, [P(ctx), ctypes.c_int, P(mcubes_opts), ctypes.c_void_p]),
+                "mcubes_set_opts": (ctypes.c_int, [ctx, P(mcubes_opts)]),
+                "mcubes_destroy": (ctypes.c_int, [ctx]),
+                "mcubes_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+                "mcubes_last_cuda_error": (ctypes.c_char_p, [ctx]),
+                "mcubes_integrate": (ctypes.c_int, [ctx, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, dp, dp, ll,
+                                                    ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                                    P(mcubes_result)]),
+                "mcubes_integrate_batch": (ctypes.c_int, [ctx, ctypes.c_int, P(mcubes_request), P(mcubes_result)]),
+                "mcubes_setup": (ctypes.c_int, [ctx, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, dp, dp, ll,
+                                                ctypes.c_int, ctypes.c_double, ctypes.c_double]),
+                "mcubes_iterate": (ctypes.c_int, [ctx, ctypes.c_int]),
+                "mcubes_result_get": (ctypes.c_int, [ctx, P(mcubes_result)]),
+                "mcubes_trace_get": (ctypes.c_int, [ctx, dp, dp, ctypes.c_int, P(ctypes.c_int)]),
+                "mcubes_grid_get": (ctypes.c_int, [ctx, dp, ll]),
+                "mcubes_grid_set": (ctypes.c_int, [ctx, dp, ll]),
+                "mcubes_hist_get": (ctypes.c_int, [ctx, dp, ll]),
+                "mcubes_sample_range": (ctypes.c_int, [ctx, ctypes.c_uint, ctypes.c_int, ll, ll, dp, dp]),
+                "mcubes_geometry_get": (ctypes.c_int, [ctx, P(ll), P(ll), P(ll), P(ctypes.c_int),
+                                                       P(ctypes.c_int)]),
+                "mcubes_timing_reset": (ctypes.c_int, [ctx, ctypes.c_int]),
+                "mcubes_timing_get": (ctypes.c_int, [ctx, dp, P(ctypes.c_int), dp, P(ctypes.c_int)]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(h, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = h
+    return _lib
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+class McubesError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        msg = lib().mcubes_strerror(status).decode()
+        super().__init__(f"{where}: {msg} ({status}){' ' + detail if detail else ''}")
+        self.status = status
+
+
+def mcubes_default_opts() -> mcubes_opts:
+    o = mcubes_opts()
+    lib().mcubes_default_opts(ctypes.byref(o))
+    return o
+
+
+def make_opts(**kw) -> mcubes_opts:
+    o = mcubes_default_opts()
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = {"fp64": FP64, "mixed": MIXED}[v]
+        setattr(o, k, v)
+    return o
+
+
+class Context:
+    """One mcubes_ctx: a device, a stream and the buffers of one integral."""
+
+    def __init__(self, device: int = 0, stream: int | None = None, **opts):
+        self._h = ctypes.c_void_p()
+        o = make_opts(**opts)
+        if stream is None:
+            st = lib().mcubes_create(ctypes.byref(self._h), device, ctypes.byref(o))
+        else:
+            st = lib().mcubes_create_on_stream(ctypes.byref(self._h), device, ctypes.byref(o),
+                                               ctypes.c_void_p(stream))
+        if st != OK:
+            raise McubesError(st, "mcubes_create")
+        self.d = self.nb = 0
+        self.opts = o
+
+    # -- lifecycle -----------------------------------------------------
+    def close(self):
+        if self._h:
+            lib().mcubes_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, where, ok=(OK,)):
+        if st not in ok:
+            detail = lib().mcubes_last_cuda_error(self._h).decode() if st == ECUDA else ""
+            raise McubesError(st, where, detail)
+        return st
+
+    def set_opts(self, **opts):
+        o = make_opts(**opts)
+        self._check(lib().mcubes_set_opts(self._h, ctypes.byref(o)), "mcubes_set_opts")
+        self.opts = o
+
+    # -- whole integrations --------------------------------------------
+    def integrate(self, fid, params, lo, hi, ncall, itmax, rel_tol=0.0, abs_tol=0.0):
+        p, lo, hi = _f64(params), _f64(lo), _f64(hi)
+        res = mcubes_result()
+        st = lib().mcubes_integrate(self._h, fid, _dp(p), len(p), len(lo), _dp(lo), _dp(hi), int(ncall), itmax,
+                                    rel_tol, abs_tol, ctypes.byref(res))
+        self._check(st, "mcubes_integrate", ok=(OK, ENOCONV))
+        self.d, self.nb = len(lo), self.opts.nbins
+        return res.as_dict()
+
+    def integrate_batch(self, requests):
+        """requests: iterable of dicts with keys fid, params, lo, hi, ncall, itmax, rel_tol, abs_tol, seed."""
+        reqs = list(requests)
+        keep = []
+        arr = (mcubes_request * len(reqs))()
+        for i, r in enumerate(reqs):
+            p, lo, hi = _f64(r["params"]), _f64(r["lo"]), _f64(r["hi"])
+            keep += [p, lo, hi]
+            arr[i] = mcubes_request(r["fid"], _dp(p), len(p), len(lo), _dp(lo), _dp(hi), int(r["ncall"]),
+                                    int(r["itmax"]), float(r.get("rel_tol", 0.0)), float(r.get("abs_tol", 0.0)),
+                                    int(r.get("seed", 0)))
+        outs = (mcubes_result * len(reqs))()
+        self._check(lib().mcubes_integrate_batch(self._h, len(reqs), arr, outs), "mcubes_integrate_batch")
+        return [o.as_dict() for o in outs]
+
+    # -- step-level -------------------------------------------------------
+    def setup(self, fid, params, lo, hi, ncall, itmax, rel_tol=0.0, abs_tol=0.0):
+        p, lo, hi = _f64(params), _f64(lo), _f64(hi)
+        self._check(lib().mcubes_setup(self._h, fid, _dp(p), len(p), len(lo), _dp(lo), _dp(hi), int(ncall), itmax,
+                                       rel_tol, abs_tol), "mcubes_setup")
+        self.d, self.nb = len(lo), self.opts.nbins
+
+    def iterate(self, n_iter=1):
+        self._check(lib().mcubes_iterate(self._h, n_iter), "mcubes_iterate")
+
+    def result(self):
+        res = mcubes_result()
+        self._check(lib().mcubes_result_get(self._h, ctypes.byref(res)), "mcubes_result_get",
+                    ok=(OK, ENOCONV, ENONFINITE))
+        return res.as_dict()
+
+    def trace(self, cap=ITMAX_MAX):
+        I = np.zeros(cap)
+        V = np.zeros(cap)
+        n = ctypes.c_int()
+        self._check(lib().mcubes_trace_get(self._h, _dp(I), _dp(V), cap, ctypes.byref(n)), "mcubes_trace_get")
+        k = min(n.value, cap)
+        return I[:k], V[:k]
+
+    def grid(self):
+        B = np.zeros(self.d * self.nb)
+        self._check(lib().mcubes_grid_get(self._h, _dp(B), B.size), "mcubes_grid_get")
+        return B.reshape(self.d, self.nb)
+
+    def set_grid(self, B):
+        B = _f64(B).reshape(-1)
+        self._check(lib().mcubes_grid_set(self._h, _dp(B), B.size), "mcubes_grid_set")
+
+    def hist(self):
+        C = np.zeros(self.d * self.nb)
+        self._check(lib().mcubes_hist_get(self._h, _dp(C), C.size), "mcubes_hist_get")
+        return C.reshape(self.d, self.nb)
+
+    def sample_range(self, it, adjust, cube_begin, cube_end):
+        sums = np.zeros(3)
+        C = np.zeros(self.d * self.nb) if adjust else None
+        self._check(lib().mcubes_sample_range(self._h, it, int(adjust), int(cube_begin), int(cube_end), _dp(sums),
+                                              _dp(C)), "mcubes_sample_range")
+        return sums, (None if C is None else C.reshape(self.d, self.nb))
+
+    def geometry(self):
+        g, m, p = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        lanes, blocks = ctypes.c_int(), ctypes.c_int()
+        self._check(lib().mcubes_geometry_get(self._h, ctypes.byref(g), ctypes.byref(m), ctypes.byref(p),
+                                              ctypes.byref(lanes), ctypes.byref(blocks)), "mcubes_geometry_get")
+        return dict(g=g.value, m=m.value, p=p.value, lanes=lanes.value, blocks=blocks.value)
+
+    def timing_reset(self, enable=True):
+        self._check(lib().mcubes_timing_reset(self._h, int(enable)), "mcubes_timing_reset")
+
+    def timing(self):
+        sm, rm = ctypes.c_double(), ctypes.c_double()
+        sn, rn = ctypes.c_int(), ctypes.c_int()
+        self._check(lib().mcubes_timing_get(self._h, ctypes.byref(sm), ctypes.byref(sn), ctypes.byref(rm),
+                                            ctypes.byref(rn)), "mcubes_timing_get")
+        return dict(sample_ms=sm.value, sample_launches=sn.value, refine_ms=rm.value, refine_launches=rn.value)

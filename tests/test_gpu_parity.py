@@ -1,0 +1,273 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances.  The double-precision path evaluates the same samples (same
+Philox words, same exact bin indices) and differs from the oracle only in
+rounding: the order of summation, CUDA's vs glibc's exp/log/cos/pow, and the
+algebraically equal forms of the map and the integrands the kernels use.  Per
+iteration the estimate must agree within 1e-12 relative to its conditioning
+scale max(|I|, sum |cube means| / m), the variance within 1e-12 relative (1e-10
+for the oscillatory family, whose cube variances come from differences of
+nearly equal values), the grid within 1e-12 absolute, the histogram within
+1e-12 relative.  The mixed-precision path is compared with the same oracle
+against a stated bound (single-precision map and integrand).
+"""
+import numpy as np
+import pytest
+
+import closed_forms as CF
+import oracle
+from paper_2202_01753_gb300 import mcubes
+from paper_2202_01753_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RTOL_I = 1e-12
+RTOL_V = 1e-12
+
+
+def oracle_run(w, **kw):
+    args = dict(ita=w.ita, nb=w.nb, g_override=w.g_override, seed=w.seed, rel_tol=w.rel_tol, abs_tol=w.abs_tol)
+    args.update(kw)
+    return oracle.integrate(w.fid, w.params, w.lo, w.hi, w.ncall, w.itmax, **args)
+
+
+def gpu_run(make_ctx, w, precision="fp64", **opts):
+    ita = -1 if w.ita is None else w.ita
+    ctx = make_ctx(nbins=w.nb, ita=ita, g_override=w.g_override, seed=w.seed, precision=precision, **opts)
+    res = ctx.integrate(w.fid, w.params, w.lo, w.hi, w.ncall, w.itmax, w.rel_tol, w.abs_tol)
+    I, V = ctx.trace()
+    out = dict(res=res, I=I, V=V, grid=ctx.grid(), hist=ctx.hist(), geom=ctx.geometry())
+    ctx.close()
+    return out
+
+
+def cond_scale(w, o):
+    # |I| or, for cancelling integrands, the mean absolute cube value
+    pb = oracle.Problem(w.fid, w.params, w.lo, w.hi, w.ncall, nb=w.nb, g_override=w.g_override, seed=w.seed)
+    B = oracle.init_grid(pb.d, pb.nb)
+    sums, _, _, _ = pb.vsample(B, 0, False, 0, min(pb.m, 2000))
+    return max(np.max(np.abs(o["trace_I"])), sums[2] / min(pb.m, 2000))
+
+
+def assert_parity(w, o, g, vtol=RTOL_V):
+    assert g["res"]["iterations"] == o["iterations"]
+    assert (g["res"]["g"], g["res"]["m"], g["res"]["p"]) == (o["g"], o["m"], o["p"])
+    scale = cond_scale(w, o)
+    np.testing.assert_allclose(g["I"], o["trace_I"], rtol=0, atol=RTOL_I * scale)
+    np.testing.assert_allclose(g["V"], o["trace_var"], rtol=vtol, atol=0)
+    np.testing.assert_allclose(g["grid"], o["grid"], rtol=0, atol=1e-12)
+    adjusting = o["iterations"] if w.ita is None else min(w.ita, o["iterations"])
+    if adjusting > 0:
+        np.testing.assert_allclose(g["hist"], o["hist"], rtol=1e-12, atol=1e-300)
+    assert g["res"]["estimate"] == pytest.approx(o["estimate"], abs=RTOL_I * scale)
+    assert g["res"]["sigma"] == pytest.approx(o["sigma"], rel=vtol)
+    assert g["res"]["chi2_dof"] == pytest.approx(o["chi2_dof"], rel=1e-9, abs=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# whole runs, double precision
+# ---------------------------------------------------------------------------
+def test_gauss3_full_config(gpu_ctx_factory):
+    """d=3 Gaussian, m=64, p=16384 (32 lanes per cube), 10 iterations, 2^20 samples each."""
+    w = W.gauss3()
+    o = oracle_run(w)
+    g = gpu_run(gpu_ctx_factory, w)
+    assert g["geom"]["lanes"] == 32
+    assert_parity(w, o, g)
+    assert abs(g["res"]["estimate"] - CF.exact(w)) < 4 * g["res"]["sigma"]
+
+
+@pytest.mark.parametrize("name,d,ncall", [
+    ("f1", 3, 60_000), ("f2", 4, 60_000), ("f3", 5, 60_000), ("f4", 3, 60_000),
+    ("f5", 2, 60_000), ("f6", 3, 60_000), ("fA", None, 80_000), ("fB", None, 200_000),
+])
+def test_paper_suite(gpu_ctx_factory, name, d, ncall):
+    w = W.suite(name, d, ncall=ncall, itmax=5, seed=7)
+    o = oracle_run(w)
+    g = gpu_run(gpu_ctx_factory, w)
+    assert_parity(w, o, g, vtol=1e-10 if w.fid == W.F_OSC else RTOL_V)
+
+
+def test_cosmo6_scaled(gpu_ctx_factory):
+    w = W.cosmo6().scaled(400_000, itmax=6)
+    o = oracle_run(w)
+    g = gpu_run(gpu_ctx_factory, w)
+    assert_parity(w, o, g)
+
+
+@pytest.mark.parametrize("make", [W.corner8, W.osc10])
+def test_mixed_configs_in_fp64_scaled(gpu_ctx_factory, make):
+    w = make().scaled(300_000, itmax=4)
+    o = oracle_run(w)
+    g = gpu_run(gpu_ctx_factory, w)
+    assert_parity(w, o, g, vtol=1e-10 if w.fid == W.F_OSC else RTOL_V)
+
+
+@pytest.mark.parametrize("d,ncall,nb,lanes", [
+    (1, 5_000, 2, 0),        # one axis, two bins
+    (12, 100, 7, 0),         # g = 1: one cube of 100 samples, lanes > 1
+    (12, 20_000, 780, 0),    # the largest dimension with the largest grid that fits
+    (8, 20_000, 1024, 0),    # the largest bin count
+    (2, 9_999, 500, 4),      # forced lanes with a ragged p (p = 4999/... )
+    (5, 77_777, 333, 8),
+])
+def test_edge_shapes(gpu_ctx_factory, d, ncall, nb, lanes):
+    rng = np.random.Generator(np.random.PCG64(d * 1000 + nb))
+    w = W.random_integral(rng, d, W.F_GAUSS, ncall, itmax=3, seed=11)
+    w.nb = nb
+    w.precision = "fp64"
+    o = oracle_run(w)
+    g = gpu_run(gpu_ctx_factory, w, lanes_per_cube=lanes)
+    assert_parity(w, o, g)
+
+
+def test_no_adjust_iterations_keep_grid(gpu_ctx_factory):
+    w = W.suite("f4", 3, ncall=50_000, itmax=5)
+    w.ita = 2
+    o = oracle_run(w)
+    g = gpu_run(gpu_ctx_factory, w)
+    assert_parity(w, o, g)
+
+
+def test_convergence_and_early_stop(gpu_ctx_factory):
+    w = W.gauss3().scaled(2 ** 16, rel_tol=1e-3)
+    o = oracle_run(w)
+    g = gpu_run(gpu_ctx_factory, w)
+    assert o["converged"] and g["res"]["converged"]
+    assert_parity(w, o, g)
+
+
+def test_nonfinite_reported(gpu_ctx_factory):
+    w = W.suite("f4", 2, ncall=2_000, itmax=3)
+    w.params = w.params.copy()
+    w.params[0] = 1e300
+    ctx = gpu_ctx_factory()
+    with pytest.raises(mcubes.McubesError) as e:
+        ctx.integrate(w.fid, w.params, w.lo, w.hi, w.ncall, w.itmax)
+    assert e.value.status == mcubes.ENONFINITE
+    ctx.close()
+
+
+def test_grid_too_large_for_shared_memory(gpu_ctx_factory):
+    # d = 12, nb = 900: 259 KB in FP64 (too large), 216 KB in MIXED (fits)
+    ctx = gpu_ctx_factory(nbins=900)
+    w = W.suite("f3", 12, ncall=10_000)
+    with pytest.raises(mcubes.McubesError) as e:
+        ctx.integrate(w.fid, w.params, w.lo, w.hi, w.ncall, 2)
+    assert e.value.status == mcubes.EINVAL
+    ctx.close()
+    ctx = gpu_ctx_factory(nbins=900, precision="mixed")
+    r = ctx.integrate(w.fid, w.params, w.lo, w.hi, w.ncall, 2)
+    assert r["iterations"] == 2
+    ctx.close()
+
+
+def test_invalid_arguments(gpu_ctx_factory):
+    ctx = gpu_ctx_factory()
+    w = W.suite("f3", 3)
+    bad = [
+        dict(fid=99), dict(params=w.params[:-1]), dict(lo=np.ones(3), hi=np.zeros(3)),
+        dict(ncall=1), dict(itmax=0), dict(params=np.full(3, np.nan)),
+    ]
+    for b in bad:
+        kw = dict(fid=w.fid, params=w.params, lo=w.lo, hi=w.hi, ncall=1000, itmax=2)
+        kw.update(b)
+        with pytest.raises(mcubes.McubesError) as e:
+            ctx.integrate(kw["fid"], kw["params"], kw["lo"], kw["hi"], kw["ncall"], kw["itmax"])
+        assert e.value.status == mcubes.EINVAL
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# full-size geometries, sampled cube ranges (launch shape of the benchmark)
+# ---------------------------------------------------------------------------
+def _ranges(m, width):
+    return [(0, width), (m // 2 - width // 2, m // 2 + width // 2), (m - width, m)]
+
+
+def _adapted_grid(w, ncall, iters=3):
+    o = oracle_run(w.scaled(ncall, itmax=iters))
+    return o["grid"]
+
+
+def test_cosmo6_full_size_sampled(gpu_ctx_factory):
+    w = W.cosmo6()
+    B = _adapted_grid(w, 300_000)
+    ctx = gpu_ctx_factory(seed=w.seed)
+    ctx.setup(w.fid, w.params, w.lo, w.hi, w.ncall, w.itmax)
+    geom = ctx.geometry()
+    assert (geom["g"], geom["m"], geom["p"]) == (19, 47045881, 2)
+    ctx.set_grid(B)
+    pb = oracle.Problem(w.fid, w.params, w.lo, w.hi, w.ncall, seed=w.seed)
+    for it in (0, 13):
+        for c0, c1 in _ranges(pb.m, 20_000):
+            s_o, C_o, _, _ = pb.vsample(B, it, True, c0, c1)
+            s_g, C_g = ctx.sample_range(it, True, c0, c1)
+            np.testing.assert_allclose(s_g, s_o, rtol=1e-12)
+            np.testing.assert_allclose(C_g, C_o, rtol=1e-12, atol=1e-300)
+    ctx.close()
+
+
+@pytest.mark.parametrize("make", [W.corner8, W.osc10])
+def test_full_size_sampled_fp64(gpu_ctx_factory, make):
+    w = make()
+    ctx = gpu_ctx_factory(seed=w.seed)
+    ctx.setup(w.fid, w.params, w.lo, w.hi, w.ncall, w.itmax)
+    pb = oracle.Problem(w.fid, w.params, w.lo, w.hi, w.ncall, seed=w.seed)
+    B = _adapted_grid(w, 200_000)
+    ctx.set_grid(B)
+    for c0, c1 in _ranges(pb.m, 10_000):
+        s_o, C_o, _, _ = pb.vsample(B, 5, True, c0, c1)
+        s_g, C_g = ctx.sample_range(5, True, c0, c1)
+        np.testing.assert_allclose(s_g[0], s_o[0], rtol=0, atol=1e-12 * s_o[2])
+        np.testing.assert_allclose(s_g[1:], s_o[1:], rtol=1e-10)
+        np.testing.assert_allclose(C_g, C_o, rtol=1e-12, atol=1e-300)
+    ctx.close()
+
+
+def test_empty_and_single_cube_ranges(gpu_ctx_factory):
+    w = W.suite("f4", 4, ncall=100_000)
+    ctx = gpu_ctx_factory(seed=w.seed)
+    ctx.setup(w.fid, w.params, w.lo, w.hi, w.ncall, w.itmax)
+    s, C = ctx.sample_range(0, True, 17, 17)
+    assert np.all(s == 0) and np.all(C == 0)
+    pb = oracle.Problem(w.fid, w.params, w.lo, w.hi, w.ncall, seed=w.seed)
+    s_o, C_o, _, _ = pb.vsample(oracle.init_grid(4, 500), 0, True, 17, 18)
+    s_g, C_g = ctx.sample_range(0, True, 17, 18)
+    np.testing.assert_allclose(s_g, s_o, rtol=1e-12)
+    np.testing.assert_allclose(C_g, C_o, rtol=1e-12, atol=1e-300)
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# mixed precision against the double-precision oracle
+# ---------------------------------------------------------------------------
+MIXED_BOUND = 2e-5   # relative error of an iteration estimate (single-precision map and f)
+
+
+@pytest.mark.parametrize("make,ncall", [(W.corner8, 400_000), (W.osc10, 400_000), (W.gauss3, 2 ** 18)])
+def test_mixed_precision_bound(gpu_ctx_factory, make, ncall):
+    w = make().scaled(ncall, itmax=5)
+    o = oracle_run(w)
+    g = gpu_run(gpu_ctx_factory, w, precision="mixed")
+    scale = cond_scale(w, o)
+    err = np.max(np.abs(g["I"] - o["trace_I"])) / scale
+    assert err < MIXED_BOUND, err
+    np.testing.assert_allclose(g["V"], o["trace_var"], rtol=1e-3)
+    exact = CF.exact(w)
+    assert abs(g["res"]["estimate"] - exact) < 5 * g["res"]["sigma"]
+
+
+def test_mixed_full_size_sampled(gpu_ctx_factory):
+    w = W.corner8()
+    ctx = gpu_ctx_factory(seed=w.seed, precision="mixed")
+    ctx.setup(w.fid, w.params, w.lo, w.hi, w.ncall, w.itmax)
+    pb = oracle.Problem(w.fid, w.params, w.lo, w.hi, w.ncall, seed=w.seed)
+    B = _adapted_grid(w, 200_000)
+    ctx.set_grid(B)
+    for c0, c1 in _ranges(pb.m, 20_000):
+        s_o, C_o, _, _ = pb.vsample(B, 3, True, c0, c1)
+        s_g, C_g = ctx.sample_range(3, True, c0, c1)
+        assert abs(s_g[0] - s_o[0]) / s_o[2] < MIXED_BOUND
+        np.testing.assert_allclose(C_g, C_o, rtol=1e-3, atol=1e-6 * C_o.max())
+    ctx.close()

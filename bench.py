@@ -248,6 +248,8 @@ def ours(args):
             dist.destroy_process_group()
         return 0
 
+    from paper_2202_01753_gb300 import peaks
+    pk = peaks.measure(local)
     props = torch.cuda.get_device_properties(local)
     sms = props.multi_processor_count
     avg_sample_ms = kt["sample_ms"] / max(kt["sample_launches"], 1)
@@ -286,6 +288,8 @@ def ours(args):
                 "call": "mcubes_integrate (host params/bounds/result), %d iterations" % K},
         "gpu_launches": kt["sample_launches"] + kt["refine_launches"],
         "clocks": clk,
+        "alu_peaks": {"ffma_tflops": 2 * pk["ffma_per_s"] / 1e12, "dfma_tflops": 2 * pk["dfma_per_s"] / 1e12,
+                      "how": "independent FMA chains on every thread of 8 blocks/SM, CUDA events"},
         "result": {"estimate": res["estimate"], "sigma": res["sigma"], "chi2_dof": res["chi2_dof"],
                    "e2e_estimate": r2["estimate"]},
     }

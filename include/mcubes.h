@@ -129,8 +129,8 @@ void mcubes_default_opts(mcubes_opts* opts);
 mcubes_status mcubes_create(mcubes_ctx** out, int device, const mcubes_opts* opts);
 
 /* As mcubes_create, but all work is enqueued on `cuda_stream` (a
- * cudaStream_t, e.g. the current PyTorch stream), which the caller keeps
- * alive until mcubes_destroy. */
+ * cudaStream_t, e.g. the current PyTorch stream; NULL means the legacy
+ * default stream), which the caller keeps alive until mcubes_destroy. */
 mcubes_status mcubes_create_on_stream(mcubes_ctx** out, int device, const mcubes_opts* opts,
                                       void* cuda_stream);
 

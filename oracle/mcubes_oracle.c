@@ -382,18 +382,62 @@ int oracle_vsample(const oracle_problem *pb, const double *B, uint32_t it, int a
 }
 
 /* ------------------------------------------------------------------------ */
-/* Adjust-Bin-Bounds (Alg. 2; Sec. 3 "bins of large contributions are made  */
-/* smaller"), following Lepage (1978): smooth the per-bin sums with their    */
-/* neighbours, normalise, compress with exponent alpha, then place new       */
-/* right edges so that every new bin holds an equal share of the compressed  */
-/* weight, the weight of an old bin being spread evenly over it.             */
-/* Returns 0 on success, 1 if the histogram of some axis was all zero (that  */
-/* axis is left unchanged), OR_ENONFINITE if it was not finite (unchanged).  */
+/* Double-double numbers (an unevaluated sum hi + lo; Dekker 1971, Knuth     */
+/* TAOCP vol. 2 Sec. 4.2.2): the cumulative bin weights below are carried   */
+/* in this form so that the quantile positions of the rebinning are exact   */
+/* to about 2^-104 of the total weight, whatever the order of addition.     */
+/* ------------------------------------------------------------------------ */
+typedef struct { double hi, lo; } ddnum;
+static ddnum dd_two_sum(double a, double b)
+{
+    double s = a + b, bb = s - a;
+    ddnum r = {s, (a - (s - bb)) + (b - bb)};
+    return r;
+}
+static ddnum dd_norm(double hi, double lo)
+{
+    double s = hi + lo;
+    ddnum r = {s, lo - (s - hi)};
+    return r;
+}
+static ddnum dd_add(ddnum a, ddnum b)
+{
+    ddnum s = dd_two_sum(a.hi, b.hi);
+    return dd_norm(s.hi, s.lo + a.lo + b.lo);
+}
+static ddnum dd_neg(ddnum a) { ddnum r = {-a.hi, -a.lo}; return r; }
+static ddnum dd_mul_d(ddnum a, double b)
+{
+    double p = a.hi * b;
+    double e = fma(a.hi, b, -p);
+    return dd_norm(p, e + a.lo * b);
+}
+static ddnum dd_div_d(ddnum a, double b)
+{
+    double q1 = a.hi / b;
+    ddnum r = dd_add(a, dd_neg(dd_mul_d((ddnum){q1, 0.0}, b)));
+    double q2 = (r.hi + r.lo) / b;
+    return dd_norm(q1, q2);
+}
+static int dd_ge(ddnum a, ddnum b) { return a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo); }
+
+/* ------------------------------------------------------------------------ */
+/* Adjust-Bin-Bounds (Alg. 2; Sec. 3: bins with large contributions are     */
+/* made smaller), following Lepage (1978): smooth the per-bin sums with     */
+/* their neighbours, normalise, compress with exponent alpha, then place    */
+/* new right edges so that every new bin holds an equal share of the        */
+/* compressed weight, the weight of an old bin being spread evenly over it. */
+/* Edge i (1..nb-1) lies where the cumulative weight reaches i/nb of the    */
+/* total: in the first bin k whose cumulative weight reaches that target,   */
+/* at fraction (target - weight before k) / w_k of its width.               */
+/* Returns 0 on success, 1 if the histogram of the axis was all zero (left  */
+/* unchanged), OR_ENONFINITE if it was not finite (left unchanged).         */
 /* ------------------------------------------------------------------------ */
 int oracle_rebin_axis(int nb, double alpha, const double *Cj, double *Bj)
 {
     double *sm = (double *)malloc(sizeof(double) * nb * 3);
-    if (!sm) return OR_ENOMEM;
+    ddnum *cum = (ddnum *)malloc(sizeof(ddnum) * (nb + 1));
+    if (!sm || !cum) { free(sm); free(cum); return OR_ENOMEM; }
     double *w = sm + nb, *newB = sm + 2 * nb;
     /* smoothing */
     if (nb == 1) sm[0] = Cj[0];
@@ -404,10 +448,9 @@ int oracle_rebin_axis(int nb, double alpha, const double *Cj, double *Bj)
     }
     double total = 0.0;
     for (int k = 0; k < nb; ++k) total += sm[k];
-    if (!isfinite(total)) { free(sm); return OR_ENONFINITE; }
-    if (total <= 0.0) { free(sm); return 1; }
+    if (!isfinite(total)) { free(sm); free(cum); return OR_ENONFINITE; }
+    if (total <= 0.0) { free(sm); free(cum); return 1; }
     /* normalisation and compression */
-    double wsum = 0.0;
     for (int k = 0; k < nb; ++k) {
         double r = sm[k] / total;
         double v;
@@ -415,19 +458,22 @@ int oracle_rebin_axis(int nb, double alpha, const double *Cj, double *Bj)
         else if (r == 1.0) v = 1.0;
         else v = pow((r - 1.0) / log(r), alpha);
         w[k] = v;
-        wsum += v;
     }
-    if (!(wsum > 0.0) || !isfinite(wsum)) { free(sm); return OR_ENONFINITE; }
+    /* cumulative weight: cum[k] = w_0 + ... + w_{k-1} */
+    cum[0].hi = 0.0;
+    cum[0].lo = 0.0;
+    for (int k = 0; k < nb; ++k) cum[k + 1] = dd_add(cum[k], (ddnum){w[k], 0.0});
+    ddnum wsum = cum[nb];
+    if (!(wsum.hi > 0.0) || !isfinite(wsum.hi)) { free(sm); free(cum); return OR_ENONFINITE; }
     /* equal-share rebinning along the cumulative weight */
-    double step = wsum / (double)nb;
     int k = 0;
-    double before = 0.0;          /* cumulative weight of bins 0..k-1 */
     for (int i = 1; i < nb; ++i) {
-        double target = (double)i * step;
-        while (k < nb - 1 && before + w[k] < target) { before += w[k]; ++k; }
+        ddnum target = dd_div_d(dd_mul_d(wsum, (double)i), (double)nb);
+        while (k < nb - 1 && !dd_ge(cum[k + 1], target)) ++k;
+        ddnum rem = dd_add(target, dd_neg(cum[k]));
         double left = k > 0 ? Bj[k - 1] : 0.0;
         double width = Bj[k] - left;
-        double frac = (target - before) / w[k];
+        double frac = (rem.hi + rem.lo) / w[k];
         if (frac > 1.0) frac = 1.0;
         if (frac < 0.0) frac = 0.0;
         newB[i - 1] = left + width * frac;
@@ -435,6 +481,7 @@ int oracle_rebin_axis(int nb, double alpha, const double *Cj, double *Bj)
     newB[nb - 1] = 1.0;
     memcpy(Bj, newB, sizeof(double) * nb);
     free(sm);
+    free(cum);
     return OR_OK;
 }
 

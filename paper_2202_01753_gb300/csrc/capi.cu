@@ -339,7 +339,8 @@ const char* mcubes_strerror(mcubes_status s)
 
 const char* mcubes_last_cuda_error(mcubes_ctx* c) { return c ? c->cuda_err : ""; }
 
-static mcubes_status create_impl(mcubes_ctx** out, int device, const mcubes_opts* opts, void* stream)
+static mcubes_status create_impl(mcubes_ctx** out, int device, const mcubes_opts* opts, bool given,
+                                 void* stream)
 {
     if (!out) return MCUBES_EINVAL;
     *out = nullptr;
@@ -356,8 +357,8 @@ static mcubes_status create_impl(mcubes_ctx** out, int device, const mcubes_opts
     cudaError_t e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) {
-        if (stream) {
-            c->stream = (cudaStream_t)stream;
+        if (given) {
+            c->stream = (cudaStream_t)stream;  // may be the legacy default stream (NULL)
         } else {
             e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
             c->own_stream = true;
@@ -376,13 +377,12 @@ static mcubes_status create_impl(mcubes_ctx** out, int device, const mcubes_opts
 
 mcubes_status mcubes_create(mcubes_ctx** out, int device, const mcubes_opts* opts)
 {
-    return create_impl(out, device, opts, nullptr);
+    return create_impl(out, device, opts, false, nullptr);
 }
 
 mcubes_status mcubes_create_on_stream(mcubes_ctx** out, int device, const mcubes_opts* opts, void* stream)
 {
-    if (!stream) return MCUBES_EINVAL;
-    return create_impl(out, device, opts, stream);
+    return create_impl(out, device, opts, true, stream);
 }
 
 mcubes_status mcubes_set_opts(mcubes_ctx* c, const mcubes_opts* o)

@@ -35,41 +35,97 @@ __device__ double block_sum(double v, double* scratch)
     return out;
 }
 
-// Inclusive prefix sum of v[0..n) in place (n <= kNbMax), fixed order:
-// each thread scans kPerThread consecutive values, then the thread totals are
-// scanned by warp shuffles and across warps.
-__device__ void block_inclusive_scan(double* v, int n, double* scratch)
+// Double-double arithmetic (value = hi + lo, |lo| <= ulp(hi)/2): error-free
+// TwoSum (Knuth) and an FMA-based exact product (Dekker).  The cumulative bin
+// weights of the rebinning are kept in this form so that the quantile edges
+// do not depend on the order in which the scan adds the weights.
+struct DD {
+    double hi, lo;
+};
+
+__device__ __forceinline__ DD dd_two_sum(double a, double b)
+{
+    const double s = __dadd_rn(a, b);
+    const double bb = __dsub_rn(s, a);
+    return DD{s, __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb))};
+}
+
+__device__ __forceinline__ DD dd_renorm(double hi, double lo)
+{
+    const double s = __dadd_rn(hi, lo);
+    return DD{s, __dsub_rn(lo, __dsub_rn(s, hi))};
+}
+
+__device__ __forceinline__ DD dd_add(DD a, DD b)
+{
+    const DD t = dd_two_sum(a.hi, b.hi);
+    return dd_renorm(t.hi, __dadd_rn(__dadd_rn(t.lo, a.lo), b.lo));
+}
+
+__device__ __forceinline__ DD dd_scale(DD a, double b)
+{
+    const double p = __dmul_rn(a.hi, b);
+    const double e = __fma_rn(a.hi, b, -p);
+    return dd_renorm(p, __fma_rn(a.lo, b, e));
+}
+
+__device__ __forceinline__ DD dd_div(DD a, double b)
+{
+    const double q1 = __ddiv_rn(a.hi, b);
+    const DD r = dd_add(a, dd_scale(DD{-q1, 0.0}, b));
+    return dd_renorm(q1, __ddiv_rn(__dadd_rn(r.hi, r.lo), b));
+}
+
+__device__ __forceinline__ bool dd_ge(DD a, DD b) { return a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo); }
+
+__device__ __forceinline__ DD dd_shfl_up(DD v, int off)
+{
+    return DD{__shfl_up_sync(0xffffffffu, v.hi, off), __shfl_up_sync(0xffffffffu, v.lo, off)};
+}
+
+// Inclusive double-double prefix sum of w[0..n) into (chi, clo), fixed
+// order: each thread adds kPerThread consecutive values, the thread totals
+// are scanned by warp shuffles and then across warps.
+__device__ void dd_inclusive_scan(const double* w, double* chi, double* clo, int n, DD* wtot)
 {
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int begin = t * kPerThread;
-    double local = 0.0;
+    DD local{0.0, 0.0};
+    DD mine[kPerThread];
     for (int i = 0; i < kPerThread; ++i) {
         const int k = begin + i;
-        if (k < n) { local += v[k]; v[k] = local; }
+        if (k < n) local = dd_add(local, DD{w[k], 0.0});
+        mine[i] = local;
     }
-    double incl = local;
+    DD incl = local;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-        const double o = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += o;
+        const DD o = dd_shfl_up(incl, off);
+        if (lane >= off) incl = dd_add(o, incl);
     }
     __syncthreads();
-    if (lane == 31) scratch[warp] = incl;
+    if (lane == 31) wtot[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        double w = lane < kWarps ? scratch[lane] : 0.0;
+        DD v = lane < kWarps ? wtot[lane] : DD{0.0, 0.0};
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
-            const double o = __shfl_up_sync(0xffffffffu, w, off);
-            if (lane >= off) w += o;
+            const DD o = dd_shfl_up(v, off);
+            if (lane >= off) v = dd_add(o, v);
         }
-        if (lane < kWarps) scratch[lane] = w;  // inclusive warp totals
+        if (lane < kWarps) wtot[lane] = v;  // inclusive warp totals
     }
     __syncthreads();
-    const double offset = (incl - local) + (warp > 0 ? scratch[warp - 1] : 0.0);
+    // exclusive prefix of this thread = (incl - local) within the warp + earlier warps
+    DD before = dd_add(incl, DD{-local.hi, -local.lo});
+    if (warp > 0) before = dd_add(wtot[warp - 1], before);
     for (int i = 0; i < kPerThread; ++i) {
         const int k = begin + i;
-        if (k < n) v[k] += offset;
+        if (k < n) {
+            const DD c = dd_add(before, mine[i]);
+            chi[k] = c.hi;
+            clo[k] = c.lo;
+        }
     }
     __syncthreads();
 }
@@ -147,12 +203,16 @@ __device__ void finalize_block(const RefineArgs& a, double* scratch)
 // smooth the bin sums with their neighbours, normalise, compress with
 // ((r - 1) / ln r)^alpha, then place the new right edges where the
 // cumulative compressed weight reaches i / nb of its total, the weight of an
-// old bin being spread evenly over it.
+// old bin being spread evenly over it.  The cumulative weight and the
+// targets are double-double, so an edge is exact to about 2^-104 of the total
+// weight and the new bin widths keep full double precision.
 __device__ void rebin_block(const RefineArgs& a, int ax, double* scratch)
 {
     __shared__ double sC[kNbMax];
     __shared__ double sW[kNbMax];
     __shared__ double sB[kNbMax];
+    __shared__ double sLo[kNbMax];
+    __shared__ DD wtot[kWarps];
     const int nb = a.nb, d = a.d;
     const size_t stride = (size_t)d * nb;
     for (int k = threadIdx.x; k < nb; k += blockDim.x) {
@@ -199,33 +259,33 @@ __device__ void rebin_block(const RefineArgs& a, int ax, double* scratch)
         else if (r == 1.0) w = 1.0;
         else w = pow((r - 1.0) / log(r), a.alpha);
         sW[k] = w;
-        sC[k] = w;
     }
     __syncthreads();
-    block_inclusive_scan(sC, nb, scratch);  // sC = cumulative weight through bin k
-    const double wsum = sC[nb - 1];
-    if (!(wsum > 0.0) || !isfinite(wsum)) {
+    // sC, sLo = cumulative weight through bin k (double-double)
+    dd_inclusive_scan(sW, sC, sLo, nb, wtot);
+    const DD wsum{sC[nb - 1], sLo[nb - 1]};
+    if (!(wsum.hi > 0.0) || !isfinite(wsum.hi)) {
         if (threadIdx.x == 0) {
             a.st->error = MCUBES_ENONFINITE;
             a.st->done = 1;
         }
         return;
     }
-    const double step = wsum / (double)nb;
     double* out = a.grid + (size_t)ax * nb;
     for (int i = 1 + threadIdx.x; i < nb; i += blockDim.x) {
-        const double target = (double)i * step;
-        // smallest k with cumulative weight through k >= target (nb-1 if none)
+        const DD target = dd_div(dd_scale(wsum, (double)i), (double)nb);
+        // first bin k whose cumulative weight through k reaches the target
         int lo = 0, hi = nb - 1;
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
-            if (sC[mid] >= target) hi = mid; else lo = mid + 1;
+            if (dd_ge(DD{sC[mid], sLo[mid]}, target)) hi = mid; else lo = mid + 1;
         }
         const int k = lo;
-        const double before = k > 0 ? sC[k - 1] : 0.0;
+        const DD before = k > 0 ? DD{sC[k - 1], sLo[k - 1]} : DD{0.0, 0.0};
+        const DD rem = dd_add(target, DD{-before.hi, -before.lo});
         const double left = k > 0 ? sB[k - 1] : 0.0;
         const double width = sB[k] - left;
-        double frac = (target - before) / sW[k];
+        double frac = (rem.hi + rem.lo) / sW[k];
         frac = fmin(fmax(frac, 0.0), 1.0);
         out[i - 1] = left + width * frac;
     }

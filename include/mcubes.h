@@ -193,11 +193,14 @@ mcubes_status mcubes_result_get(mcubes_ctx* ctx, mcubes_result* out);
  * of `cap` entries); *n receives the number of iterations recorded. */
 mcubes_status mcubes_trace_get(mcubes_ctx* ctx, double* I_it, double* var_it, int cap, int* n);
 
-/* Waits, then copies the current bin grid ([d][nb] right edges, host). */
+/* Waits, then copies the current bin grid ([d][nb] right edges, host).  The
+ * library keeps every edge as a double-double number (so that narrow bins
+ * keep their width to full precision); this returns the rounded edges. */
 mcubes_status mcubes_grid_get(mcubes_ctx* ctx, double* B, long long count);
 
 /* Replaces the current bin grid ([d][nb], host): every axis must have
- * strictly increasing edges in (0, 1] ending at 1. Errors: EINVAL, ESTATE. */
+ * strictly increasing edges in (0, 1] ending at 1; the edges are taken as
+ * exact (zero low parts). Errors: EINVAL, ESTATE. */
 mcubes_status mcubes_grid_set(mcubes_ctx* ctx, const double* B, long long count);
 
 /* Waits, then copies the per-bin sums of f^2 ([d][nb], host) of the last

@@ -65,16 +65,16 @@ def _lib():
                                               ctypes.c_uint32, ctypes.c_int, u32p]
             h.oracle_geometry.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                                           i64p, i64p, i64p]
-            h.oracle_init_grid.argtypes = [ctypes.c_int, ctypes.c_int, dp]
+            h.oracle_init_grid.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
             h.oracle_bin_of.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_int), dp]
             h.oracle_nparams.argtypes = [ctypes.c_int, ctypes.c_int]
             h.oracle_integrand.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp]
             h.oracle_integrand.restype = ctypes.c_double
-            h.oracle_vsample.argtypes = [ctypes.c_void_p, dp, ctypes.c_uint32, ctypes.c_int,
+            h.oracle_vsample.argtypes = [ctypes.c_void_p, dp, dp, ctypes.c_uint32, ctypes.c_int,
                                          ctypes.c_uint64, ctypes.c_uint64, dp, dp,
                                          ctypes.POINTER(ctypes.c_uint64)]
-            h.oracle_rebin_axis.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp]
+            h.oracle_rebin_axis.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp, dp]
             h.oracle_weighted.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double,
                                           dp, dp, dp, ctypes.POINTER(ctypes.c_int)]
             h.oracle_integrate.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp, dp, ctypes.c_int64,
@@ -131,11 +131,13 @@ def geometry(d, ncall, g_override=0, nb=500):
     return g.value, m.value, p.value
 
 
-def init_grid(d, nb):
-    """Init-Bins of Alg. 2: [d][nb] right edges of equal bins."""
+def init_grid(d, nb, with_lo=False):
+    """Init-Bins of Alg. 2: [d][nb] right edges of equal bins (and, with
+    with_lo, the low parts of their double-double values)."""
     B = np.zeros(d * nb)
-    _lib().oracle_init_grid(d, nb, _dp(B))
-    return B.reshape(d, nb)
+    L = np.zeros(d * nb)
+    _lib().oracle_init_grid(d, nb, _dp(B), _dp(L))
+    return (B.reshape(d, nb), L.reshape(d, nb)) if with_lo else B.reshape(d, nb)
 
 
 def bin_of(c, w, g, nb):
@@ -177,7 +179,7 @@ class Problem:
     def n_samples(self):
         return self.m * self.p
 
-    def vsample(self, B, it, adjust, cube_begin=0, cube_end=None, hits=False):
+    def vsample(self, B, it, adjust, cube_begin=0, cube_end=None, hits=False, Blo=None):
         """One V-Sample pass (Alg. 3) over a cube range.
 
         Returns (sums, C, H): sums = [sum of cube means, sum of cube mean
@@ -186,10 +188,11 @@ class Problem:
         """
         cube_end = self.m if cube_end is None else cube_end
         B = _f64(B).reshape(-1)
+        L = None if Blo is None else _f64(Blo).reshape(-1)
         sums = np.zeros(3)
         C = np.zeros(self.d * self.nb) if adjust else None
         H = np.zeros(self.d * self.nb, dtype=np.uint64) if (adjust and hits) else None
-        st = _lib().oracle_vsample(ctypes.byref(self._c), _dp(B), it, int(adjust), cube_begin, cube_end,
+        st = _lib().oracle_vsample(ctypes.byref(self._c), _dp(B), _dp(L), it, int(adjust), cube_begin, cube_end,
                                    _dp(sums), _dp(C),
                                    H.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)) if H is not None else None)
         if st not in (OK, ENONFINITE):
@@ -198,12 +201,14 @@ class Problem:
                 None if H is None else H.reshape(self.d, self.nb), st)
 
 
-def rebin_axis(Cj, Bj, alpha=1.5):
-    """Adjust-Bin-Bounds of one axis (Alg. 2; Lepage 1978). Returns (status, new edges)."""
+def rebin_axis(Cj, Bj, alpha=1.5, Blo=None, with_lo=False):
+    """Adjust-Bin-Bounds of one axis (Alg. 2; Lepage 1978). Returns (status,
+    new edges) or, with with_lo, (status, new edges, their low parts)."""
     C = _f64(Cj).copy()
     B = _f64(Bj).copy()
-    st = _lib().oracle_rebin_axis(len(B), alpha, _dp(C), _dp(B))
-    return st, B
+    L = np.zeros_like(B) if Blo is None else _f64(Blo).copy()
+    st = _lib().oracle_rebin_axis(len(B), alpha, _dp(C), _dp(B), _dp(L))
+    return (st, B, L) if with_lo else (st, B)
 
 
 def weighted(I_it, var_it, rel_tol=0.0, abs_tol=0.0):

@@ -53,6 +53,49 @@
 #define OR_F_COSMO6 7
 
 /* ------------------------------------------------------------------------ */
+/* Double-double numbers (an unevaluated sum hi + lo; Dekker 1971, Knuth     */
+/* TAOCP vol. 2 Sec. 4.2.2).  Grid edges are kept in this form so that a    */
+/* narrow bin's width, the difference of two edges near the same value,    */
+/* keeps full relative precision (the Jacobian is a product of widths);    */
+/* the cumulative bin weights of the rebinning are kept in it so that the   */
+/* quantile edges are exact to about 2^-104 of the total weight, whatever   */
+/* the order of addition.                                                   */
+/* ------------------------------------------------------------------------ */
+typedef struct { double hi, lo; } ddnum;
+static ddnum dd_two_sum(double a, double b)
+{
+    double s = a + b, bb = s - a;
+    ddnum r = {s, (a - (s - bb)) + (b - bb)};
+    return r;
+}
+static ddnum dd_norm(double hi, double lo)
+{
+    double s = hi + lo;
+    ddnum r = {s, lo - (s - hi)};
+    return r;
+}
+static ddnum dd_add(ddnum a, ddnum b)
+{
+    ddnum s = dd_two_sum(a.hi, b.hi);
+    return dd_norm(s.hi, s.lo + a.lo + b.lo);
+}
+static ddnum dd_neg(ddnum a) { ddnum r = {-a.hi, -a.lo}; return r; }
+static ddnum dd_mul_d(ddnum a, double b)
+{
+    double p = a.hi * b;
+    double e = fma(a.hi, b, -p);
+    return dd_norm(p, e + a.lo * b);
+}
+static ddnum dd_div_d(ddnum a, double b)
+{
+    double q1 = a.hi / b;
+    ddnum r = dd_add(a, dd_neg(dd_mul_d((ddnum){q1, 0.0}, b)));
+    double q2 = (r.hi + r.lo) / b;
+    return dd_norm(q1, q2);
+}
+static int dd_ge(ddnum a, ddnum b) { return a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo); }
+
+/* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon et al., SC'11, Sec. 3.3 and Table 2).               */
 /* Alg. 3 seeds a generator per thread but names none;                      */
 /* this counter-based one makes every sample reproducible from    */
@@ -150,11 +193,17 @@ int oracle_geometry(int d, int64_t ncall, int64_t g_override, int nb,
 /* Init-Bins (Alg. 2; Sec. 4): every axis starts as nb bins of equal width, */
 /* kept as their right edges.  B is [d][nb], in unit coordinates.           */
 /* ------------------------------------------------------------------------ */
-void oracle_init_grid(int d, int nb, double *B)
+void oracle_init_grid(int d, int nb, double *B, double *Blo)
 {
+    /* right edge (k+1)/nb as hi + lo: hi rounded, lo the rounded remainder */
     for (int j = 0; j < d; ++j) {
-        for (int k = 0; k < nb; ++k) B[j * nb + k] = (double)(k + 1) / (double)nb;
-        B[j * nb + nb - 1] = 1.0;
+        for (int k = 0; k < nb; ++k) {
+            double hi = (double)(k + 1) / (double)nb;
+            double rem = fma(-hi, (double)nb, (double)(k + 1)); /* exact */
+            if (k == nb - 1) { hi = 1.0; rem = 0.0; }
+            B[j * nb + k] = hi;
+            if (Blo) Blo[j * nb + k] = rem / (double)nb;
+        }
     }
 }
 
@@ -177,13 +226,16 @@ void oracle_bin_of(uint32_t c, uint32_t w, int64_t g, int nb, int *k_out, double
 
 /* Lepage's map through the bin grid of one axis: bin k spans
  * [B[k-1], B[k]] (B[-1] = 0); x = lo + (hi-lo)*(left + width*phi) and the
- * axis contributes (hi-lo)*nb*width to the Jacobian. */
-static void map_axis(const double *Bj, int nb, double lo, double hi, int k, double phi,
-                     double *x, double *jac)
+ * axis contributes (hi-lo)*nb*width to the Jacobian.  The edges are
+ * double-double (Blo may be NULL: zero low parts). */
+static void map_axis(const double *Bj, const double *Blj, int nb, double lo, double hi, int k,
+                     double phi, double *x, double *jac)
 {
-    double left = k > 0 ? Bj[k - 1] : 0.0;
-    double width = Bj[k] - left;
-    *x = lo + (hi - lo) * (left + width * phi);
+    ddnum left = {0.0, 0.0}, right = {Bj[k], Blj ? Blj[k] : 0.0};
+    if (k > 0) { left.hi = Bj[k - 1]; left.lo = Blj ? Blj[k - 1] : 0.0; }
+    ddnum wd = dd_add(right, dd_neg(left));
+    double width = wd.hi + wd.lo;
+    *x = lo + (hi - lo) * (left.hi + width * phi);
     *jac = (hi - lo) * (double)nb * width;
 }
 
@@ -303,7 +355,8 @@ static double ks_val(const ksum *a) { return a->s + a->c; }
 /* C[j][k_j] for every axis j (Alg. 3: the bin contribution is the square   */
 /* of the sample's estimate; the printed index C[b[j]] drops the axis and   */
 /* is read as C[j][b[j]], one histogram per axis), and count hits H[j][k_j].*/
-/* C and H are [d][nb], added to (not cleared); either may be NULL.          */
+/* C and H are [d][nb], added to (not cleared); either may be NULL.  B/Blo */
+/* are the grid's double-double right edges ([d][nb]; Blo may be NULL).     */
 /* Returns OR_ENONFINITE if any F is not finite.                             */
 /* ------------------------------------------------------------------------ */
 typedef struct {
@@ -315,7 +368,7 @@ typedef struct {
     uint64_t seed;
 } oracle_problem;
 
-int oracle_vsample(const oracle_problem *pb, const double *B, uint32_t it, int adjust,
+int oracle_vsample(const oracle_problem *pb, const double *B, const double *Blo, uint32_t it, int adjust,
                    uint64_t cube_begin, uint64_t cube_end, double *sums_out,
                    double *C, uint64_t *H)
 {
@@ -345,7 +398,8 @@ int oracle_vsample(const oracle_problem *pb, const double *B, uint32_t it, int a
             for (int j = 0; j < d; ++j) {
                 double phi, jj;
                 oracle_bin_of(digit[j], words[j], pb->g, nb, &kbin[j], &phi);
-                map_axis(B + (size_t)j * nb, nb, pb->lo[j], pb->hi[j], kbin[j], phi, &x[j], &jj);
+                map_axis(B + (size_t)j * nb, Blo ? Blo + (size_t)j * nb : NULL, nb, pb->lo[j], pb->hi[j],
+                         kbin[j], phi, &x[j], &jj);
                 jac *= jj;
             }
             double v = oracle_integrand(pb->id, pb->params, d, x) * jac;
@@ -382,46 +436,6 @@ int oracle_vsample(const oracle_problem *pb, const double *B, uint32_t it, int a
 }
 
 /* ------------------------------------------------------------------------ */
-/* Double-double numbers (an unevaluated sum hi + lo; Dekker 1971, Knuth     */
-/* TAOCP vol. 2 Sec. 4.2.2): the cumulative bin weights below are carried   */
-/* in this form so that the quantile positions of the rebinning are exact   */
-/* to about 2^-104 of the total weight, whatever the order of addition.     */
-/* ------------------------------------------------------------------------ */
-typedef struct { double hi, lo; } ddnum;
-static ddnum dd_two_sum(double a, double b)
-{
-    double s = a + b, bb = s - a;
-    ddnum r = {s, (a - (s - bb)) + (b - bb)};
-    return r;
-}
-static ddnum dd_norm(double hi, double lo)
-{
-    double s = hi + lo;
-    ddnum r = {s, lo - (s - hi)};
-    return r;
-}
-static ddnum dd_add(ddnum a, ddnum b)
-{
-    ddnum s = dd_two_sum(a.hi, b.hi);
-    return dd_norm(s.hi, s.lo + a.lo + b.lo);
-}
-static ddnum dd_neg(ddnum a) { ddnum r = {-a.hi, -a.lo}; return r; }
-static ddnum dd_mul_d(ddnum a, double b)
-{
-    double p = a.hi * b;
-    double e = fma(a.hi, b, -p);
-    return dd_norm(p, e + a.lo * b);
-}
-static ddnum dd_div_d(ddnum a, double b)
-{
-    double q1 = a.hi / b;
-    ddnum r = dd_add(a, dd_neg(dd_mul_d((ddnum){q1, 0.0}, b)));
-    double q2 = (r.hi + r.lo) / b;
-    return dd_norm(q1, q2);
-}
-static int dd_ge(ddnum a, ddnum b) { return a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo); }
-
-/* ------------------------------------------------------------------------ */
 /* Adjust-Bin-Bounds (Alg. 2; Sec. 3: bins with large contributions are     */
 /* made smaller), following Lepage (1978): smooth the per-bin sums with     */
 /* their neighbours, normalise, compress with exponent alpha, then place    */
@@ -430,15 +444,16 @@ static int dd_ge(ddnum a, ddnum b) { return a.hi > b.hi || (a.hi == b.hi && a.lo
 /* Edge i (1..nb-1) lies where the cumulative weight reaches i/nb of the    */
 /* total: in the first bin k whose cumulative weight reaches that target,   */
 /* at fraction (target - weight before k) / w_k of its width.               */
-/* Returns 0 on success, 1 if the histogram of the axis was all zero (left  */
+/* The edges Bj/Blj ([nb], double-double) are updated in place.  Returns 0 */
+/* on success, 1 if the histogram of the axis was all zero (left            */
 /* unchanged), OR_ENONFINITE if it was not finite (left unchanged).         */
 /* ------------------------------------------------------------------------ */
-int oracle_rebin_axis(int nb, double alpha, const double *Cj, double *Bj)
+int oracle_rebin_axis(int nb, double alpha, const double *Cj, double *Bj, double *Blj)
 {
-    double *sm = (double *)malloc(sizeof(double) * nb * 3);
+    double *sm = (double *)malloc(sizeof(double) * nb * 4);
     ddnum *cum = (ddnum *)malloc(sizeof(ddnum) * (nb + 1));
     if (!sm || !cum) { free(sm); free(cum); return OR_ENOMEM; }
-    double *w = sm + nb, *newB = sm + 2 * nb;
+    double *w = sm + nb, *newB = sm + 2 * nb, *newL = sm + 3 * nb;
     /* smoothing */
     if (nb == 1) sm[0] = Cj[0];
     else {
@@ -471,15 +486,20 @@ int oracle_rebin_axis(int nb, double alpha, const double *Cj, double *Bj)
         ddnum target = dd_div_d(dd_mul_d(wsum, (double)i), (double)nb);
         while (k < nb - 1 && !dd_ge(cum[k + 1], target)) ++k;
         ddnum rem = dd_add(target, dd_neg(cum[k]));
-        double left = k > 0 ? Bj[k - 1] : 0.0;
-        double width = Bj[k] - left;
+        ddnum left = {0.0, 0.0}, right = {Bj[k], Blj[k]};
+        if (k > 0) { left.hi = Bj[k - 1]; left.lo = Blj[k - 1]; }
+        ddnum width = dd_add(right, dd_neg(left));
         double frac = (rem.hi + rem.lo) / w[k];
         if (frac > 1.0) frac = 1.0;
         if (frac < 0.0) frac = 0.0;
-        newB[i - 1] = left + width * frac;
+        ddnum e = dd_add(left, dd_mul_d(width, frac));
+        newB[i - 1] = e.hi;
+        newL[i - 1] = e.lo;
     }
     newB[nb - 1] = 1.0;
+    newL[nb - 1] = 0.0;
     memcpy(Bj, newB, sizeof(double) * nb);
+    memcpy(Blj, newL, sizeof(double) * nb);
     free(sm);
     free(cum);
     return OR_OK;
@@ -546,11 +566,12 @@ int oracle_integrate(int id, const double *params, int d, const double *lo, cons
     if (st) return st;
     if (geom_out) { geom_out[0] = g; geom_out[1] = m; geom_out[2] = p; }
     double *B = (double *)malloc(sizeof(double) * d * nb);
+    double *Blo = (double *)malloc(sizeof(double) * d * nb);
     double *C = (double *)malloc(sizeof(double) * d * nb);
     double *hI = (double *)malloc(sizeof(double) * itmax);
     double *hV = (double *)malloc(sizeof(double) * itmax);
-    if (!B || !C || !hI || !hV) { free(B); free(C); free(hI); free(hV); return OR_ENOMEM; }
-    oracle_init_grid(d, nb, B);
+    if (!B || !Blo || !C || !hI || !hV) { free(B); free(Blo); free(C); free(hI); free(hV); return OR_ENOMEM; }
+    oracle_init_grid(d, nb, B, Blo);
     oracle_problem pb = {id, params, d, nb, lo, hi, g, m, p, seed};
     double est = 0, sig = 0, chi2 = 0;
     int conv = 0, n = 0;
@@ -559,7 +580,7 @@ int oracle_integrate(int id, const double *params, int d, const double *lo, cons
         int adjust = it < ita;
         double sums[3];
         if (adjust) memset(C, 0, sizeof(double) * d * nb);
-        int s = oracle_vsample(&pb, B, (uint32_t)it, adjust, 0, (uint64_t)m, sums, adjust ? C : NULL, NULL);
+        int s = oracle_vsample(&pb, B, Blo, (uint32_t)it, adjust, 0, (uint64_t)m, sums, adjust ? C : NULL, NULL);
         double I_it = sums[0] / (double)m;
         double V_it = sums[1] / ((double)m * (double)m);
         hI[n] = I_it;
@@ -572,7 +593,7 @@ int oracle_integrate(int id, const double *params, int d, const double *lo, cons
         if (adjust) {
             if (C_out) memcpy(C_out, C, sizeof(double) * d * nb);
             for (int j = 0; j < d; ++j) {
-                int r = oracle_rebin_axis(nb, alpha, C + (size_t)j * nb, B + (size_t)j * nb);
+                int r = oracle_rebin_axis(nb, alpha, C + (size_t)j * nb, B + (size_t)j * nb, Blo + (size_t)j * nb);
                 if (r == OR_ENONFINITE) st = OR_ENONFINITE;
             }
             if (st) break;
@@ -583,7 +604,7 @@ int oracle_integrate(int id, const double *params, int d, const double *lo, cons
     if (iters_out) *iters_out = n;
     if (conv_out) *conv_out = conv;
     if (B_out) memcpy(B_out, B, sizeof(double) * d * nb);
-    free(B); free(C); free(hI); free(hV);
+    free(B); free(Blo); free(C); free(hI); free(hV);
     if (st) return st;
     return conv ? OR_OK : OR_ENOCONV;
 }

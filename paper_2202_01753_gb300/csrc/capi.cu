@@ -474,7 +474,7 @@ mcubes_status mcubes_setup(mcubes_ctx* c, int id, const double* params, int npar
 
     // device buffers
     const size_t hist_elem = c->mixed ? sizeof(float) : sizeof(double);
-    MC_CHECK(c, c->grid.reserve(sizeof(double) * d * nb));
+    MC_CHECK(c, c->grid.reserve(2 * sizeof(double) * d * nb));  // high parts, then low parts
     MC_CHECK(c, c->hist.reserve(sizeof(double) * d * nb));
     MC_CHECK(c, c->part.reserve(sizeof(double) * 3 * grid_max));
     MC_CHECK(c, c->part_hist.reserve(hist_elem * (size_t)grid_max * d * nb));
@@ -483,6 +483,7 @@ mcubes_status mcubes_setup(mcubes_ctx* c, int id, const double* params, int npar
     VsArgs& a = c->vs;
     std::memset(&a, 0, sizeof a);
     a.grid = (const double*)c->grid.ptr;
+    a.grid_lo = (const double*)c->grid.ptr + (size_t)d * nb;
     a.part = (double*)c->part.ptr;
     a.part_hist = c->part_hist.ptr;
     a.st = (DevState*)c->state.ptr;
@@ -510,6 +511,7 @@ mcubes_status mcubes_setup(mcubes_ctx* c, int id, const double* params, int npar
     RefineArgs& r = c->rf;
     std::memset(&r, 0, sizeof r);
     r.grid = (double*)c->grid.ptr;
+    r.grid_lo = (double*)c->grid.ptr + (size_t)d * nb;
     r.hist = (double*)c->hist.ptr;
     r.part = (const double*)c->part.ptr;
     r.part_hist = c->part_hist.ptr;
@@ -526,7 +528,7 @@ mcubes_status mcubes_setup(mcubes_ctx* c, int id, const double* params, int npar
     hst.rel_tol = rel_tol;
     hst.abs_tol = abs_tol;
     MC_CHECK(c, cudaMemcpyAsync(c->state.ptr, &hst, offsetof(DevState, hist_I), cudaMemcpyHostToDevice, c->stream));
-    MC_CHECK(c, launch_init_grid((double*)c->grid.ptr, d, nb, c->stream));
+    MC_CHECK(c, launch_init_grid((double*)c->grid.ptr, (double*)c->grid.ptr + (size_t)d * nb, d, nb, c->stream));
     MC_CHECK(c, cudaMemsetAsync(c->hist.ptr, 0, sizeof(double) * d * nb, c->stream));
     MC_CHECK(c, cudaStreamSynchronize(c->stream));  // hst lives on this stack frame
     c->it_enqueued = 0;
@@ -655,6 +657,7 @@ mcubes_status mcubes_grid_set(mcubes_ctx* c, const double* B, long long count)
     }
     MC_CHECK(c, cudaSetDevice(c->device));
     MC_CHECK(c, cudaMemcpyAsync(c->grid.ptr, B, sizeof(double) * count, cudaMemcpyHostToDevice, c->stream));
+    MC_CHECK(c, cudaMemsetAsync((double*)c->grid.ptr + count, 0, sizeof(double) * count, c->stream));
     MC_CHECK(c, cudaStreamSynchronize(c->stream));
     return MCUBES_OK;
 }

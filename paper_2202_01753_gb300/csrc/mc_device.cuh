@@ -10,6 +10,53 @@
 namespace mc {
 
 // ---------------------------------------------------------------------------
+// Double-double arithmetic (value = hi + lo, |lo| <= ulp(hi)/2): error-free
+// TwoSum (Knuth) and an FMA-based exact product (Dekker).  Grid edges are held
+// in this form so that a narrow bin's width (a difference of two nearly equal
+// edges, and a factor of the Jacobian) keeps full relative precision; the
+// rebinning's cumulative weights use it so that the quantile edges do not
+// depend on the order in which a scan adds the weights.
+// ---------------------------------------------------------------------------
+struct DD {
+    double hi, lo;
+};
+
+__device__ __forceinline__ DD dd_two_sum(double a, double b)
+{
+    const double s = __dadd_rn(a, b);
+    const double bb = __dsub_rn(s, a);
+    return DD{s, __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb))};
+}
+
+__device__ __forceinline__ DD dd_renorm(double hi, double lo)
+{
+    const double s = __dadd_rn(hi, lo);
+    return DD{s, __dsub_rn(lo, __dsub_rn(s, hi))};
+}
+
+__device__ __forceinline__ DD dd_add(DD a, DD b)
+{
+    const DD t = dd_two_sum(a.hi, b.hi);
+    return dd_renorm(t.hi, __dadd_rn(__dadd_rn(t.lo, a.lo), b.lo));
+}
+
+__device__ __forceinline__ DD dd_scale(DD a, double b)
+{
+    const double p = __dmul_rn(a.hi, b);
+    const double e = __fma_rn(a.hi, b, -p);
+    return dd_renorm(p, __fma_rn(a.lo, b, e));
+}
+
+__device__ __forceinline__ DD dd_div(DD a, double b)
+{
+    const double q1 = __ddiv_rn(a.hi, b);
+    const DD r = dd_add(a, dd_scale(DD{-q1, 0.0}, b));
+    return dd_renorm(q1, __ddiv_rn(__dadd_rn(r.hi, r.lo), b));
+}
+
+__device__ __forceinline__ bool dd_ge(DD a, DD b) { return a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo); }
+
+// ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
 // as 1, 2, 3", SC'11).  The round keys (key + r * Weyl increments) are
 // precomputed on the host and read from the kernel's constant bank.

@@ -45,7 +45,8 @@ struct FamParams {
 // __grid_constant__ kernel parameter: indices known at compile time become
 // constant-bank operands.
 struct VsArgs {
-    const double* grid;       // [d][nb] right edges, unit coordinates
+    const double* grid;       // [d][nb] right edges, unit coordinates (double-double: high parts)
+    const double* grid_lo;    // [d][nb] low parts
     double* part;             // [gridDim][3]: sum of cube means, of their variances, of |means|
     void* part_hist;          // [gridDim][d][nb] per-block sums of F^2 (double or float)
     DevState* st;             // iteration state; nullptr -> use it_fixed and always run
@@ -64,7 +65,8 @@ struct VsArgs {
 };
 
 struct RefineArgs {
-    double* grid;             // [d][nb], updated in place by the rebin blocks
+    double* grid;             // [d][nb] edge high parts, updated in place by the rebin blocks
+    double* grid_lo;          // [d][nb] edge low parts
     double* hist;             // [d][nb] reduced histogram (written for read-back)
     const double* part;       // [nblocks][3]
     const void* part_hist;    // [nblocks][d][nb]
@@ -84,6 +86,6 @@ cudaError_t launch_refine(const RefineArgs& a, cudaStream_t s);
 cudaError_t launch_reduce_range(const double* part, const void* part_hist, int hist_is_float,
                                 int nblocks, int d, int nb, int adjust, double* out_sums,
                                 double* out_hist, cudaStream_t s);
-cudaError_t launch_init_grid(double* grid, int d, int nb, cudaStream_t s);
+cudaError_t launch_init_grid(double* grid, double* grid_lo, int d, int nb, cudaStream_t s);
 
 }  // namespace mc

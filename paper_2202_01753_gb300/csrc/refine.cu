@@ -5,7 +5,7 @@
 // lets a whole iteration run without the host.
 #include <cmath>
 
-#include "mc_internal.h"
+#include "mc_device.cuh"
 
 namespace mc {
 
@@ -34,49 +34,6 @@ __device__ double block_sum(double v, double* scratch)
     __syncthreads();
     return out;
 }
-
-// Double-double arithmetic (value = hi + lo, |lo| <= ulp(hi)/2): error-free
-// TwoSum (Knuth) and an FMA-based exact product (Dekker).  The cumulative bin
-// weights of the rebinning are kept in this form so that the quantile edges
-// do not depend on the order in which the scan adds the weights.
-struct DD {
-    double hi, lo;
-};
-
-__device__ __forceinline__ DD dd_two_sum(double a, double b)
-{
-    const double s = __dadd_rn(a, b);
-    const double bb = __dsub_rn(s, a);
-    return DD{s, __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb))};
-}
-
-__device__ __forceinline__ DD dd_renorm(double hi, double lo)
-{
-    const double s = __dadd_rn(hi, lo);
-    return DD{s, __dsub_rn(lo, __dsub_rn(s, hi))};
-}
-
-__device__ __forceinline__ DD dd_add(DD a, DD b)
-{
-    const DD t = dd_two_sum(a.hi, b.hi);
-    return dd_renorm(t.hi, __dadd_rn(__dadd_rn(t.lo, a.lo), b.lo));
-}
-
-__device__ __forceinline__ DD dd_scale(DD a, double b)
-{
-    const double p = __dmul_rn(a.hi, b);
-    const double e = __fma_rn(a.hi, b, -p);
-    return dd_renorm(p, __fma_rn(a.lo, b, e));
-}
-
-__device__ __forceinline__ DD dd_div(DD a, double b)
-{
-    const double q1 = __ddiv_rn(a.hi, b);
-    const DD r = dd_add(a, dd_scale(DD{-q1, 0.0}, b));
-    return dd_renorm(q1, __ddiv_rn(__dadd_rn(r.hi, r.lo), b));
-}
-
-__device__ __forceinline__ bool dd_ge(DD a, DD b) { return a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo); }
 
 __device__ __forceinline__ DD dd_shfl_up(DD v, int off)
 {
@@ -212,6 +169,7 @@ __device__ void rebin_block(const RefineArgs& a, int ax, double* scratch)
     __shared__ double sW[kNbMax];
     __shared__ double sB[kNbMax];
     __shared__ double sLo[kNbMax];
+    __shared__ double sBlo[kNbMax];
     __shared__ DD wtot[kWarps];
     const int nb = a.nb, d = a.d;
     const size_t stride = (size_t)d * nb;
@@ -227,6 +185,7 @@ __device__ void rebin_block(const RefineArgs& a, int ax, double* scratch)
         sC[k] = acc;
         a.hist[(size_t)ax * nb + k] = acc;
         sB[k] = a.grid[(size_t)ax * nb + k];
+        sBlo[k] = a.grid_lo[(size_t)ax * nb + k];
     }
     __syncthreads();
     double part = 0.0;
@@ -272,6 +231,7 @@ __device__ void rebin_block(const RefineArgs& a, int ax, double* scratch)
         return;
     }
     double* out = a.grid + (size_t)ax * nb;
+    double* out_lo = a.grid_lo + (size_t)ax * nb;
     for (int i = 1 + threadIdx.x; i < nb; i += blockDim.x) {
         const DD target = dd_div(dd_scale(wsum, (double)i), (double)nb);
         // first bin k whose cumulative weight through k reaches the target
@@ -283,13 +243,18 @@ __device__ void rebin_block(const RefineArgs& a, int ax, double* scratch)
         const int k = lo;
         const DD before = k > 0 ? DD{sC[k - 1], sLo[k - 1]} : DD{0.0, 0.0};
         const DD rem = dd_add(target, DD{-before.hi, -before.lo});
-        const double left = k > 0 ? sB[k - 1] : 0.0;
-        const double width = sB[k] - left;
+        const DD left = k > 0 ? DD{sB[k - 1], sBlo[k - 1]} : DD{0.0, 0.0};
+        const DD width = dd_add(DD{sB[k], sBlo[k]}, DD{-left.hi, -left.lo});
         double frac = (rem.hi + rem.lo) / sW[k];
         frac = fmin(fmax(frac, 0.0), 1.0);
-        out[i - 1] = left + width * frac;
+        const DD e = dd_add(left, dd_scale(width, frac));
+        out[i - 1] = e.hi;
+        out_lo[i - 1] = e.lo;
     }
-    if (threadIdx.x == 0) out[nb - 1] = 1.0;
+    if (threadIdx.x == 0) {
+        out[nb - 1] = 1.0;
+        out_lo[nb - 1] = 0.0;
+    }
 }
 
 __global__ void __launch_bounds__(kRefineThreads) refine_kernel(const __grid_constant__ RefineArgs a)
@@ -334,13 +299,22 @@ reduce_range_kernel(const double* part, const void* part_hist, int hist_is_float
     }
 }
 
-// Init-Bins (Alg. 2): nb equal bins per axis, right edges (k+1)/nb, last = 1.
-__global__ void init_grid_kernel(double* grid, int d, int nb)
+// Init-Bins (Alg. 2): nb equal bins per axis, right edges (k+1)/nb held as
+// double-double (rounded value + rounded remainder), last edge exactly 1.
+__global__ void init_grid_kernel(double* grid, double* grid_lo, int d, int nb)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d * nb) return;
     const int k = i % nb;
-    grid[i] = (k == nb - 1) ? 1.0 : (double)(k + 1) / (double)nb;
+    if (k == nb - 1) {
+        grid[i] = 1.0;
+        grid_lo[i] = 0.0;
+        return;
+    }
+    const double hi = __ddiv_rn((double)(k + 1), (double)nb);
+    const double rem = __fma_rn(-hi, (double)nb, (double)(k + 1));  // exact
+    grid[i] = hi;
+    grid_lo[i] = __ddiv_rn(rem, (double)nb);
 }
 
 }  // namespace
@@ -362,10 +336,10 @@ cudaError_t launch_reduce_range(const double* part, const void* part_hist, int h
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_grid(double* grid, int d, int nb, cudaStream_t s)
+cudaError_t launch_init_grid(double* grid, double* grid_lo, int d, int nb, cudaStream_t s)
 {
     const int n = d * nb;
-    init_grid_kernel<<<(n + 255) / 256, 256, 0, s>>>(grid, d, nb);
+    init_grid_kernel<<<(n + 255) / 256, 256, 0, s>>>(grid, grid_lo, d, nb);
     return cudaGetLastError();
 }
 

@@ -104,10 +104,11 @@ vsample_kernel(const __grid_constant__ VsArgs a)
     HT* hist = reinterpret_cast<HT*>(smem + sizeof(Cell) * d * nb);
     for (uint32_t i = threadIdx.x; i < d * nb; i += blockDim.x) {
         const uint32_t j = i / nb, k = i - j * nb;
-        const double right = a.grid[i];
-        const double left = k ? a.grid[i - 1] : 0.0;
-        const double xl = a.lo[j] + a.scale[j] * left;
-        const double xw = a.scale[j] * (right - left);
+        const DD right{a.grid[i], a.grid_lo[i]};
+        const DD left = k ? DD{a.grid[i - 1], a.grid_lo[i - 1]} : DD{0.0, 0.0};
+        const DD wd = dd_add(right, DD{-left.hi, -left.lo});
+        const double xl = a.lo[j] + a.scale[j] * left.hi;
+        const double xw = a.scale[j] * (wd.hi + wd.lo);
         if constexpr (MIXED) cells[i] = make_float4((float)xl, (float)xw, (float)(xw * (double)nb), 0.0f);
         else cells[i] = make_double2(xl, xw);
         if constexpr (ADJ) hist[i] = HT(0);

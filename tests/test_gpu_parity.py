@@ -79,13 +79,47 @@ def test_gauss3_full_config(gpu_ctx_factory):
 
 @pytest.mark.parametrize("name,d,ncall", [
     ("f1", 3, 60_000), ("f2", 4, 60_000), ("f3", 5, 60_000), ("f4", 3, 60_000),
-    ("f5", 2, 60_000), ("f6", 3, 60_000), ("fA", None, 80_000), ("fB", None, 200_000),
+    ("f5", 2, 60_000), ("f6", 3, 60_000), ("fA", None, 80_000), ("fB", None, 1_000_000),
 ])
 def test_paper_suite(gpu_ctx_factory, name, d, ncall):
     w = W.suite(name, d, ncall=ncall, itmax=5, seed=7)
     o = oracle_run(w)
     g = gpu_run(gpu_ctx_factory, w)
     assert_parity(w, o, g, vtol=1e-10 if w.fid == W.F_OSC else RTOL_V)
+
+
+def _oracle_trace_with_noise(w, noise, rng):
+    """The oracle's iteration loop with the histogram perturbed by relative
+    noise before every rebin (noise = 0: the plain loop)."""
+    pb = oracle.Problem(w.fid, w.params, w.lo, w.hi, w.ncall, nb=w.nb, seed=w.seed)
+    B, L = oracle.init_grid(pb.d, pb.nb, with_lo=True)
+    out = []
+    for it in range(w.itmax):
+        sums, C, _, _ = pb.vsample(B, it, True, Blo=L)
+        out.append(sums[0] / pb.m)
+        if noise:
+            C = C * (1 + noise * rng.standard_normal(C.shape))
+        for j in range(pb.d):
+            _, B[j], L[j] = oracle.rebin_axis(C[j], B[j], Blo=L[j], with_lo=True)
+    return np.array(out)
+
+
+def test_ill_conditioned_adaptation_within_measured_sensitivity(gpu_ctx_factory):
+    """f_B (9-d peak) with only 2e5 calls: each adjusting iteration amplifies
+    rounding-level differences in the histogram about six-fold, so after five
+    iterations the oracle itself is only good to ~1e-12 relative.  The
+    tolerance here is derived from that measured sensitivity: the GPU must
+    agree within 10x the spread the oracle shows under 1e-15 relative noise."""
+    w = W.suite("fB", None, ncall=200_000, itmax=5, seed=7)
+    base = _oracle_trace_with_noise(w, 0.0, None)
+    rng = np.random.default_rng(1)
+    spread = np.zeros(w.itmax)
+    for _ in range(4):
+        spread = np.maximum(spread, np.abs(_oracle_trace_with_noise(w, 1e-15, rng) - base))
+    g = gpu_run(gpu_ctx_factory, w)
+    tol = np.maximum(10 * spread, RTOL_I * np.abs(base))
+    assert np.all(np.abs(g["I"] - base) <= tol), (np.abs(g["I"] - base), tol)
+    assert spread[-1] > 100 * spread[1]   # the amplification this test is about
 
 
 def test_cosmo6_scaled(gpu_ctx_factory):

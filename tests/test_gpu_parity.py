@@ -49,7 +49,7 @@ def cond_scale(w, o):
     return max(np.max(np.abs(o["trace_I"])), sums[2] / min(pb.m, 2000))
 
 
-def assert_parity(w, o, g, vtol=RTOL_V):
+def assert_parity(w, o, g, vtol=RTOL_V, hist_tol=None):
     assert g["res"]["iterations"] == o["iterations"]
     assert (g["res"]["g"], g["res"]["m"], g["res"]["p"]) == (o["g"], o["m"], o["p"])
     scale = cond_scale(w, o)
@@ -58,7 +58,10 @@ def assert_parity(w, o, g, vtol=RTOL_V):
     np.testing.assert_allclose(g["grid"], o["grid"], rtol=0, atol=1e-12)
     adjusting = o["iterations"] if w.ita is None else min(w.ita, o["iterations"])
     if adjusting > 0:
-        np.testing.assert_allclose(g["hist"], o["hist"], rtol=1e-12, atol=1e-300)
+        if hist_tol is None:
+            np.testing.assert_allclose(g["hist"], o["hist"], rtol=1e-12, atol=1e-300)
+        else:
+            assert np.all(np.abs(g["hist"] - o["hist"]) <= hist_tol), np.max(np.abs(g["hist"] - o["hist"]) / hist_tol)
     assert g["res"]["estimate"] == pytest.approx(o["estimate"], abs=RTOL_I * scale)
     assert g["res"]["sigma"] == pytest.approx(o["sigma"], rel=vtol)
     assert g["res"]["chi2_dof"] == pytest.approx(o["chi2_dof"], rel=1e-9, abs=1e-12)
@@ -85,7 +88,18 @@ def test_paper_suite(gpu_ctx_factory, name, d, ncall):
     w = W.suite(name, d, ncall=ncall, itmax=5, seed=7)
     o = oracle_run(w)
     g = gpu_run(gpu_ctx_factory, w)
-    assert_parity(w, o, g, vtol=1e-10 if w.fid == W.F_OSC else RTOL_V)
+    hist_tol = None
+    if name == "fB":
+        # 9-d peak: every rebin amplifies rounding in the narrow peak bins, and
+        # each sample's F^2 lands on all nine axes, so the oracle's own final
+        # histogram moves by ~5e-11 under 1e-15 perturbations.  Tolerance: 10x
+        # the spread measured here (the estimates keep the 1e-12 bar).
+        rng = np.random.default_rng(2)
+        spread = np.zeros_like(o["hist"])
+        for _ in range(3):
+            spread = np.maximum(spread, np.abs(_oracle_last_hist_with_noise(w, 1e-15, rng) - o["hist"]))
+        hist_tol = np.maximum(10 * spread, 1e-12 * np.abs(o["hist"]))
+    assert_parity(w, o, g, vtol=1e-10 if w.fid == W.F_OSC else RTOL_V, hist_tol=hist_tol)
 
 
 def _oracle_trace_with_noise(w, noise, rng):
@@ -102,6 +116,20 @@ def _oracle_trace_with_noise(w, noise, rng):
         for j in range(pb.d):
             _, B[j], L[j] = oracle.rebin_axis(C[j], B[j], Blo=L[j], with_lo=True)
     return np.array(out)
+
+
+def _oracle_last_hist_with_noise(w, noise, rng):
+    """Histogram of the last adjusting iteration of the oracle's loop with
+    relative noise added to every histogram before its rebin."""
+    pb = oracle.Problem(w.fid, w.params, w.lo, w.hi, w.ncall, nb=w.nb, seed=w.seed)
+    B, L = oracle.init_grid(pb.d, pb.nb, with_lo=True)
+    C = None
+    for it in range(w.itmax):
+        _, C, _, _ = pb.vsample(B, it, True, Blo=L)
+        Cn = C * (1 + noise * rng.standard_normal(C.shape))
+        for j in range(pb.d):
+            _, B[j], L[j] = oracle.rebin_axis(Cn[j], B[j], Blo=L[j], with_lo=True)
+    return C
 
 
 def test_ill_conditioned_adaptation_within_measured_sensitivity(gpu_ctx_factory):

@@ -216,6 +216,47 @@ mcubes_status mcubes_hist_get(mcubes_ctx* ctx, double* C, long long count);
 mcubes_status mcubes_sample_range(mcubes_ctx* ctx, unsigned it, int adjust, long long cube_begin,
                                   long long cube_end, double* sums, double* C);
 
+/* ---- sampling without device allocation ----------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory: code that runs while its stream is
+ * being captured into a CUDA graph (cudaMalloc cannot be captured), hosts
+ * whose device memory belongs to another allocator (a framework's caching
+ * pool, a fixed arena in an embedded or real-time service), and processes
+ * that must not grow their device footprint once running.
+ *
+ * One sampling pass (Alg. 3) over sub-cubes [cube_begin, cube_end) of
+ * iteration `it`, as mcubes_sample_range does, but with no context: the
+ * problem is given directly (params, lo, hi are host arrays of nparams and d
+ * values; nbins, g_override, seed and precision as in mcubes_opts), the grid
+ * is read from the caller's device array d_grid ([d][nbins] right edges,
+ * taken as exact), and the results go to the caller's device arrays d_sums
+ * (3 values: sum of cube means, of their variances, of |cube means|) and,
+ * when adjust != 0, d_hist ([d][nbins] per-bin sums of f^2; may be NULL
+ * otherwise).  Work is enqueued on cuda_stream (NULL = legacy default
+ * stream) and the call returns without waiting.
+ *
+ * It allocates nothing: per-block partial sums live in one static device
+ * array of the library, MCUBES_NOALLOC_MAX_BLOCKS x MCUBES_NOALLOC_MAX_BINS
+ * doubles plus small change (about 7.5 MiB), which every GPU that loads the
+ * library keeps until the process exits.  Limits: d * nbins <=
+ * MCUBES_NOALLOC_MAX_BINS, otherwise EINVAL (as for any invalid argument);
+ * at most MCUBES_NOALLOC_MAX_BLOCKS sampling blocks are launched.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and must therefore come before any stream capture on that device.  All
+ * calls share the array and each overwrites what it uses (the part that must
+ * start at zero is cleared on the stream first), so calls whose work
+ * overlaps on the GPU -- on different streams, or from different threads --
+ * race and corrupt each other's results: serialise them.
+ * Errors: EINVAL, ECUDA. */
+#define MCUBES_NOALLOC_MAX_BLOCKS 304
+#define MCUBES_NOALLOC_MAX_BINS 3072
+mcubes_status mcubes_sample_range_noalloc(int device, int integrand_id, const double* params, int nparams,
+                                          int d, const double* lo, const double* hi, long long ncall,
+                                          int nbins, long long g_override, uint64_t seed, int precision,
+                                          unsigned it, int adjust, long long cube_begin, long long cube_end,
+                                          const double* d_grid, double* d_sums, double* d_hist,
+                                          void* cuda_stream);
+
 /* Geometry of the current setup: sub-cubes per axis, sub-cubes, samples per
  * sub-cube, lanes per cube and sampling blocks chosen. */
 mcubes_status mcubes_geometry_get(mcubes_ctx* ctx, long long* g, long long* m, long long* p,

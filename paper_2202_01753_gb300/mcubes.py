@@ -25,6 +25,7 @@ EXPORTED = [
     "mcubes_integrate_batch", "mcubes_setup", "mcubes_iterate", "mcubes_result_get",
     "mcubes_trace_get", "mcubes_grid_get", "mcubes_grid_set", "mcubes_hist_get",
     "mcubes_sample_range", "mcubes_geometry_get", "mcubes_timing_reset", "mcubes_timing_get",
+    "mcubes_sample_range_noalloc",
 ]
 
 
@@ -99,6 +100,10 @@ def lib():
                                                        P(ctypes.c_int)]),
                 "mcubes_timing_reset": (ctypes.c_int, [ctx, ctypes.c_int]),
                 "mcubes_timing_get": (ctypes.c_int, [ctx, dp, P(ctypes.c_int), dp, P(ctypes.c_int)]),
+                "mcubes_sample_range_noalloc": (ctypes.c_int, [
+                    ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, dp, dp, ll, ctypes.c_int, ll,
+                    ctypes.c_uint64, ctypes.c_int, ctypes.c_uint, ctypes.c_int, ll, ll, ctypes.c_void_p,
+                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(h, name)
@@ -114,6 +119,20 @@ def _dp(a):
 
 def _f64(a):
     return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def mcubes_sample_range_noalloc(device, fid, params, lo, hi, ncall, nbins, g_override, seed, precision, it,
+                                adjust, cube_begin, cube_end, d_grid, d_sums, d_hist, stream=0):
+    """Binding of the allocation-free sampling pass: d_grid, d_sums and d_hist
+    are device addresses (ints) owned by the caller; returns the status."""
+    p, lo, hi = _f64(params), _f64(lo), _f64(hi)
+    if isinstance(precision, str):
+        precision = {"fp64": FP64, "mixed": MIXED}[precision]
+    return lib().mcubes_sample_range_noalloc(device, fid, _dp(p), len(p), len(lo), _dp(lo), _dp(hi), int(ncall),
+                                             nbins, int(g_override), int(seed), precision, it, int(adjust),
+                                             int(cube_begin), int(cube_end), ctypes.c_void_p(d_grid),
+                                             ctypes.c_void_p(d_sums), ctypes.c_void_p(d_hist),
+                                             ctypes.c_void_p(stream))
 
 
 class McubesError(RuntimeError):

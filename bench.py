@@ -33,10 +33,17 @@ if ROOT not in sys.path:
 
 from paper_2202_01753_gb300 import workloads as W  # noqa: E402
 
-# Issued warp instructions per sample of the sampling kernel, from the ncu
-# capture summarised in profiles/ (smsp__inst_issued.sum / samples), keyed by
-# (config, precision, adjusting).  None until measured for a kernel version.
-INST_PER_SAMPLE = {}
+# Work per sample of the sampling kernel, from the ncu captures summarised in
+# profiles/ (the per-unit figures of the roofline), keyed by (config,
+# precision).  "fp64": FP64 flops per sample (2 DFMA + DADD + DMUL) against the
+# FP64 pipe (2 DFMA/clk/SM on GB300, ncu peak_sustained); "issue": issued warp
+# instructions per 32 samples against 4 issue slots/clk/SM.
+ROOFLINE_UNITS = {
+    ("cosmo6", "fp64"): {"kind": "fp64", "per_sample": 399.9,
+                         "source": "profiles/vsample_cosmo6_fp64.md"},
+}
+DFMA_PER_CLK_PER_SM = 2.0
+ISSUE_PER_CLK_PER_SM = 4.0
 
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2: written between timed steps
 
@@ -47,7 +54,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="cosmo6", choices=sorted(W.CONFIGS))
+    ap.add_argument("--config", default="cosmo6", choices=sorted(W.CONFIGS) + ["batch4096"])
+    ap.add_argument("--batch-n", type=int, default=4096)
+    ap.add_argument("--seq-sample", type=int, default=96, help="integrals timed one by one in plain FP64")
     ap.add_argument("--ncall", type=float, default=None, help="override calls per iteration (profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -59,6 +68,24 @@ def workload(args, rank):
     if args.ncall:
         w = w.scaled(int(args.ncall))
     return w
+
+
+# ---------------------------------------------------------------------------
+# cross-rank aggregation (weak scaling: every rank integrates its own copy)
+# ---------------------------------------------------------------------------
+def aggregate_ranks(local_ms, local_samples, device):
+    """Whole-job throughput: the samples of all ranks over the slowest rank's
+    time.  Returns (samples_per_s, max_ms, total_samples); works on any
+    initialised process group (NCCL on GPUs, gloo on CPUs) or none."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    n = torch.tensor([float(local_samples)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    max_ms, total = float(t.item()), float(n.item())
+    return total / (max_ms / 1e3), max_ms, total
 
 
 # ---------------------------------------------------------------------------
@@ -221,12 +248,7 @@ def ours(args):
     ctx.close()
 
     # slowest rank's time, all ranks' samples
-    t_max = total_ms
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = N * K * world / (t_max / 1e3)
+    value, t_max, _ = aggregate_ranks(total_ms, N * K, "cuda")
 
     # end to end through the public call with host buffers (copies inside)
     ctx2 = mcubes.Context(local, nbins=w.nb, g_override=w.g_override, seed=w.seed, precision=prec, ita=-1)
@@ -236,10 +258,7 @@ def ours(args):
     r2 = ctx2.integrate(w.fid, w.params, w.lo, w.hi, w.ncall, K)
     e2e_s = time.perf_counter() - t0
     ctx2.close()
-    e2e_t = torch.tensor([e2e_s], device="cuda")
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = N * K * world / float(e2e_t.item())
+    e2e_value, _, _ = aggregate_ranks(e2e_s * 1e3, N * K, "cuda")
     h2d = 8 * (len(w.params) + 2 * w.d)
     d2h = 88
 
@@ -253,18 +272,27 @@ def ours(args):
     props = torch.cuda.get_device_properties(local)
     sms = props.multi_processor_count
     avg_sample_ms = kt["sample_ms"] / max(kt["sample_launches"], 1)
-    key = (args.config, prec, True)
-    ips = INST_PER_SAMPLE.get(key)
+    unit = ROOFLINE_UNITS.get((args.config, prec))
     sm_mhz = clk.get("sm_mhz") or 0.0
-    peak_issue = 4.0 * sms * sm_mhz * 1e6 / 1e9           # G warp-instructions / s
-    if ips is not None and sm_mhz:
-        achieved = ips * N / (avg_sample_ms / 1e3) / 1e9
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak_issue, "unit": "Gwarp-inst/s",
-                "frac": achieved / peak_issue, "traffic": None,
-                "note": "issue slots: 4 warp-instructions/clk/SM x SMs x median SM clock under load"}
+    t_launch = avg_sample_ms / 1e3
+    if unit and unit["kind"] == "fp64" and sm_mhz:
+        peak = 2 * DFMA_PER_CLK_PER_SM * sms * sm_mhz * 1e6 / 1e12          # TFLOP/s
+        achieved = unit["per_sample"] * N / t_launch / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "pipe": "fp64",
+                "peak_how": "2 DFMA/clk/SM (ncu peak_sustained) x 2 flops x SMs x median SM clock under load",
+                "measured_dfma_tflops": 2 * pk["dfma_per_s"] / 1e12,
+                "per_sample": f"{unit['per_sample']} FP64 flops ({unit['source']})"}
+    elif unit and unit["kind"] == "issue" and sm_mhz:
+        peak = ISSUE_PER_CLK_PER_SM * sms * sm_mhz * 1e6 / 1e9              # G warp-instructions/s
+        achieved = unit["per_sample"] * (N / 32.0) / t_launch / 1e9
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gwarp-inst/s", "frac": achieved / peak,
+                "traffic": None, "pipe": "issue",
+                "peak_how": "4 warp-instructions/clk/SM x SMs x median SM clock under load",
+                "per_sample": f"{unit['per_sample']} thread-instructions ({unit['source']})"}
     else:
-        roof = {"bound": "alu", "achieved": None, "peak": peak_issue, "unit": "Gwarp-inst/s", "frac": None,
-                "traffic": None, "note": "per-sample instruction count not yet measured for this kernel"}
+        roof = {"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
+                "note": "no ncu per-sample count recorded for this configuration"}
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -299,8 +327,67 @@ def ours(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# batched integrals: integrals/s of the batched mixed-precision path against
+# the plain per-integral FP64 path on the same GPU
+# ---------------------------------------------------------------------------
+def batch_arm(args):
+    import torch
+
+    from paper_2202_01753_gb300 import build, mcubes
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    build.build()
+    ws = W.batch4096(n=args.batch_n)
+    reqs = [dict(fid=w.fid, params=w.params, lo=w.lo, hi=w.hi, ncall=w.ncall, itmax=w.itmax, seed=w.seed)
+            for w in ws]
+    ctx = mcubes.Context(local, precision="mixed")
+    ctx.integrate_batch(reqs[: min(64, len(reqs))])        # warm-up (autotune, graph capture)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    out = ctx.integrate_batch(reqs)
+    t_batch = time.perf_counter() - t0
+    clk = clocks.stop()
+    ctx.close()
+    # plain FP64, one integral at a time, on an evenly spaced sample
+    step = max(1, len(ws) // args.seq_sample)
+    idx = list(range(0, len(ws), step))[: args.seq_sample]
+    solo = mcubes.Context(local, precision="fp64")
+    solo.integrate(ws[0].fid, ws[0].params, ws[0].lo, ws[0].hi, ws[0].ncall, 2)
+    t_seq, rel = 0.0, []
+    for i in idx:
+        w = ws[i]
+        solo.set_opts(seed=w.seed)
+        t0 = time.perf_counter()
+        r = solo.integrate(w.fid, w.params, w.lo, w.hi, w.ncall, w.itmax)
+        t_seq += time.perf_counter() - t0
+        rel.append(abs(out[i]["estimate"] - r["estimate"]) / max(abs(r["estimate"]), r["sigma"]))
+    solo.close()
+    seq_per_integral = t_seq / len(idx)
+    samples = sum(o["samples_per_iter"] * o["iterations"] for o in out)
+    line = {
+        "metric": "integrals per second", "value": len(ws) / t_batch, "unit": "integrals/s", "n_gpus": 1,
+        "steps": 1, "warmup": 1, "ms_per_step": 1e3 * t_batch, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"batch{len(ws)}", "integrals": len(ws), "iterations": ws[0].itmax,
+                   "samples_total": samples, "precision": "mixed"},
+        "evals_per_s": samples / t_batch,
+        "sequential_fp64": {"integrals_per_s": 1.0 / seq_per_integral, "sample": f"{len(idx)} integrals",
+                            "speedup_of_batched": seq_per_integral * len(ws) / t_batch,
+                            "max_rel_diff_of_estimates": max(rel), "median_rel_diff": statistics.median(rel)},
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
+    if args.config == "batch4096":
+        return batch_arm(args)
     if args.impl == "reference":
         return reference_arm(args)
     return ours(args)

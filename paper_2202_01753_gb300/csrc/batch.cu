@@ -1,0 +1,547 @@
+// batch.cu -- the batched engine: a table of resident integrals ("slots"),
+// each with its own grid, iteration state and history on the device, that
+// are iterated together.  One iteration of every live integral is one
+// persistent sampling launch (batch.cuh) plus one refinement launch
+// (Adjust-Bin-Bounds per axis, Weighted-Estimates and Check-Convergence per
+// integral, Alg. 2); both are captured once as a CUDA graph whose arguments
+// live in device memory, and the host rewrites the work partition between
+// replays.  Integrals may be admitted and retired between iterations, which
+// is what the continuous-batching server (server.cu) builds on.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "batch_engine.h"
+#include "refine_dev.cuh"
+
+namespace mc {
+bool integrand_prepare(int id, const double* p, int np, int d, FamParams* out);
+bool geometry(int d, long long ncall, long long g_override, int nb, long long* g, long long* m, long long* p);
+cudaError_t launch_vsample_batch_fp64(const BatchArgs& a, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_vsample_batch_mixed(const BatchArgs& a, int grid, size_t smem, cudaStream_t s);
+cudaError_t vsample_batch_occupancy_fp64(size_t smem, int* blocks);
+cudaError_t vsample_batch_occupancy_mixed(size_t smem, int* blocks);
+
+cudaError_t launch_vsample_batch(bool mixed, const BatchArgs& a, int grid, size_t smem, cudaStream_t s)
+{
+    return mixed ? launch_vsample_batch_mixed(a, grid, smem, s) : launch_vsample_batch_fp64(a, grid, smem, s);
+}
+
+cudaError_t vsample_batch_occupancy(bool mixed, size_t smem, int* blocks)
+{
+    return mixed ? vsample_batch_occupancy_mixed(smem, blocks) : vsample_batch_occupancy_fp64(smem, blocks);
+}
+
+namespace {
+
+using namespace refine_detail;
+
+// Refinement of one iteration of every live integral: block (axis, j) of the
+// live integral j rebins that axis (adjusting iterations); block (d or 0, j)
+// reduces the integral's segment partials in order and weighs the iteration.
+__global__ void __launch_bounds__(kRefineThreads) refine_batch_kernel(const __grid_constant__ BatchRefineArgs a)
+{
+    __shared__ double scratch[33];
+    const uint32_t j = blockIdx.y;
+    if (j >= *a.nlive) return;
+    const uint32_t slot = a.live[j];
+    const BatchDesc& D = a.desc[slot];
+    const uint32_t s0 = a.live_seg[j], s1 = a.live_seg[j + 1];
+    const bool adjust = a.segs[s0].adjust != 0;
+    const int d = (int)D.d, nb = (int)D.nb;
+    const int nrebin = adjust ? d : 0;
+    if ((int)blockIdx.x > nrebin) return;
+    BatchState* st = a.st + slot;
+    if ((int)blockIdx.x == nrebin) {
+        const IterRecord r{&st->it, &st->done, &st->error, &st->n, &st->converged, &st->estimate, &st->sigma,
+                           &st->chi2_dof, D.hist_I, D.hist_V, D.itmax, D.rel_tol, D.abs_tol};
+        finalize_iteration(a.seg_part + 3 * (size_t)s0, (int)(s1 - s0), (double)D.m, r, scratch);
+    } else {
+        const int ax = blockIdx.x;
+        const size_t off = (size_t)ax * nb;
+        const size_t elem = a.hist_is_float ? sizeof(float) : sizeof(double);
+        const char* parts = static_cast<const char*>(a.seg_hist) + (a.segs[s0].hist_off + off) * elem;
+        rebin_axis(parts, (size_t)d * nb, (int)(s1 - s0), a.hist_is_float != 0, nb, a.alpha, D.grid + off,
+                   D.grid + (size_t)d * nb + off, D.hist + off, &st->error, &st->done, scratch);
+    }
+}
+
+// Uniform grid (Init-Bins, Alg. 2, double-double edges), empty histogram and
+// a cleared state for every newly admitted slot.
+__global__ void init_slots_kernel(const BatchDesc* desc, BatchState* st, const uint32_t* slots, int count)
+{
+    const uint32_t slot = slots[blockIdx.x];
+    const BatchDesc& D = desc[slot];
+    const int d = (int)D.d, nb = (int)D.nb;
+    for (int i = threadIdx.x; i < d * nb; i += blockDim.x) {
+        const int k = i % nb;
+        double hi = 1.0, lo = 0.0;
+        if (k != nb - 1) {
+            hi = __ddiv_rn((double)(k + 1), (double)nb);
+            lo = __ddiv_rn(__fma_rn(-hi, (double)nb, (double)(k + 1)), (double)nb);
+        }
+        D.grid[i] = hi;
+        D.grid[(size_t)d * nb + i] = lo;
+        D.hist[i] = 0.0;
+    }
+    if (threadIdx.x == 0) {
+        BatchState z;
+        memset(&z, 0, sizeof z);
+        st[slot] = z;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_refine_batch(const BatchRefineArgs& a, int capacity, cudaStream_t s)
+{
+    refine_batch_kernel<<<dim3(kDMax + 1, capacity), kRefineThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_slots(const BatchDesc* desc, BatchState* st, const uint32_t* slots, int count,
+                              cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    init_slots_kernel<<<count, 256, 0, s>>>(desc, st, slots, count);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// engine
+// ---------------------------------------------------------------------------
+BatchEngine::BatchEngine(int device, cudaStream_t stream, int num_sms, const mcubes_opts& o)
+    : device_(device), stream_(stream), num_sms_(num_sms), opts_(o), mixed_(o.precision == MCUBES_MIXED)
+{
+}
+
+BatchEngine::~BatchEngine() { release(); }
+
+void BatchEngine::release()
+{
+    if (exec_) cudaGraphExecDestroy(exec_);
+    if (graph_) cudaGraphDestroy(graph_);
+    exec_ = nullptr;
+    graph_ = nullptr;
+    for (DevBuf* b : {&desc_, &st_, &grids_, &hists_, &histories_, &segs_, &blk_seg_, &live_, &live_seg_, &nlive_,
+                      &seg_part_, &seg_hist_, &admit_slots_})
+        b->release();
+    if (h_segs_) cudaFreeHost(h_segs_);
+    if (h_small_) cudaFreeHost(h_small_);
+    if (h_states_) cudaFreeHost(h_states_);
+    h_segs_ = nullptr;
+    h_small_ = nullptr;
+    h_states_ = nullptr;
+    capacity_ = 0;
+}
+
+size_t BatchEngine::smem_bytes() const
+{
+    return (size_t)kDMax * opts_.nbins * (cell_bytes(mixed_) + hist_bytes(mixed_));
+}
+
+cudaError_t BatchEngine::reserve(int capacity, int itcap)
+{
+    if (capacity <= capacity_ && itcap <= itcap_) return cudaSuccess;
+    release();
+    const int nb = opts_.nbins;
+    int occ = 0;
+    cudaError_t e = vsample_batch_occupancy(mixed_, smem_bytes(), &occ);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    occ_max_ = occ;
+    const int bmax = occ * num_sms_;
+    const size_t segmax = (size_t)capacity + bmax + 1;
+    const size_t grid_stride = 2 * (size_t)kDMax * nb, hist_stride = (size_t)kDMax * nb;
+    const size_t elem = mixed_ ? sizeof(float) : sizeof(double);
+    if ((e = desc_.reserve(sizeof(BatchDesc) * capacity)) ||
+        (e = st_.reserve(sizeof(BatchState) * capacity)) ||
+        (e = grids_.reserve(sizeof(double) * grid_stride * capacity)) ||
+        (e = hists_.reserve(sizeof(double) * hist_stride * capacity)) ||
+        (e = histories_.reserve(sizeof(double) * 2 * (size_t)itcap * capacity)) ||
+        (e = segs_.reserve(sizeof(BatchSeg) * segmax)) || (e = blk_seg_.reserve(sizeof(uint32_t) * (bmax + 1))) ||
+        (e = live_.reserve(sizeof(uint32_t) * capacity)) ||
+        (e = live_seg_.reserve(sizeof(uint32_t) * (capacity + 1))) || (e = nlive_.reserve(sizeof(uint32_t))) ||
+        (e = seg_part_.reserve(sizeof(double) * 3 * segmax)) ||
+        (e = seg_hist_.reserve(elem * hist_stride * segmax)) || (e = admit_slots_.reserve(sizeof(uint32_t) * capacity)))
+        return e;
+    if ((e = cudaHostAlloc((void**)&h_segs_, sizeof(BatchSeg) * segmax, cudaHostAllocDefault)) ||
+        (e = cudaHostAlloc((void**)&h_small_, sizeof(uint32_t) * (3 * (size_t)capacity + bmax + 8),
+                           cudaHostAllocDefault)) ||
+        (e = cudaHostAlloc((void**)&h_states_, sizeof(BatchState) * capacity, cudaHostAllocDefault)))
+        return e;
+    capacity_ = capacity;
+    itcap_ = itcap;
+    slots_.assign(capacity, Slot{});
+    hdesc_.assign(capacity, BatchDesc{});
+    free_.clear();
+    for (int i = capacity - 1; i >= 0; --i) free_.push_back(i);
+    pending_.clear();
+    return cudaSuccess;
+}
+
+int BatchEngine::choose_lanes(long long p) const
+{
+    if (opts_.lanes_per_cube > 0) return std::min<long long>(opts_.lanes_per_cube, std::max<long long>(p, 1));
+    int L = 1;
+    while (L < 32 && 2 * L <= p && p / L > lanes_cap_) L *= 2;
+    return L;
+}
+
+mcubes_status BatchEngine::admit(const mcubes_request& r, long long tag, int* slot_out)
+{
+    const int d = r.d, nb = opts_.nbins;
+    if (d < 1 || d > MCUBES_DMAX || r.ncall < 2 || r.itmax < 1 || r.itmax > itcap_ || !r.lo || !r.hi)
+        return MCUBES_EINVAL;
+    if (!(r.rel_tol >= 0.0) || !(r.abs_tol >= 0.0)) return MCUBES_EINVAL;
+    FamParams fp;
+    if (!integrand_prepare(r.integrand_id, r.params, r.nparams, d, &fp)) return MCUBES_EINVAL;
+    for (int j = 0; j < d; ++j)
+        if (!std::isfinite(r.lo[j]) || !std::isfinite(r.hi[j]) || !(r.lo[j] < r.hi[j])) return MCUBES_EINVAL;
+    long long g, m, p;
+    if (!geometry(d, r.ncall, opts_.g_override, nb, &g, &m, &p)) return MCUBES_EINVAL;
+    if (free_.empty()) return MCUBES_ENOMEM;
+    const int slot = free_.back();
+    free_.pop_back();
+    BatchDesc& D = hdesc_[slot];
+    std::memset(&D, 0, sizeof D);
+    D.d = (uint32_t)d;
+    D.nb = (uint32_t)nb;
+    D.g = (uint32_t)g;
+    D.gmagic = (uint32_t)(0xFFFFFFFFu / (uint32_t)g);
+    D.p = (uint32_t)p;
+    D.lanes = (uint32_t)choose_lanes(p);
+    D.key0 = (uint32_t)r.seed;
+    D.key1 = (uint32_t)(r.seed >> 32);
+    D.family = r.integrand_id;
+    D.ita = opts_.ita < 0 ? r.itmax : std::min(opts_.ita, r.itmax);
+    D.itmax = r.itmax;
+    D.m = (uint64_t)m;
+    D.phi_scale = std::ldexp(1.0 / ((double)g * nb), -33);
+    D.phi_scale_f = (float)(1.0 / ((double)g * nb));
+    for (int j = 0; j < d; ++j) {
+        D.lo[j] = r.lo[j];
+        D.scale[j] = r.hi[j] - r.lo[j];
+    }
+    D.fam = fp;
+    const size_t grid_stride = 2 * (size_t)kDMax * nb, hist_stride = (size_t)kDMax * nb;
+    D.grid = (double*)grids_.ptr + grid_stride * slot;
+    D.hist = (double*)hists_.ptr + hist_stride * slot;
+    D.hist_I = (double*)histories_.ptr + 2 * (size_t)itcap_ * slot;
+    D.hist_V = D.hist_I + itcap_;
+    D.rel_tol = r.rel_tol;
+    D.abs_tol = r.abs_tol;
+    Slot& S = slots_[slot];
+    S = Slot{};
+    S.used = true;
+    S.tag = tag;
+    S.work = (double)m * (double)p;
+    S.g = g;
+    S.m = m;
+    S.p = p;
+    pending_.push_back(slot);
+    if (slot_out) *slot_out = slot;
+    return MCUBES_OK;
+}
+
+cudaError_t BatchEngine::flush_admissions()
+{
+    if (pending_.empty()) return cudaSuccess;
+    cudaError_t e;
+    for (int slot : pending_) {
+        if ((e = cudaMemcpyAsync((BatchDesc*)desc_.ptr + slot, &hdesc_[slot], sizeof(BatchDesc),
+                                 cudaMemcpyHostToDevice, stream_)))
+            return e;
+    }
+    uint32_t* hs = h_small_;  // staging: slot list
+    for (size_t i = 0; i < pending_.size(); ++i) hs[i] = (uint32_t)pending_[i];
+    if ((e = cudaMemcpyAsync(admit_slots_.ptr, hs, sizeof(uint32_t) * pending_.size(), cudaMemcpyHostToDevice,
+                             stream_)))
+        return e;
+    if ((e = launch_init_slots((const BatchDesc*)desc_.ptr, (BatchState*)st_.ptr, (const uint32_t*)admit_slots_.ptr,
+                               (int)pending_.size(), stream_)))
+        return e;
+    e = cudaStreamSynchronize(stream_);  // the pinned staging is reused below
+    pending_.clear();
+    return e;
+}
+
+// Lays the live integrals' samples end to end and cuts the line into
+// `blocks` equal chunks; cube c of an integral goes to the chunk holding its
+// first sample.  Writes the segment list (ordered by block and, within the
+// whole list, by live integral), the block and live-integral offsets.
+void BatchEngine::partition(const std::vector<int>& live, int blocks, int* nseg_out)
+{
+    double total = 0.0;
+    for (int s : live) total += slots_[s].work;
+    const double chunk = total / blocks;
+    uint32_t* blk_seg = h_small_;
+    uint32_t* live_slot = h_small_ + blocks + 1;
+    uint32_t* live_seg = live_slot + capacity_;
+    int nseg = 0;
+    size_t hist_off = 0;
+    double start = 0.0;  // first sample of the current integral on the line
+    int b = 0;
+    blk_seg[0] = 0;
+    for (size_t j = 0; j < live.size(); ++j) {
+        const int s = live[j];
+        const Slot& S = slots_[s];
+        live_slot[j] = (uint32_t)s;
+        live_seg[j] = (uint32_t)nseg;
+        const bool adjust = S.it < hdesc_[s].ita;
+        const double p = (double)S.p;
+        uint64_t c = 0;
+        while (c < (uint64_t)S.m) {
+            // last cube whose first sample lies in chunk b
+            const double chunk_end = (b + 1 == blocks) ? 1e300 : (b + 1) * chunk;
+            double cend_d = std::ceil((chunk_end - start) / p);
+            uint64_t cend = cend_d >= (double)S.m ? (uint64_t)S.m : (uint64_t)std::max(cend_d, 0.0);
+            if (cend > c) {
+                BatchSeg& g = h_segs_[nseg++];
+                g.slot = (uint32_t)s;
+                g.adjust = adjust ? 1u : 0u;
+                g.c0 = c;
+                g.c1 = cend;
+                g.hist_off = hist_off;
+                if (adjust) hist_off += (size_t)hdesc_[s].d * hdesc_[s].nb;
+                c = cend;
+            }
+            if (c < (uint64_t)S.m) {
+                blk_seg[++b] = (uint32_t)nseg;  // block b is full
+            }
+        }
+        start += S.work;
+    }
+    while (b < blocks) blk_seg[++b] = (uint32_t)nseg;
+    live_seg[live.size()] = (uint32_t)nseg;
+    *nseg_out = nseg;
+}
+
+cudaError_t BatchEngine::upload_partition(const std::vector<int>& live, int blocks, int nseg)
+{
+    cudaError_t e;
+    const uint32_t* blk_seg = h_small_;
+    const uint32_t* live_slot = h_small_ + blocks + 1;
+    const uint32_t* live_seg = live_slot + capacity_;
+    uint32_t* nl = h_small_ + blocks + 1 + 2 * (size_t)capacity_ + 1;
+    *nl = (uint32_t)live.size();
+    if ((e = cudaMemcpyAsync(segs_.ptr, h_segs_, sizeof(BatchSeg) * nseg, cudaMemcpyHostToDevice, stream_)) ||
+        (e = cudaMemcpyAsync(blk_seg_.ptr, blk_seg, sizeof(uint32_t) * (blocks + 1), cudaMemcpyHostToDevice,
+                             stream_)) ||
+        (e = cudaMemcpyAsync(live_.ptr, live_slot, sizeof(uint32_t) * live.size(), cudaMemcpyHostToDevice,
+                             stream_)) ||
+        (e = cudaMemcpyAsync(live_seg_.ptr, live_seg, sizeof(uint32_t) * (live.size() + 1),
+                             cudaMemcpyHostToDevice, stream_)) ||
+        (e = cudaMemcpyAsync(nlive_.ptr, nl, sizeof(uint32_t), cudaMemcpyHostToDevice, stream_)))
+        return e;
+    return cudaSuccess;
+}
+
+BatchArgs BatchEngine::sample_args() const
+{
+    BatchArgs a;
+    a.desc = (const BatchDesc*)desc_.ptr;
+    a.st = (const BatchState*)st_.ptr;
+    a.segs = (const BatchSeg*)segs_.ptr;
+    a.blk_seg = (const uint32_t*)blk_seg_.ptr;
+    a.seg_part = (double*)seg_part_.ptr;
+    a.seg_hist = seg_hist_.ptr;
+    return a;
+}
+
+BatchRefineArgs BatchEngine::refine_args() const
+{
+    BatchRefineArgs r;
+    r.desc = (const BatchDesc*)desc_.ptr;
+    r.st = (BatchState*)st_.ptr;
+    r.live = (const uint32_t*)live_.ptr;
+    r.live_seg = (const uint32_t*)live_seg_.ptr;
+    r.nlive = (const uint32_t*)nlive_.ptr;
+    r.segs = (const BatchSeg*)segs_.ptr;
+    r.seg_part = (const double*)seg_part_.ptr;
+    r.seg_hist = seg_hist_.ptr;
+    r.hist_is_float = mixed_ ? 1 : 0;
+    r.alpha = opts_.alpha;
+    return r;
+}
+
+cudaError_t BatchEngine::enqueue_iteration(int blocks)
+{
+    cudaError_t e = launch_vsample_batch(mixed_, sample_args(), blocks, smem_bytes(), stream_);
+    if (e) return e;
+    return launch_refine_batch(refine_args(), capacity_, stream_);
+}
+
+cudaError_t BatchEngine::capture(int blocks)
+{
+    if (exec_ && graph_blocks_ == blocks) return cudaSuccess;
+    if (exec_) cudaGraphExecDestroy(exec_);
+    if (graph_) cudaGraphDestroy(graph_);
+    exec_ = nullptr;
+    graph_ = nullptr;
+    if (stream_ == nullptr) return cudaSuccess;  // the legacy stream cannot be captured: launch directly
+    cudaError_t e = cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal);
+    if (e) return e;
+    cudaError_t le = enqueue_iteration(blocks);
+    e = cudaStreamEndCapture(stream_, &graph_);
+    if (le) return le;
+    if (e) return e;
+    e = cudaGraphInstantiate(&exec_, graph_, 0);
+    if (e) return e;
+    graph_blocks_ = blocks;
+    return cudaSuccess;
+}
+
+void BatchEngine::live_slots(std::vector<int>* live) const
+{
+    live->clear();
+    for (int s = 0; s < capacity_; ++s) {
+        const Slot& S = slots_[s];
+        if (S.used && !S.finished && S.it < hdesc_[s].itmax) live->push_back(s);
+    }
+}
+
+// Picks the resident sampling blocks per SM (and the samples-per-thread cap
+// that sets lanes per cube) by timing sampling-only launches of this batch's
+// first iteration; the choice is kept for the life of the engine.
+cudaError_t BatchEngine::autotune(const std::vector<int>& live)
+{
+    if (tuned_) return cudaSuccess;
+    std::vector<int> bps_list;
+    if (opts_.blocks_per_sm > 0) bps_list.push_back(std::min(opts_.blocks_per_sm, occ_max_));
+    else for (int b = 1; b <= occ_max_; ++b) bps_list.push_back(b);
+    std::vector<int> cap_list = opts_.lanes_per_cube > 0 ? std::vector<int>{lanes_cap_} : std::vector<int>{16, 64, 256};
+    // a subset of the batch (every k-th integral) keeps tuning cheap
+    std::vector<int> sub;
+    const size_t stride = std::max<size_t>(1, live.size() / 256);
+    for (size_t i = 0; i < live.size(); i += stride) sub.push_back(live[i]);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int best_bps = bps_list.back(), best_cap = 64;
+    cudaError_t e = cudaSuccess;
+    for (int cap : cap_list) {
+        lanes_cap_ = cap;
+        for (int s : sub) {
+            hdesc_[s].lanes = (uint32_t)choose_lanes(slots_[s].p);
+            if ((e = cudaMemcpyAsync((BatchDesc*)desc_.ptr + s, &hdesc_[s], sizeof(BatchDesc), cudaMemcpyHostToDevice,
+                                     stream_)))
+                break;
+        }
+        if (e) break;
+        for (int bps : bps_list) {
+            const int blocks = bps * num_sms_;
+            int nseg = 0;
+            if ((e = cudaStreamSynchronize(stream_))) break;  // pinned staging reuse
+            partition(sub, blocks, &nseg);
+            if ((e = upload_partition(sub, blocks, nseg))) break;
+            float ms = 0.f;
+            for (int rep = 0; rep < 2; ++rep) {  // first launch warms up
+                cudaEventRecord(e0, stream_);
+                if ((e = launch_vsample_batch(mixed_, sample_args(), blocks, smem_bytes(), stream_))) break;
+                cudaEventRecord(e1, stream_);
+                if ((e = cudaEventSynchronize(e1))) break;
+                cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (e) break;
+            if (ms < best) {
+                best = ms;
+                best_bps = bps;
+                best_cap = cap;
+            }
+        }
+        if (e) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e) return e;
+    lanes_cap_ = best_cap;
+    tuned_bps_ = best_bps;
+    tuned_ = true;
+    // final lanes for every resident integral
+    for (int s = 0; s < capacity_; ++s) {
+        if (!slots_[s].used) continue;
+        hdesc_[s].lanes = (uint32_t)choose_lanes(slots_[s].p);
+        if ((e = cudaMemcpyAsync((BatchDesc*)desc_.ptr + s, &hdesc_[s], sizeof(BatchDesc), cudaMemcpyHostToDevice,
+                                 stream_)))
+            return e;
+    }
+    return cudaStreamSynchronize(stream_);
+}
+
+cudaError_t BatchEngine::step(int* ran)
+{
+    *ran = 0;
+    cudaError_t e = flush_admissions();
+    if (e) return e;
+    std::vector<int> live;
+    live_slots(&live);
+    if (live.empty()) return cudaSuccess;
+    if ((e = autotune(live))) return e;
+    const int blocks = tuned_bps_ * num_sms_;
+    if ((e = capture(blocks))) return e;
+    int nseg = 0;
+    partition(live, blocks, &nseg);
+    if ((e = upload_partition(live, blocks, nseg))) return e;
+    if (exec_) e = cudaGraphLaunch(exec_, stream_);
+    else e = enqueue_iteration(blocks);
+    if (e) return e;
+    for (int s : live) slots_[s].it += 1;
+    *ran = (int)live.size();
+    // the pinned partition staging is rewritten by the next step: wait here,
+    // then read back which integrals have finished
+    return refresh();
+}
+
+cudaError_t BatchEngine::refresh()
+{
+    cudaError_t e = cudaMemcpyAsync(h_states_, st_.ptr, sizeof(BatchState) * capacity_, cudaMemcpyDeviceToHost, stream_);
+    if (e) return e;
+    if ((e = cudaStreamSynchronize(stream_))) return e;
+    for (int s = 0; s < capacity_; ++s) {
+        Slot& S = slots_[s];
+        if (!S.used || S.finished) continue;
+        const BatchState& B = h_states_[s];
+        if (B.done || S.it >= hdesc_[s].itmax) {
+            S.finished = true;
+            mcubes_result& R = S.result;
+            R.estimate = B.estimate;
+            R.sigma = B.sigma;
+            R.chi2_dof = B.chi2_dof;
+            R.iterations = B.n;
+            R.converged = B.converged;
+            R.samples_per_iter = S.m * S.p;
+            R.g = S.g;
+            R.m = S.m;
+            R.p = S.p;
+            R.status = B.error ? B.error : (B.converged ? MCUBES_OK : MCUBES_ENOCONV);
+        }
+    }
+    return cudaSuccess;
+}
+
+void BatchEngine::finished(std::vector<std::pair<long long, mcubes_result>>* out, bool free_slots)
+{
+    for (int s = 0; s < capacity_; ++s) {
+        Slot& S = slots_[s];
+        if (S.used && S.finished && !S.reported) {
+            out->emplace_back(S.tag, S.result);
+            S.reported = true;
+            if (free_slots) {
+                S.used = false;
+                free_.push_back(s);
+            }
+        }
+    }
+}
+
+int BatchEngine::resident() const
+{
+    int n = 0;
+    for (const Slot& S : slots_) n += S.used && !S.finished ? 1 : 0;
+    return n;
+}
+
+}  // namespace mc

@@ -1,0 +1,113 @@
+// batch_engine.h -- host side of the batched path: device buffers, the slot
+// table of resident integrals, the per-iteration work partition, the CUDA
+// graph of one iteration and the launch-shape autotuner (batch.cu).
+#pragma once
+
+#include <utility>
+#include <vector>
+
+#include "mc_internal.h"
+
+namespace mc {
+
+// A device allocation that only grows.
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    cudaError_t reserve(size_t n)
+    {
+        if (n <= bytes) return cudaSuccess;
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMalloc(&ptr, n);
+        if (e == cudaSuccess) bytes = n;
+        return e;
+    }
+    void release()
+    {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+    }
+};
+
+class BatchEngine {
+public:
+    BatchEngine(int device, cudaStream_t stream, int num_sms, const mcubes_opts& opts);
+    ~BatchEngine();
+    BatchEngine(const BatchEngine&) = delete;
+    BatchEngine& operator=(const BatchEngine&) = delete;
+
+    // Room for `capacity` resident integrals of up to itcap iterations each
+    // (every slot can hold MCUBES_DMAX axes of opts.nbins bins).
+    cudaError_t reserve(int capacity, int itcap);
+    int capacity() const { return capacity_; }
+    int itcap() const { return itcap_; }
+    int free_slots() const { return (int)free_.size(); }
+    int resident() const;
+
+    // Validates one request and places it in a free slot (its grid and state
+    // are initialised on the device at the next step).  tag identifies it in
+    // finished().  EINVAL: invalid request; ENOMEM: no free slot.
+    mcubes_status admit(const mcubes_request& r, long long tag, int* slot = nullptr);
+
+    // One iteration of every resident, unfinished integral (graph replay),
+    // then a read-back of which ones have finished.  *ran = integrals iterated.
+    cudaError_t step(int* ran);
+
+    // Results of integrals that finished since the last call (tag, result);
+    // with free_slots their slots become free for new admissions.
+    void finished(std::vector<std::pair<long long, mcubes_result>>* out, bool free_slots);
+
+    int tuned_blocks_per_sm() const { return tuned_bps_; }
+    int lanes_cap() const { return lanes_cap_; }
+
+private:
+    struct Slot {
+        bool used = false, finished = false, reported = false;
+        long long tag = 0;
+        int it = 0;           // iterations enqueued
+        double work = 0.0;    // samples per iteration
+        long long g = 0, m = 0, p = 0;
+        mcubes_result result{};
+    };
+
+    void release();
+    size_t smem_bytes() const;
+    int choose_lanes(long long p) const;
+    cudaError_t flush_admissions();
+    void live_slots(std::vector<int>* live) const;
+    void partition(const std::vector<int>& live, int blocks, int* nseg);
+    cudaError_t upload_partition(const std::vector<int>& live, int blocks, int nseg);
+    BatchArgs sample_args() const;
+    BatchRefineArgs refine_args() const;
+    cudaError_t enqueue_iteration(int blocks);
+    cudaError_t capture(int blocks);
+    cudaError_t autotune(const std::vector<int>& live);
+    cudaError_t refresh();
+
+    int device_;
+    cudaStream_t stream_;
+    int num_sms_;
+    mcubes_opts opts_;
+    bool mixed_;
+    int capacity_ = 0, itcap_ = 0, occ_max_ = 1;
+    bool tuned_ = false;
+    int tuned_bps_ = 1, lanes_cap_ = 64;
+
+    std::vector<Slot> slots_;
+    std::vector<BatchDesc> hdesc_;
+    std::vector<int> free_, pending_;
+
+    DevBuf desc_, st_, grids_, hists_, histories_, segs_, blk_seg_, live_, live_seg_, nlive_, seg_part_, seg_hist_,
+        admit_slots_;
+    BatchSeg* h_segs_ = nullptr;     // pinned staging
+    uint32_t* h_small_ = nullptr;    // pinned staging: block offsets, live lists, counts
+    BatchState* h_states_ = nullptr; // pinned read-back
+    cudaGraph_t graph_ = nullptr;
+    cudaGraphExec_t exec_ = nullptr;
+    int graph_blocks_ = 0;
+};
+
+}  // namespace mc

@@ -8,7 +8,7 @@
 #include <new>
 #include <vector>
 
-#include "mc_internal.h"
+#include "batch_engine.h"
 
 using namespace mc;
 
@@ -63,7 +63,7 @@ cudaError_t vsample_occupancy(int family, bool mixed, bool adjust, size_t smem, 
 
 size_t vsample_smem_bytes(bool mixed, bool adjust, int d, int nb)
 {
-    const size_t cell = mixed ? 16 : 16;  // float4 or double2
+    const size_t cell = mixed ? 8 : 16;  // float2 or double2 cells
     const size_t h = adjust ? (mixed ? 4 : 8) : 0;
     return (size_t)d * nb * (cell + h);
 }
@@ -210,27 +210,6 @@ struct EventPair {
     cudaEvent_t a = nullptr, b = nullptr;
 };
 
-struct DevBuf {
-    void* ptr = nullptr;
-    size_t bytes = 0;
-    cudaError_t reserve(size_t n)
-    {
-        if (n <= bytes) return cudaSuccess;
-        if (ptr) cudaFree(ptr);
-        ptr = nullptr;
-        bytes = 0;
-        cudaError_t e = cudaMalloc(&ptr, n);
-        if (e == cudaSuccess) bytes = n;
-        return e;
-    }
-    void release()
-    {
-        if (ptr) cudaFree(ptr);
-        ptr = nullptr;
-        bytes = 0;
-    }
-};
-
 }  // namespace
 
 struct mcubes_ctx {
@@ -254,6 +233,8 @@ struct mcubes_ctx {
     RefineArgs rf{};
 
     DevBuf grid, hist, part, part_hist, state, range_out;
+
+    BatchEngine* engine = nullptr;  // batched path, created on first use
 
     bool timing = false;
     std::vector<EventPair> ev_sample, ev_refine;
@@ -390,6 +371,8 @@ mcubes_status mcubes_set_opts(mcubes_ctx* c, const mcubes_opts* o)
     if (!c || !o || !opts_valid(o)) return MCUBES_EINVAL;
     c->opts = *o;
     c->ready = false;
+    delete c->engine;  // the batched path's buffers depend on the options
+    c->engine = nullptr;
     return MCUBES_OK;
 }
 
@@ -404,6 +387,8 @@ mcubes_status mcubes_destroy(mcubes_ctx* c)
     c->part_hist.release();
     c->state.release();
     c->range_out.release();
+    delete c->engine;
+    c->engine = nullptr;
     recycle_events(c);
     for (auto& e : c->pool) {
         cudaEventDestroy(e.a);
@@ -496,15 +481,12 @@ mcubes_status mcubes_setup(mcubes_ctx* c, int id, const double* params, int npar
     a.cube_begin = 0;
     a.cube_end = (uint64_t)m;
     philox_round_keys(c->opts.seed, a.rk);
-    double jc = 1.0;
     for (int j = 0; j < d; ++j) {
         a.lo[j] = lo[j];
         a.scale[j] = hi[j] - lo[j];
-        jc *= (double)nb;
     }
-    a.jac_const = jc;
-    a.inv_g_2p33 = std::ldexp(1.0 / (double)g, -33);
-    a.inv_g_f = (float)(1.0 / (double)g);
+    a.phi_scale = std::ldexp(1.0 / ((double)g * nb), -33);
+    a.phi_scale_f = (float)(1.0 / ((double)g * nb));
     a.nb_f = (float)nb;
     a.fam = fp;
 
@@ -737,22 +719,34 @@ mcubes_status mcubes_timing_get(mcubes_ctx* c, double* sample_ms, int* sample_la
 
 mcubes_status mcubes_integrate_batch(mcubes_ctx* c, int n, const mcubes_request* reqs, mcubes_result* outs)
 {
-    // Sequential fallback until the persistent batched kernel lands: every
-    // request runs through the single-integral path with its own seed.
     if (!c || n < 0 || (n > 0 && (!reqs || !outs))) return MCUBES_EINVAL;
-    const uint64_t saved_seed = c->opts.seed;
+    if (n == 0) return MCUBES_OK;
+    if (n > 65535) return MCUBES_EINVAL;
+    int itcap = 1;
     for (int i = 0; i < n; ++i) {
-        const mcubes_request& r = reqs[i];
-        c->opts.seed = r.seed;
-        mcubes_status st = mcubes_integrate(c, r.integrand_id, r.params, r.nparams, r.d, r.lo, r.hi, r.ncall,
-                                            r.itmax, r.rel_tol, r.abs_tol, &outs[i]);
-        outs[i].status = st;
-        if (st == MCUBES_ECUDA || st == MCUBES_ENOMEM) {
-            c->opts.seed = saved_seed;
+        if (reqs[i].itmax < 1 || reqs[i].itmax > MCUBES_ITMAX_MAX) return MCUBES_EINVAL;
+        itcap = std::max(itcap, reqs[i].itmax);
+    }
+    MC_CHECK(c, cudaSetDevice(c->device));
+    if (!c->engine) c->engine = new (std::nothrow) BatchEngine(c->device, c->stream, c->num_sms, c->opts);
+    if (!c->engine) return MCUBES_ENOMEM;
+    BatchEngine& E = *c->engine;
+    MC_CHECK(c, E.reserve(std::max(n, E.capacity()), std::max(itcap, E.itcap())));
+    for (int i = 0; i < n; ++i) {
+        const mcubes_status st = E.admit(reqs[i], i);
+        if (st != MCUBES_OK) {
+            // nothing has run: drop what was admitted
+            std::vector<std::pair<long long, mcubes_result>> none;
+            delete c->engine;
+            c->engine = nullptr;
             return st;
         }
     }
-    c->opts.seed = saved_seed;
+    int ran = 1;
+    while (ran > 0) MC_CHECK(c, E.step(&ran));
+    std::vector<std::pair<long long, mcubes_result>> done;
+    E.finished(&done, true);
+    for (auto& kv : done) outs[kv.first] = kv.second;
     return MCUBES_OK;
 }
 

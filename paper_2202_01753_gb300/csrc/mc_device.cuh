@@ -72,6 +72,37 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 x, const uint32_t (&rk)[10]
     return x;
 }
 
+// The same generator with the round keys formed on the fly from the key
+// (for kernels whose key is per-integral data rather than a launch constant).
+__device__ __forceinline__ uint4 philox4x32_10_key(uint4 x, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t a0 = x.x * 0xD2511F53u, h0 = __umulhi(x.x, 0xD2511F53u);
+        const uint32_t a1 = x.z * 0xCD9E8D57u, h1 = __umulhi(x.z, 0xCD9E8D57u);
+        x = make_uint4(h1 ^ x.y ^ k0, a1, h0 ^ x.w ^ k1, a0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return x;
+}
+
+__device__ __forceinline__ uint4 sample_words(const VsArgs& a, uint4 ctr) { return philox4x32_10(ctr, a.rk); }
+
+// Register view of one batch integral for the per-sample code (the family
+// constants stay in shared memory).
+struct BatchView {
+    uint32_t d, nb, g, gmagic, key0, key1;
+    double phi_scale;
+    float phi_scale_f;
+    const FamParams& fam;
+};
+
+__device__ __forceinline__ uint4 sample_words(const BatchView& v, uint4 ctr)
+{
+    return philox4x32_10_key(ctr, v.key0, v.key1);
+}
+
 // ---------------------------------------------------------------------------
 // Exact position of one coordinate (Alg. 1 map step, Alg. 3 Get-Bin-ID).  The
 // sample sits at y = (c + u)/g on this axis, c the sub-cube digit and
@@ -106,18 +137,19 @@ __device__ __forceinline__ BinPos bin_pos(uint32_t w, uint32_t nb_c, uint32_t nb
     return b;
 }
 
-// phi in double: (r 2^33 + a_lo) * 2^-33 / g  (the numerator is exact below 2^53)
-__device__ __forceinline__ double bin_phi_f64(const BinPos& b, double inv_g_2p33)
+// phi scaled by `scale`: (r 2^33 + a_lo) * scale, with scale = 2^-33 / g for
+// phi itself (the numerator is exact below 2^53); the kernels fold 1/nb in.
+__device__ __forceinline__ double bin_phi_f64(const BinPos& b, double scale)
 {
     const uint64_t num = ((uint64_t)b.r << 33) | ((uint64_t)b.ahi << 32) | (uint64_t)b.alo;
-    return __ull2double_rn(num) * inv_g_2p33;
+    return __ull2double_rn(num) * scale;
 }
 
-// phi in single precision
-__device__ __forceinline__ float bin_phi_f32(const BinPos& b, float inv_g)
+// the same in single precision: (r + a_lo 2^-33) * scale, scale = 1/g for phi
+__device__ __forceinline__ float bin_phi_f32(const BinPos& b, float scale)
 {
     const float base = __uint2float_rn(b.r) + (b.ahi ? 0.5f : 0.0f);
-    return __fmul_rn(__fmaf_rn(__uint2float_rn(b.alo), 1.16415321826934814453125e-10f /*2^-33*/, base), inv_g);
+    return __fmul_rn(__fmaf_rn(__uint2float_rn(b.alo), 1.16415321826934814453125e-10f /*2^-33*/, base), scale);
 }
 
 // ---------------------------------------------------------------------------

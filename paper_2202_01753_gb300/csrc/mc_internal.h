@@ -18,6 +18,11 @@ constexpr int kItMax = MCUBES_ITMAX_MAX;
 constexpr int kVsThreads = 256;    // sampling block size (8 warps)
 constexpr int kRefineThreads = 512;
 
+// Shared-memory bytes per bin of the sampling kernels: a grid cell (left
+// edge, nb * width) in double or single precision, and a histogram entry.
+__host__ __device__ constexpr size_t cell_bytes(bool mixed) { return mixed ? 8 : 16; }
+__host__ __device__ constexpr size_t hist_bytes(bool mixed) { return mixed ? 4 : 8; }
+
 // Per-integral state kept on the device across iterations, so that the whole
 // iteration loop (sample -> refine -> weight -> converge) runs without the
 // host.  One instance per single-integral context.
@@ -57,12 +62,78 @@ struct VsArgs {
     uint32_t rk[10][2];       // Philox round keys (key + r * Weyl constants)
     double lo[kDMax];
     double scale[kDMax];      // hi - lo
-    double jac_const;         // nb^d
-    double inv_g_2p33;        // 2^-33 / g
-    float inv_g_f;            // 1/g
+    double phi_scale;         // 2^-33 / (g nb): bin numerator -> phi / nb
+    float phi_scale_f;        // 1 / (g nb)
     float nb_f;
     FamParams fam;
 };
+
+// ---------------------------------------------------------------------------
+// Batched iterations (many independent integrals per launch)
+// ---------------------------------------------------------------------------
+
+// One resident integral of a batch, as the batched kernels read it.
+struct BatchDesc {
+    uint32_t d, nb, g, gmagic;
+    uint32_t p, lanes;
+    uint32_t key0, key1;        // Philox key = the integral's own seed
+    int family, ita, itmax, pad;
+    uint64_t m;
+    double phi_scale;           // 2^-33 / (g nb)
+    float phi_scale_f;          // 1 / (g nb)
+    float pad2;
+    double lo[kDMax];
+    double scale[kDMax];
+    FamParams fam;
+    double* grid;               // [d][nb] edge high parts, then [d][nb] low parts
+    double* hist;               // [d][nb] histogram of the last adjusting iteration
+    double* hist_I;             // [itmax] iteration estimates
+    double* hist_V;             // [itmax] iteration variances
+    double rel_tol, abs_tol;
+};
+
+// Per-integral iteration state of a batch (device).
+struct BatchState {
+    uint32_t it;
+    int done, error, n, converged, pad;
+    double estimate, sigma, chi2_dof;
+};
+
+// A run of cubes [c0, c1) of one integral, sampled by one block.
+struct BatchSeg {
+    uint32_t slot;
+    uint32_t adjust;
+    uint64_t c0, c1;
+    uint64_t hist_off;          // element offset of the segment's partial histogram
+};
+
+struct BatchArgs {
+    const BatchDesc* desc;
+    const BatchState* st;
+    const BatchSeg* segs;
+    const uint32_t* blk_seg;    // block b samples segments [blk_seg[b], blk_seg[b+1])
+    double* seg_part;           // [segment][3] partial sums
+    void* seg_hist;             // partial histograms (float in mixed, double in fp64)
+};
+
+struct BatchRefineArgs {
+    const BatchDesc* desc;
+    BatchState* st;
+    const uint32_t* live;       // [capacity]: slot of live integral j
+    const uint32_t* live_seg;   // [capacity + 1]: live integral j owns segments [live_seg[j], live_seg[j+1])
+    const uint32_t* nlive;      // device scalar
+    const BatchSeg* segs;
+    const double* seg_part;
+    const void* seg_hist;
+    int hist_is_float;
+    double alpha;
+};
+
+cudaError_t launch_vsample_batch(bool mixed, const BatchArgs& a, int grid, size_t smem, cudaStream_t s);
+cudaError_t vsample_batch_occupancy(bool mixed, size_t smem, int* blocks_per_sm);
+cudaError_t launch_refine_batch(const BatchRefineArgs& a, int capacity, cudaStream_t s);
+cudaError_t launch_init_slots(const BatchDesc* desc, BatchState* st, const uint32_t* slots, int count,
+                              cudaStream_t s);
 
 struct RefineArgs {
     double* grid;             // [d][nb] edge high parts, updated in place by the rebin blocks

@@ -126,15 +126,12 @@ extern "C" mcubes_status mcubes_sample_range_noalloc(
         a.cube_begin = (uint64_t)cube_begin;
         a.cube_end = (uint64_t)cube_end;
         philox_round_keys(seed, a.rk);
-        double jc = 1.0;
         for (int j = 0; j < d; ++j) {
             a.lo[j] = lo[j];
             a.scale[j] = hi[j] - lo[j];
-            jc *= (double)nbins;
         }
-        a.jac_const = jc;
-        a.inv_g_2p33 = std::ldexp(1.0 / (double)g, -33);
-        a.inv_g_f = (float)(1.0 / (double)g);
+        a.phi_scale = std::ldexp(1.0 / ((double)g * nbins), -33);
+        a.phi_scale_f = (float)(1.0 / ((double)g * nbins));
         a.nb_f = (float)nbins;
         a.fam = fp;
 

@@ -1,6 +1,7 @@
 // vsample.cuh -- the sampling kernel (V-Sample / V-Sample-No-Adjust of
 // Alg. 3 in the paper), instantiated once per integrand family by the
-// vsample_<family>.cu translation units.
+// vsample_<family>.cu translation units, and the device pieces it shares with
+// the batched kernel (batch.cuh).
 //
 // Work layout.  A run of `lanes` consecutive threads of a warp owns one
 // sub-cube; lane l of the run draws samples l, l + lanes, ... of it.  With
@@ -8,12 +9,12 @@
 // whole cubes and its cube moments need no communication; larger p spreads a
 // cube over up to 32 lanes whose moments are merged by XOR shuffles.  Blocks
 // walk the cube range with a grid stride.  The bin grid of all axes is staged
-// in shared memory once per block as (left edge, width[, Jacobian factor])
-// cells in the integration box's coordinates.  In adjusting iterations every
-// sample adds F^2 to a per-block shared-memory histogram [d][nb], flushed to
-// global memory once at the end of the block: no per-sample global atomics.
-// Each block writes three double partials (sum of cube means, of their
-// variances, of |means|) which the refinement launch reduces in fixed order.
+// in shared memory once per block as (left edge, nb * width) cells in the
+// integration box's coordinates.  In adjusting iterations every sample adds
+// F^2 to a per-block shared-memory histogram [d][nb], flushed to global
+// memory once at the end of the block: no per-sample global atomics.  Each
+// block writes three double partials (sum of cube means, of their variances,
+// of |means|) which the refinement launch reduces in fixed order.
 #pragma once
 
 #include "mc_device.cuh"
@@ -23,21 +24,44 @@ namespace mc {
 template <bool MIXED> struct Prec;
 template <> struct Prec<false> {
     using R = double;
-    using Cell = double2;  // (x left, x width); Jacobian factor = width, times nb^d at the end
+    using Cell = double2;  // (x left edge, nb * x width): x = left + (nb*width)(phi/nb), J factor = nb*width
     using H = double;
 };
 template <> struct Prec<true> {
     using R = float;
-    using Cell = float4;   // (x left, x width, nb * x width, unused)
+    using Cell = float2;
     using H = float;
 };
 
+// Stages the grid of all axes into shared-memory cells and clears the
+// histogram.  grid/grid_lo: [d][nb] double-double right edges (unit cube);
+// lo/scale: the box's lower corner and hi - lo.
+template <bool MIXED, bool ADJ, class Arr>
+__device__ __forceinline__ void stage_grid(typename Prec<MIXED>::Cell* cells, typename Prec<MIXED>::H* hist,
+                                           const double* grid, const double* grid_lo, const Arr& lo,
+                                           const Arr& scale, uint32_t d, uint32_t nb)
+{
+    for (uint32_t i = threadIdx.x; i < d * nb; i += blockDim.x) {
+        const uint32_t j = i / nb, k = i - j * nb;
+        const DD right{grid[i], grid_lo[i]};
+        const DD left = k ? DD{grid[i - 1], grid_lo[i - 1]} : DD{0.0, 0.0};
+        const DD wd = dd_add(right, DD{-left.hi, -left.lo});
+        const double xl = lo[j] + scale[j] * left.hi;
+        const double xwn = scale[j] * (wd.hi + wd.lo) * (double)nb;
+        if constexpr (MIXED) cells[i] = make_float2((float)xl, (float)xwn);
+        else cells[i] = make_double2(xl, xwn);
+        if constexpr (ADJ) hist[i] = typename Prec<MIXED>::H(0);
+    }
+}
+
 // One sample: random words -> exact bin position -> map -> integrand.
-// Returns F = f(x) * J and leaves the flat histogram index of every axis in idx.
-template <int FAM, bool MIXED>
+// Returns F = f(x) * J and leaves the flat histogram index of every axis in
+// idx.  A provides d, nb, g, gmagic, phi_scale (2^-33/(g nb)), phi_scale_f
+// (1/(g nb)) and fam, and sample_words(a, counter) its Philox block.
+template <int FAM, bool MIXED, class A>
 __device__ __forceinline__ typename Prec<MIXED>::R
-sample_point(const VsArgs& a, const typename Prec<MIXED>::Cell* cells, uint32_t c, uint32_t s,
-             uint32_t it, const uint32_t (&nbc)[kDMax], uint32_t (&idx)[kDMax])
+sample_point(const A& a, const typename Prec<MIXED>::Cell* cells, uint32_t c, uint32_t s, uint32_t it,
+             const uint32_t (&nbc)[kDMax], uint32_t (&idx)[kDMax])
 {
     using R = typename Prec<MIXED>::R;
     using Fam = Family<FAM, R>;
@@ -46,7 +70,7 @@ sample_point(const VsArgs& a, const typename Prec<MIXED>::Cell* cells, uint32_t 
 #pragma unroll
     for (int b = 0; b < kDMax / 4; ++b) {
         if (4 * b < (int)d) {
-            const uint4 r = philox4x32_10(make_uint4(s, c, it, (uint32_t)b), a.rk);
+            const uint4 r = sample_words(a, make_uint4(s, c, it, (uint32_t)b));
             w[4 * b + 0] = r.x;
             w[4 * b + 1] = r.y;
             w[4 * b + 2] = r.z;
@@ -64,70 +88,50 @@ sample_point(const VsArgs& a, const typename Prec<MIXED>::Cell* cells, uint32_t 
             const auto cell = cells[flat];
             R x;
             if constexpr (MIXED) {
-                const float phi = bin_phi_f32(bp, a.inv_g_f);
-                x = fmaf(cell.y, phi, cell.x);
-                jac *= cell.z;
+                const float phin = bin_phi_f32(bp, a.phi_scale_f);   // phi / nb
+                x = fmaf(cell.y, phin, cell.x);
             } else {
-                const double phi = bin_phi_f64(bp, a.inv_g_2p33);
-                x = fma(cell.y, phi, cell.x);
-                jac *= cell.y;
+                const double phin = bin_phi_f64(bp, a.phi_scale);     // phi / nb
+                x = fma(cell.y, phin, cell.x);
             }
+            jac *= cell.y;
             Fam::add(fs, j, x, a.fam);
             idx[j] = flat;
         }
     }
-    R F = Fam::end(fs, d, a.fam) * jac;
-    if constexpr (!MIXED) F *= a.jac_const;
-    return F;
+    return Fam::end(fs, d, a.fam) * jac;
 }
 
-template <int FAM, bool MIXED, bool ADJ>
-__global__ void __launch_bounds__(kVsThreads)
-vsample_kernel(const __grid_constant__ VsArgs a)
+// Per-thread sums over the cubes a thread finishes: double, or a compensated
+// single-precision pair in the mixed path (no FP64 work per cube).
+struct CubeSums {
+    double I = 0.0, V = 0.0, A = 0.0;
+    DFloat fI{0.f, 0.f}, fV{0.f, 0.f}, fA{0.f, 0.f};
+    __device__ double vI() const { return I + fI.value(); }
+    __device__ double vV() const { return V + fV.value(); }
+    __device__ double vA() const { return A + fA.value(); }
+};
+
+// Samples cubes [cube_lo, cube_lo + ncubes) of one integral.  The block takes
+// groups of (blockDim / lanes) consecutive cubes: group0, group0 + gstride, ...
+template <int FAM, bool MIXED, bool ADJ, class A>
+__device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIXED>::Cell* cells,
+                                             typename Prec<MIXED>::H* hist, uint64_t cube_lo, uint64_t ncubes,
+                                             uint64_t group0, uint64_t gstride, uint32_t it, uint32_t lanes,
+                                             uint32_t p, CubeSums& acc)
 {
     using R = typename Prec<MIXED>::R;
-    using Cell = typename Prec<MIXED>::Cell;
     using HT = typename Prec<MIXED>::H;
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double red[3][kVsThreads / 32];
-
     const uint32_t d = a.d, nb = a.nb;
-    uint32_t it = a.it_fixed;
-    if (a.st != nullptr) {
-        const int done = *(volatile const int*)&a.st->done;
-        if (blockIdx.x == 0 && threadIdx.x == 0) a.st->active = done ? 0 : 1;
-        if (done) return;
-        it = *(volatile const uint32_t*)&a.st->it;
-    }
-
-    Cell* cells = reinterpret_cast<Cell*>(smem);
-    HT* hist = reinterpret_cast<HT*>(smem + sizeof(Cell) * d * nb);
-    for (uint32_t i = threadIdx.x; i < d * nb; i += blockDim.x) {
-        const uint32_t j = i / nb, k = i - j * nb;
-        const DD right{a.grid[i], a.grid_lo[i]};
-        const DD left = k ? DD{a.grid[i - 1], a.grid_lo[i - 1]} : DD{0.0, 0.0};
-        const DD wd = dd_add(right, DD{-left.hi, -left.lo});
-        const double xl = a.lo[j] + a.scale[j] * left.hi;
-        const double xw = a.scale[j] * (wd.hi + wd.lo);
-        if constexpr (MIXED) cells[i] = make_float4((float)xl, (float)xw, (float)(xw * (double)nb), 0.0f);
-        else cells[i] = make_double2(xl, xw);
-        if constexpr (ADJ) hist[i] = HT(0);
-    }
-    __syncthreads();
-
-    const uint32_t L = a.lanes;
+    const uint32_t L = lanes;
     const uint32_t seg_lane = threadIdx.x & (L - 1u);
-    const uint32_t cubes_per_round = blockDim.x / L;
-    const uint64_t ncubes = a.cube_end - a.cube_begin;
-    const uint64_t stride = (uint64_t)gridDim.x * cubes_per_round;
-
-    double accI = 0.0, accV = 0.0, accA = 0.0;
-    DFloat dfI{0.f, 0.f}, dfV{0.f, 0.f}, dfA{0.f, 0.f};
-
-    for (uint64_t base = (uint64_t)blockIdx.x * cubes_per_round; base < ncubes; base += stride) {
+    const uint32_t cubes_per_group = blockDim.x / L;
+    const R inv_p = R(1) / R(p);
+    const R inv_var_den = inv_p / R(p - 1);   // 1 / (p (p-1))
+    for (uint64_t base = group0 * cubes_per_group; base < ncubes; base += gstride * cubes_per_group) {
         const uint64_t ci = base + threadIdx.x / L;
         const bool valid = ci < ncubes;
-        const uint32_t c = (uint32_t)(a.cube_begin + (valid ? ci : 0));
+        const uint32_t c = (uint32_t)(cube_lo + (valid ? ci : 0));
         // sub-cube digits (axis 0 fastest), kept as nb * digit
         uint32_t nbc[kDMax];
         {
@@ -148,7 +152,7 @@ vsample_kernel(const __grid_constant__ VsArgs a)
         R K = R(0), S1 = R(0), S2 = R(0);
         uint32_t n = 0;
         if (valid) {
-            for (uint32_t s = seg_lane; s < a.p; s += L) {
+            for (uint32_t s = seg_lane; s < p; s += L) {
                 uint32_t idx[kDMax];
                 const R F = sample_point<FAM, MIXED>(a, cells, c, s, it, nbc, idx);
                 if (n == 0) K = F;
@@ -167,17 +171,16 @@ vsample_kernel(const __grid_constant__ VsArgs a)
         if (L == 1u) {
             if (valid) {
                 // UpdateVariance (Alg. 3): cube mean and the variance of that mean
-                const R pf = R(a.p);
-                const R mean = K + S1 / pf;
-                const R var = (S2 - S1 * S1 / pf) / (pf * (pf - R(1)));
+                const R mean = K + S1 * inv_p;
+                const R var = (S2 - S1 * S1 * inv_p) * inv_var_den;
                 if constexpr (MIXED) {
-                    dfI.add(mean);
-                    dfV.add(var);
-                    dfA.add(fabsf(mean));
+                    acc.fI.add(mean);
+                    acc.fV.add(var);
+                    acc.fA.add(fabsf(mean));
                 } else {
-                    accI += mean;
-                    accV += var;
-                    accA += fabs(mean);
+                    acc.I += mean;
+                    acc.V += var;
+                    acc.A += fabs(mean);
                 }
             }
         } else {
@@ -198,16 +201,18 @@ vsample_kernel(const __grid_constant__ VsArgs a)
                 cnt = tot;
             }
             if (valid && seg_lane == 0) {
-                const double var = M2 / (cnt * (cnt - 1.0));
-                accI += mean;
-                accV += var;
-                accA += fabs(mean);
+                acc.I += mean;
+                acc.V += M2 / (cnt * (cnt - 1.0));
+                acc.A += fabs(mean);
             }
         }
     }
+}
 
-    // block partials, reduced in a fixed order
-    double v0 = accI + dfI.value(), v1 = accV + dfV.value(), v2 = accA + dfA.value();
+// Fixed-order block sum of the three per-thread sums; thread 0 writes them.
+__device__ __forceinline__ void block_write_sums(const CubeSums& acc, double (*red)[kVsThreads / 32], double* out)
+{
+    double v0 = acc.vI(), v1 = acc.vV(), v2 = acc.vA();
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         v0 += __shfl_down_sync(0xffffffffu, v0, off);
@@ -228,11 +233,41 @@ vsample_kernel(const __grid_constant__ VsArgs a)
             s1 += red[1][w];
             s2 += red[2][w];
         }
-        a.part[3 * (size_t)blockIdx.x + 0] = s0;
-        a.part[3 * (size_t)blockIdx.x + 1] = s1;
-        a.part[3 * (size_t)blockIdx.x + 2] = s2;
+        out[0] = s0;
+        out[1] = s1;
+        out[2] = s2;
     }
+}
+
+template <int FAM, bool MIXED, bool ADJ>
+__global__ void __launch_bounds__(kVsThreads)
+vsample_kernel(const __grid_constant__ VsArgs a)
+{
+    using Cell = typename Prec<MIXED>::Cell;
+    using HT = typename Prec<MIXED>::H;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double red[3][kVsThreads / 32];
+
+    const uint32_t d = a.d, nb = a.nb;
+    uint32_t it = a.it_fixed;
+    if (a.st != nullptr) {
+        const int done = *(volatile const int*)&a.st->done;
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.st->active = done ? 0 : 1;
+        if (done) return;
+        it = *(volatile const uint32_t*)&a.st->it;
+    }
+
+    Cell* cells = reinterpret_cast<Cell*>(smem);
+    HT* hist = reinterpret_cast<HT*>(smem + cell_bytes(MIXED) * d * nb);
+    stage_grid<MIXED, ADJ>(cells, hist, a.grid, a.grid_lo, a.lo, a.scale, d, nb);
+    __syncthreads();
+
+    CubeSums acc;
+    sample_cubes<FAM, MIXED, ADJ>(a, cells, hist, a.cube_begin, a.cube_end - a.cube_begin, blockIdx.x, gridDim.x,
+                                  it, a.lanes, a.p, acc);
+    block_write_sums(acc, red, a.part + 3 * (size_t)blockIdx.x);
     if constexpr (ADJ) {
+        __syncthreads();
         HT* out = reinterpret_cast<HT*>(a.part_hist) + (size_t)blockIdx.x * d * nb;
         for (uint32_t i = threadIdx.x; i < d * nb; i += blockDim.x) out[i] = hist[i];
     }

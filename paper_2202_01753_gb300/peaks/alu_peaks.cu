@@ -67,7 +67,7 @@ int measure(int blocks_per_sm, int iters, double* fma_per_s, float* ms_out)
 extern "C" int mcpeaks_fma(int device, double* ffma_per_s, double* dfma_per_s, float* ms_f32, float* ms_f64)
 {
     if (cudaSetDevice(device) != cudaSuccess) return 3;
-    int r = measure<float>(8, 512, ffma_per_s, ms_f32);
+    int r = measure<float>(8, 2048, ffma_per_s, ms_f32);
     if (r) return r;
-    return measure<double>(8, 16, dfma_per_s, ms_f64);
+    return measure<double>(8, 64, dfma_per_s, ms_f64);
 }

@@ -1,0 +1,121 @@
+"""The batched path (mcubes_integrate_batch): many independent integrals
+iterated together by one persistent sampling launch and one refinement
+launch per iteration, replayed as a CUDA graph.
+
+Every integral draws the same Philox words as when it runs alone (its own
+seed and iteration index), so batch and solo results differ only in how the
+per-block partial sums are grouped: at rounding level in FP64, at the level
+of single-precision histogram sums in mixed precision, amplified mildly by
+the grid adaptation.  Tolerances below are those levels with margin.
+"""
+import numpy as np
+import pytest
+
+import closed_forms as CF
+import oracle
+from paper_2202_01753_gb300 import mcubes
+from paper_2202_01753_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _mix(n, seed, ncall_lo=1e4, ncall_hi=3e5, itmax=5, dmax=8):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ws = []
+    for i in range(n):
+        d = int(rng.integers(2, dmax + 1))
+        fam = int(rng.choice([W.F_GAUSS, W.F_CORNER, W.F_OSC]))
+        ncall = int(round(10 ** rng.uniform(np.log10(ncall_lo), np.log10(ncall_hi))))
+        ws.append(W.random_integral(rng, d, fam, ncall, itmax, seed=7000 + i))
+    return ws
+
+
+def _req(w):
+    return dict(fid=w.fid, params=w.params, lo=w.lo, hi=w.hi, ncall=w.ncall, itmax=w.itmax, rel_tol=w.rel_tol,
+                abs_tol=w.abs_tol, seed=w.seed)
+
+
+def _solo(make_ctx, w, precision):
+    ctx = make_ctx(seed=w.seed, precision=precision)
+    r = ctx.integrate(w.fid, w.params, w.lo, w.hi, w.ncall, w.itmax, w.rel_tol, w.abs_tol)
+    ctx.close()
+    return r
+
+
+@pytest.mark.parametrize("precision,rtol", [("fp64", 1e-10), ("mixed", 2e-4)])
+def test_batch_matches_solo(gpu_ctx_factory, precision, rtol):
+    ws = _mix(40, seed=11)
+    ctx = gpu_ctx_factory(precision=precision)
+    out = ctx.integrate_batch([_req(w) for w in ws])
+    ctx.close()
+    for w, b in zip(ws, out):
+        s = _solo(gpu_ctx_factory, w, precision)
+        assert b["status"] == s["status"] == mcubes.ENOCONV
+        assert b["iterations"] == s["iterations"] == w.itmax
+        assert (b["g"], b["m"], b["p"]) == (s["g"], s["m"], s["p"])
+        scale = max(abs(s["estimate"]), s["sigma"])
+        assert abs(b["estimate"] - s["estimate"]) <= rtol * scale, (w.name, b["estimate"], s["estimate"])
+        assert b["sigma"] == pytest.approx(s["sigma"], rel=rtol * 10)
+
+
+def test_batch_fp64_against_oracle(gpu_ctx_factory):
+    ws = _mix(6, seed=12, ncall_hi=1e5, itmax=4)
+    ctx = gpu_ctx_factory()
+    out = ctx.integrate_batch([_req(w) for w in ws])
+    ctx.close()
+    for w, b in zip(ws, out):
+        o = oracle.integrate(w.fid, w.params, w.lo, w.hi, w.ncall, w.itmax, seed=w.seed)
+        assert b["iterations"] == o["iterations"]
+        assert b["estimate"] == pytest.approx(o["estimate"], rel=1e-10)
+        assert b["sigma"] == pytest.approx(o["sigma"], rel=1e-9)
+
+
+def test_batch_early_convergence_per_integral(gpu_ctx_factory):
+    ws = _mix(30, seed=13, ncall_lo=3e4, ncall_hi=3e5, itmax=12)
+    for i, w in enumerate(ws):
+        w.rel_tol = [1e-2, 3e-3, 1e-3][i % 3]
+    ctx = gpu_ctx_factory()
+    out = ctx.integrate_batch([_req(w) for w in ws])
+    ctx.close()
+    its = set()
+    for w, b in zip(ws, out):
+        s = _solo(gpu_ctx_factory, w, "fp64")
+        assert b["iterations"] == s["iterations"]
+        assert b["converged"] == s["converged"]
+        assert b["estimate"] == pytest.approx(s["estimate"], rel=1e-10)
+        its.add(b["iterations"])
+        if b["converged"]:
+            assert b["sigma"] <= w.rel_tol * abs(b["estimate"])
+            assert abs(b["estimate"] - CF.exact(w)) < 6 * b["sigma"]
+    assert len(its) > 1   # integrals left the batch at different iterations
+
+
+def test_batch_rejects_invalid_request(gpu_ctx_factory):
+    ws = _mix(3, seed=14)
+    reqs = [_req(w) for w in ws]
+    reqs[1]["lo"] = reqs[1]["hi"]
+    ctx = gpu_ctx_factory()
+    with pytest.raises(mcubes.McubesError) as e:
+        ctx.integrate_batch(reqs)
+    assert e.value.status == mcubes.EINVAL
+    # the context is still usable
+    out = ctx.integrate_batch([_req(w) for w in ws])
+    assert all(r["status"] == mcubes.ENOCONV for r in out)
+    ctx.close()
+
+
+def test_batch_4096_uneven_integrals(gpu_ctx_factory):
+    """The batched configuration's shape (4096 integrals, d in 2..10, three
+    families, ncall log-uniform) scaled to 1e4..1e5 calls: every integral
+    finishes and agrees with its closed form."""
+    ws = W.batch4096(n=4096, itmax=4)
+    ws = [w.scaled(min(w.ncall, 100_000)) for w in ws]
+    ctx = gpu_ctx_factory(precision="mixed")
+    out = ctx.integrate_batch([_req(w) for w in ws])
+    ctx.close()
+    z = []
+    for w, b in zip(ws, out):
+        assert b["status"] == mcubes.ENOCONV and b["iterations"] == 4
+        z.append((b["estimate"] - CF.exact(w)) / b["sigma"])
+    z = np.abs(np.array(z))
+    assert np.mean(z < 3) > 0.97

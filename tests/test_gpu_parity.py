@@ -23,6 +23,10 @@ pytestmark = pytest.mark.gpu
 
 RTOL_I = 1e-12
 RTOL_V = 1e-12
+# relative difference between the kernel's and the oracle's F of one sample
+# in high dimension (d Jacobian factors, transcendental functions of sums,
+# CUDA's vs glibc's libm): the noise level of the sensitivity experiments
+F_NOISE = 1e-14
 
 
 def oracle_run(w, **kw):
@@ -92,12 +96,14 @@ def test_paper_suite(gpu_ctx_factory, name, d, ncall):
     if name == "fB":
         # 9-d peak: every rebin amplifies rounding in the narrow peak bins, and
         # each sample's F^2 lands on all nine axes, so the oracle's own final
-        # histogram moves by ~5e-11 under 1e-15 perturbations.  Tolerance: 10x
-        # the spread measured here (the estimates keep the 1e-12 bar).
+        # histogram moves by ~5e-10 when every histogram is perturbed at the
+        # level by which the kernel's F differs from the oracle's (1e-14: nine
+        # Jacobian factors, an exp of a nine-term sum, another libm).
+        # Tolerance: 10x the spread measured here (estimates keep 1e-12).
         rng = np.random.default_rng(2)
         spread = np.zeros_like(o["hist"])
         for _ in range(3):
-            spread = np.maximum(spread, np.abs(_oracle_last_hist_with_noise(w, 1e-15, rng) - o["hist"]))
+            spread = np.maximum(spread, np.abs(_oracle_last_hist_with_noise(w, F_NOISE, rng) - o["hist"]))
         hist_tol = np.maximum(10 * spread, 1e-12 * np.abs(o["hist"]))
     assert_parity(w, o, g, vtol=1e-10 if w.fid == W.F_OSC else RTOL_V, hist_tol=hist_tol)
 
@@ -135,15 +141,16 @@ def _oracle_last_hist_with_noise(w, noise, rng):
 def test_ill_conditioned_adaptation_within_measured_sensitivity(gpu_ctx_factory):
     """f_B (9-d peak) with only 2e5 calls: each adjusting iteration amplifies
     rounding-level differences in the histogram about six-fold, so after five
-    iterations the oracle itself is only good to ~1e-12 relative.  The
+    iterations the oracle itself is only good to ~1e-11 relative.  The
     tolerance here is derived from that measured sensitivity: the GPU must
-    agree within 10x the spread the oracle shows under 1e-15 relative noise."""
+    agree within 10x the spread the oracle shows when its histograms are
+    perturbed at the kernel's per-sample difference from it (F_NOISE)."""
     w = W.suite("fB", None, ncall=200_000, itmax=5, seed=7)
     base = _oracle_trace_with_noise(w, 0.0, None)
     rng = np.random.default_rng(1)
     spread = np.zeros(w.itmax)
     for _ in range(4):
-        spread = np.maximum(spread, np.abs(_oracle_trace_with_noise(w, 1e-15, rng) - base))
+        spread = np.maximum(spread, np.abs(_oracle_trace_with_noise(w, F_NOISE, rng) - base))
     g = gpu_run(gpu_ctx_factory, w)
     tol = np.maximum(10 * spread, RTOL_I * np.abs(base))
     assert np.all(np.abs(g["I"] - base) <= tol), (np.abs(g["I"] - base), tol)

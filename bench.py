@@ -39,8 +39,12 @@ from paper_2202_01753_gb300 import workloads as W  # noqa: E402
 # FP64 pipe (2 DFMA/clk/SM on GB300, ncu peak_sustained); "issue": issued warp
 # instructions per 32 samples against 4 issue slots/clk/SM.
 ROOFLINE_UNITS = {
-    ("cosmo6", "fp64"): {"kind": "fp64", "per_sample": 399.9,
+    ("cosmo6", "fp64"): {"kind": "fp64", "per_sample": 366.1,
                          "source": "profiles/vsample_cosmo6_fp64.md"},
+    ("corner8", "mixed"): {"kind": "issue", "per_sample": 745.0,
+                           "source": "profiles/vsample_corner8_mixed.md"},
+    ("osc10", "mixed"): {"kind": "issue", "per_sample": 793.5,
+                         "source": "profiles/vsample_osc10_mixed.md"},
 }
 DFMA_PER_CLK_PER_SM = 2.0
 ISSUE_PER_CLK_PER_SM = 4.0

@@ -41,7 +41,7 @@ from paper_2202_01753_gb300 import workloads as W  # noqa: E402
 ROOFLINE_UNITS = {
     ("cosmo6", "fp64"): {"kind": "fp64", "per_sample": 366.1,
                          "source": "profiles/vsample_cosmo6_fp64.md"},
-    ("corner8", "mixed"): {"kind": "issue", "per_sample": 745.0,
+    ("corner8", "mixed"): {"kind": "issue", "per_sample": 684.4,
                            "source": "profiles/vsample_corner8_mixed.md"},
     ("osc10", "mixed"): {"kind": "issue", "per_sample": 793.5,
                          "source": "profiles/vsample_osc10_mixed.md"},

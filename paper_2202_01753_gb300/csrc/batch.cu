@@ -18,19 +18,53 @@
 namespace mc {
 bool integrand_prepare(int id, const double* p, int np, int d, FamParams* out);
 bool geometry(int d, long long ncall, long long g_override, int nb, long long* g, long long* m, long long* p);
-cudaError_t launch_vsample_batch_fp64(const BatchArgs& a, int grid, size_t smem, cudaStream_t s);
-cudaError_t launch_vsample_batch_mixed(const BatchArgs& a, int grid, size_t smem, cudaStream_t s);
-cudaError_t vsample_batch_occupancy_fp64(size_t smem, int* blocks);
-cudaError_t vsample_batch_occupancy_mixed(size_t smem, int* blocks);
+cudaError_t launch_vsample_batch_const(bool, int, const BatchArgs&, int, size_t, cudaStream_t);
+cudaError_t vsample_batch_occupancy_const(bool, int, size_t, int*);
+cudaError_t launch_vsample_batch_gauss(bool, int, const BatchArgs&, int, size_t, cudaStream_t);
+cudaError_t vsample_batch_occupancy_gauss(bool, int, size_t, int*);
+cudaError_t launch_vsample_batch_corner(bool, int, const BatchArgs&, int, size_t, cudaStream_t);
+cudaError_t vsample_batch_occupancy_corner(bool, int, size_t, int*);
+cudaError_t launch_vsample_batch_osc(bool, int, const BatchArgs&, int, size_t, cudaStream_t);
+cudaError_t vsample_batch_occupancy_osc(bool, int, size_t, int*);
+cudaError_t launch_vsample_batch_prodpeak(bool, int, const BatchArgs&, int, size_t, cudaStream_t);
+cudaError_t vsample_batch_occupancy_prodpeak(bool, int, size_t, int*);
+cudaError_t launch_vsample_batch_c0(bool, int, const BatchArgs&, int, size_t, cudaStream_t);
+cudaError_t vsample_batch_occupancy_c0(bool, int, size_t, int*);
+cudaError_t launch_vsample_batch_discont(bool, int, const BatchArgs&, int, size_t, cudaStream_t);
+cudaError_t vsample_batch_occupancy_discont(bool, int, size_t, int*);
+cudaError_t launch_vsample_batch_cosmo6(bool, int, const BatchArgs&, int, size_t, cudaStream_t);
+cudaError_t vsample_batch_occupancy_cosmo6(bool, int, size_t, int*);
 
-cudaError_t launch_vsample_batch(bool mixed, const BatchArgs& a, int grid, size_t smem, cudaStream_t s)
+cudaError_t launch_vsample_batch(int cls, bool mixed, const BatchArgs& a, int grid, size_t smem, cudaStream_t s)
 {
-    return mixed ? launch_vsample_batch_mixed(a, grid, smem, s) : launch_vsample_batch_fp64(a, grid, smem, s);
+    const int nb4 = cls % 3 + 1;
+    switch (cls / 3) {
+    case MCUBES_F_CONST: return launch_vsample_batch_const(mixed, nb4, a, grid, smem, s);
+    case MCUBES_F_GAUSS: return launch_vsample_batch_gauss(mixed, nb4, a, grid, smem, s);
+    case MCUBES_F_CORNER: return launch_vsample_batch_corner(mixed, nb4, a, grid, smem, s);
+    case MCUBES_F_OSC: return launch_vsample_batch_osc(mixed, nb4, a, grid, smem, s);
+    case MCUBES_F_PRODPEAK: return launch_vsample_batch_prodpeak(mixed, nb4, a, grid, smem, s);
+    case MCUBES_F_C0: return launch_vsample_batch_c0(mixed, nb4, a, grid, smem, s);
+    case MCUBES_F_DISCONT: return launch_vsample_batch_discont(mixed, nb4, a, grid, smem, s);
+    case MCUBES_F_COSMO6: return launch_vsample_batch_cosmo6(mixed, nb4, a, grid, smem, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
-cudaError_t vsample_batch_occupancy(bool mixed, size_t smem, int* blocks)
+cudaError_t vsample_batch_occupancy(int cls, bool mixed, size_t smem, int* blocks)
 {
-    return mixed ? vsample_batch_occupancy_mixed(smem, blocks) : vsample_batch_occupancy_fp64(smem, blocks);
+    const int nb4 = cls % 3 + 1;
+    switch (cls / 3) {
+    case MCUBES_F_CONST: return vsample_batch_occupancy_const(mixed, nb4, smem, blocks);
+    case MCUBES_F_GAUSS: return vsample_batch_occupancy_gauss(mixed, nb4, smem, blocks);
+    case MCUBES_F_CORNER: return vsample_batch_occupancy_corner(mixed, nb4, smem, blocks);
+    case MCUBES_F_OSC: return vsample_batch_occupancy_osc(mixed, nb4, smem, blocks);
+    case MCUBES_F_PRODPEAK: return vsample_batch_occupancy_prodpeak(mixed, nb4, smem, blocks);
+    case MCUBES_F_C0: return vsample_batch_occupancy_c0(mixed, nb4, smem, blocks);
+    case MCUBES_F_DISCONT: return vsample_batch_occupancy_discont(mixed, nb4, smem, blocks);
+    case MCUBES_F_COSMO6: return vsample_batch_occupancy_cosmo6(mixed, nb4, smem, blocks);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 namespace {
@@ -136,38 +170,45 @@ void BatchEngine::release()
     capacity_ = 0;
 }
 
-size_t BatchEngine::smem_bytes() const
+size_t BatchEngine::smem_bytes(int cls) const
 {
-    return (size_t)kDMax * opts_.nbins * (cell_bytes(mixed_) + hist_bytes(mixed_));
+    const int nb4 = cls % 3 + 1;
+    return (size_t)4 * nb4 * opts_.nbins * (cell_bytes(mixed_) + hist_bytes(mixed_));
 }
+
+int BatchEngine::class_blocks(int cls) const { return std::max(1, std::min(tuned_bps_, occ_[cls])) * num_sms_; }
 
 cudaError_t BatchEngine::reserve(int capacity, int itcap)
 {
     if (capacity <= capacity_ && itcap <= itcap_) return cudaSuccess;
     release();
     const int nb = opts_.nbins;
-    int occ = 0;
-    cudaError_t e = vsample_batch_occupancy(mixed_, smem_bytes(), &occ);
-    if (e != cudaSuccess) return e;
-    if (occ < 1) return cudaErrorInvalidConfiguration;
-    occ_max_ = occ;
-    const int bmax = occ * num_sms_;
-    const size_t segmax = (size_t)capacity + bmax + 1;
+    cudaError_t e;
+    int occ_max = 1;
+    for (int c = 0; c < kNumClasses; ++c) {
+        occ_[c] = 0;
+        if (c / 3 == MCUBES_F_COSMO6 && c % 3 != 1) continue;  // six axes only
+        if ((e = vsample_batch_occupancy(c, mixed_, smem_bytes(c), &occ_[c]))) return e;
+        occ_max = std::max(occ_max, occ_[c]);
+    }
+    bmax_ = occ_max * num_sms_;
+    const size_t segmax = (size_t)capacity + (size_t)kNumClasses * bmax_ + 1;
     const size_t grid_stride = 2 * (size_t)kDMax * nb, hist_stride = (size_t)kDMax * nb;
     const size_t elem = mixed_ ? sizeof(float) : sizeof(double);
-    if ((e = desc_.reserve(sizeof(BatchDesc) * capacity)) ||
-        (e = st_.reserve(sizeof(BatchState) * capacity)) ||
+    const size_t table = (size_t)kNumClasses * (bmax_ + 1);
+    if ((e = desc_.reserve(sizeof(BatchDesc) * capacity)) || (e = st_.reserve(sizeof(BatchState) * capacity)) ||
         (e = grids_.reserve(sizeof(double) * grid_stride * capacity)) ||
         (e = hists_.reserve(sizeof(double) * hist_stride * capacity)) ||
         (e = histories_.reserve(sizeof(double) * 2 * (size_t)itcap * capacity)) ||
-        (e = segs_.reserve(sizeof(BatchSeg) * segmax)) || (e = blk_seg_.reserve(sizeof(uint32_t) * (bmax + 1))) ||
+        (e = segs_.reserve(sizeof(BatchSeg) * segmax)) || (e = blk_seg_.reserve(sizeof(uint32_t) * table)) ||
         (e = live_.reserve(sizeof(uint32_t) * capacity)) ||
         (e = live_seg_.reserve(sizeof(uint32_t) * (capacity + 1))) || (e = nlive_.reserve(sizeof(uint32_t))) ||
         (e = seg_part_.reserve(sizeof(double) * 3 * segmax)) ||
-        (e = seg_hist_.reserve(elem * hist_stride * segmax)) || (e = admit_slots_.reserve(sizeof(uint32_t) * capacity)))
+        (e = seg_hist_.reserve(elem * hist_stride * segmax)) ||
+        (e = admit_slots_.reserve(sizeof(uint32_t) * capacity)))
         return e;
     if ((e = cudaHostAlloc((void**)&h_segs_, sizeof(BatchSeg) * segmax, cudaHostAllocDefault)) ||
-        (e = cudaHostAlloc((void**)&h_small_, sizeof(uint32_t) * (3 * (size_t)capacity + bmax + 8),
+        (e = cudaHostAlloc((void**)&h_small_, sizeof(uint32_t) * (table + 2 * (size_t)capacity + 8),
                            cudaHostAllocDefault)) ||
         (e = cudaHostAlloc((void**)&h_states_, sizeof(BatchState) * capacity, cudaHostAllocDefault)))
         return e;
@@ -183,7 +224,7 @@ cudaError_t BatchEngine::reserve(int capacity, int itcap)
 
 int BatchEngine::choose_lanes(long long p) const
 {
-    if (opts_.lanes_per_cube > 0) return std::min<long long>(opts_.lanes_per_cube, std::max<long long>(p, 1));
+    if (opts_.lanes_per_cube > 0) return (int)std::min<long long>(opts_.lanes_per_cube, std::max<long long>(p, 1));
     int L = 1;
     while (L < 32 && 2 * L <= p && p / L > lanes_cap_) L *= 2;
     return L;
@@ -201,6 +242,7 @@ mcubes_status BatchEngine::admit(const mcubes_request& r, long long tag, int* sl
         if (!std::isfinite(r.lo[j]) || !std::isfinite(r.hi[j]) || !(r.lo[j] < r.hi[j])) return MCUBES_EINVAL;
     long long g, m, p;
     if (!geometry(d, r.ncall, opts_.g_override, nb, &g, &m, &p)) return MCUBES_EINVAL;
+    if (occ_[batch_class(r.integrand_id, d)] < 1) return MCUBES_EINVAL;
     if (free_.empty()) return MCUBES_ENOMEM;
     const int slot = free_.back();
     free_.pop_back();
@@ -267,70 +309,98 @@ cudaError_t BatchEngine::flush_admissions()
     return e;
 }
 
-// Lays the live integrals' samples end to end and cuts the line into
-// `blocks` equal chunks; cube c of an integral goes to the chunk holding its
-// first sample.  Writes the segment list (ordered by block and, within the
-// whole list, by live integral), the block and live-integral offsets.
-void BatchEngine::partition(const std::vector<int>& live, int blocks, int* nseg_out)
+void BatchEngine::live_slots(std::vector<int>* live, unsigned* class_mask) const
 {
-    double total = 0.0;
-    for (int s : live) total += slots_[s].work;
-    const double chunk = total / blocks;
-    uint32_t* blk_seg = h_small_;
-    uint32_t* live_slot = h_small_ + blocks + 1;
+    live->clear();
+    *class_mask = 0;
+    std::vector<int> by_class[kNumClasses];
+    for (int s = 0; s < capacity_; ++s) {
+        const Slot& S = slots_[s];
+        if (S.used && !S.finished && S.it < hdesc_[s].itmax)
+            by_class[batch_class(hdesc_[s].family, (int)hdesc_[s].d)].push_back(s);
+    }
+    for (int c = 0; c < kNumClasses; ++c) {
+        if (by_class[c].empty()) continue;
+        *class_mask |= 1u << c;
+        live->insert(live->end(), by_class[c].begin(), by_class[c].end());
+    }
+}
+
+// For every class, lays its live integrals' samples end to end and cuts the
+// line into class_blocks(class) equal chunks; cube c of an integral goes to
+// the chunk holding its first sample.  Writes the segment list (class by
+// class, then block by block), every class's block table (a fixed region of
+// bmax_+1 entries per class; classes without work get empty tables) and the
+// live integrals' segment offsets.
+void BatchEngine::partition(const std::vector<int>& live, int* nseg_out)
+{
+    uint32_t* table = h_small_;
+    const size_t table_n = (size_t)kNumClasses * (bmax_ + 1);
+    uint32_t* live_slot = h_small_ + table_n;
     uint32_t* live_seg = live_slot + capacity_;
+    std::memset(table, 0, sizeof(uint32_t) * table_n);
     int nseg = 0;
     size_t hist_off = 0;
-    double start = 0.0;  // first sample of the current integral on the line
-    int b = 0;
-    blk_seg[0] = 0;
-    for (size_t j = 0; j < live.size(); ++j) {
-        const int s = live[j];
-        const Slot& S = slots_[s];
-        live_slot[j] = (uint32_t)s;
-        live_seg[j] = (uint32_t)nseg;
-        const bool adjust = S.it < hdesc_[s].ita;
-        const double p = (double)S.p;
-        uint64_t c = 0;
-        while (c < (uint64_t)S.m) {
-            // last cube whose first sample lies in chunk b
-            const double chunk_end = (b + 1 == blocks) ? 1e300 : (b + 1) * chunk;
-            double cend_d = std::ceil((chunk_end - start) / p);
-            uint64_t cend = cend_d >= (double)S.m ? (uint64_t)S.m : (uint64_t)std::max(cend_d, 0.0);
-            if (cend > c) {
-                BatchSeg& g = h_segs_[nseg++];
-                g.slot = (uint32_t)s;
-                g.adjust = adjust ? 1u : 0u;
-                g.c0 = c;
-                g.c1 = cend;
-                g.hist_off = hist_off;
-                if (adjust) hist_off += (size_t)hdesc_[s].d * hdesc_[s].nb;
-                c = cend;
+    size_t j = 0;
+    while (j < live.size()) {
+        const int cls = batch_class(hdesc_[live[j]].family, (int)hdesc_[live[j]].d);
+        size_t j1 = j;
+        double total = 0.0;
+        while (j1 < live.size() && batch_class(hdesc_[live[j1]].family, (int)hdesc_[live[j1]].d) == cls)
+            total += slots_[live[j1++]].work;
+        const int blocks = class_blocks(cls);
+        uint32_t* blk_seg = table + (size_t)cls * (bmax_ + 1);
+        const double chunk = total / blocks;
+        double start = 0.0;  // first sample of the current integral on the class's line
+        int b = 0;
+        blk_seg[0] = (uint32_t)nseg;
+        for (; j < j1; ++j) {
+            const int s = live[j];
+            const Slot& S = slots_[s];
+            live_slot[j] = (uint32_t)s;
+            live_seg[j] = (uint32_t)nseg;
+            const bool adjust = S.it < hdesc_[s].ita;
+            const double p = (double)S.p;
+            uint64_t c = 0;
+            while (c < (uint64_t)S.m) {
+                const double chunk_end = (b + 1 == blocks) ? 1e300 : (b + 1) * chunk;
+                const double cend_d = std::ceil((chunk_end - start) / p);
+                const uint64_t cend =
+                    cend_d >= (double)S.m ? (uint64_t)S.m : (uint64_t)std::max(cend_d, 0.0);
+                if (cend > c) {
+                    BatchSeg& g = h_segs_[nseg++];
+                    g.slot = (uint32_t)s;
+                    g.adjust = adjust ? 1u : 0u;
+                    g.c0 = c;
+                    g.c1 = cend;
+                    g.perm_k = cube_permutation(cend - c);
+                    g.hist_off = hist_off;
+                    if (adjust) hist_off += (size_t)hdesc_[s].d * hdesc_[s].nb;
+                    c = cend;
+                }
+                if (c < (uint64_t)S.m) blk_seg[++b] = (uint32_t)nseg;  // block b is full
             }
-            if (c < (uint64_t)S.m) {
-                blk_seg[++b] = (uint32_t)nseg;  // block b is full
-            }
+            start += S.work;
         }
-        start += S.work;
+        while (b < blocks) blk_seg[++b] = (uint32_t)nseg;
     }
-    while (b < blocks) blk_seg[++b] = (uint32_t)nseg;
     live_seg[live.size()] = (uint32_t)nseg;
     *nseg_out = nseg;
 }
 
-cudaError_t BatchEngine::upload_partition(const std::vector<int>& live, int blocks, int nseg)
+cudaError_t BatchEngine::upload_partition(const std::vector<int>& live, int nseg)
 {
     cudaError_t e;
-    const uint32_t* blk_seg = h_small_;
-    const uint32_t* live_slot = h_small_ + blocks + 1;
+    const size_t table_n = (size_t)kNumClasses * (bmax_ + 1);
+    const uint32_t* live_slot = h_small_ + table_n;
     const uint32_t* live_seg = live_slot + capacity_;
-    uint32_t* nl = h_small_ + blocks + 1 + 2 * (size_t)capacity_ + 1;
+    uint32_t* nl = h_small_ + table_n + 2 * (size_t)capacity_ + 1;
     *nl = (uint32_t)live.size();
-    if ((e = cudaMemcpyAsync(segs_.ptr, h_segs_, sizeof(BatchSeg) * nseg, cudaMemcpyHostToDevice, stream_)) ||
-        (e = cudaMemcpyAsync(blk_seg_.ptr, blk_seg, sizeof(uint32_t) * (blocks + 1), cudaMemcpyHostToDevice,
+    if ((e = cudaMemcpyAsync(segs_.ptr, h_segs_, sizeof(BatchSeg) * std::max(nseg, 1), cudaMemcpyHostToDevice,
                              stream_)) ||
-        (e = cudaMemcpyAsync(live_.ptr, live_slot, sizeof(uint32_t) * live.size(), cudaMemcpyHostToDevice,
-                             stream_)) ||
+        (e = cudaMemcpyAsync(blk_seg_.ptr, h_small_, sizeof(uint32_t) * table_n, cudaMemcpyHostToDevice, stream_)) ||
+        (e = cudaMemcpyAsync(live_.ptr, live_slot, sizeof(uint32_t) * std::max<size_t>(live.size(), 1),
+                             cudaMemcpyHostToDevice, stream_)) ||
         (e = cudaMemcpyAsync(live_seg_.ptr, live_seg, sizeof(uint32_t) * (live.size() + 1),
                              cudaMemcpyHostToDevice, stream_)) ||
         (e = cudaMemcpyAsync(nlive_.ptr, nl, sizeof(uint32_t), cudaMemcpyHostToDevice, stream_)))
@@ -338,13 +408,13 @@ cudaError_t BatchEngine::upload_partition(const std::vector<int>& live, int bloc
     return cudaSuccess;
 }
 
-BatchArgs BatchEngine::sample_args() const
+BatchArgs BatchEngine::sample_args(int cls) const
 {
     BatchArgs a;
     a.desc = (const BatchDesc*)desc_.ptr;
     a.st = (const BatchState*)st_.ptr;
     a.segs = (const BatchSeg*)segs_.ptr;
-    a.blk_seg = (const uint32_t*)blk_seg_.ptr;
+    a.blk_seg = (const uint32_t*)blk_seg_.ptr + (size_t)cls * (bmax_ + 1);
     a.seg_part = (double*)seg_part_.ptr;
     a.seg_hist = seg_hist_.ptr;
     return a;
@@ -366,53 +436,57 @@ BatchRefineArgs BatchEngine::refine_args() const
     return r;
 }
 
-cudaError_t BatchEngine::enqueue_iteration(int blocks)
+cudaError_t BatchEngine::enqueue_iteration(unsigned mask)
 {
-    cudaError_t e = launch_vsample_batch(mixed_, sample_args(), blocks, smem_bytes(), stream_);
-    if (e) return e;
+    for (int c = 0; c < kNumClasses; ++c) {
+        if (!(mask >> c & 1u)) continue;
+        cudaError_t e = launch_vsample_batch(c, mixed_, sample_args(c), class_blocks(c), smem_bytes(c), stream_);
+        if (e) return e;
+    }
     return launch_refine_batch(refine_args(), capacity_, stream_);
 }
 
-cudaError_t BatchEngine::capture(int blocks)
+// One iteration as a CUDA graph: the sampling kernels of the classes in the
+// mask, then the refinement.  Re-captured only when a class appears that
+// the graph does not launch, or the launch shape changes.
+cudaError_t BatchEngine::capture(unsigned mask)
 {
-    if (exec_ && graph_blocks_ == blocks) return cudaSuccess;
+    if (exec_ && (mask & ~graph_mask_) == 0 && graph_bps_ == tuned_bps_) return cudaSuccess;
+    mask |= graph_mask_;
     if (exec_) cudaGraphExecDestroy(exec_);
     if (graph_) cudaGraphDestroy(graph_);
     exec_ = nullptr;
     graph_ = nullptr;
+    graph_mask_ = 0;
     if (stream_ == nullptr) return cudaSuccess;  // the legacy stream cannot be captured: launch directly
     cudaError_t e = cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal);
     if (e) return e;
-    cudaError_t le = enqueue_iteration(blocks);
+    cudaError_t le = enqueue_iteration(mask);
     e = cudaStreamEndCapture(stream_, &graph_);
     if (le) return le;
     if (e) return e;
-    e = cudaGraphInstantiate(&exec_, graph_, 0);
-    if (e) return e;
-    graph_blocks_ = blocks;
+    if ((e = cudaGraphInstantiate(&exec_, graph_, 0))) return e;
+    graph_mask_ = mask;
+    graph_bps_ = tuned_bps_;
     return cudaSuccess;
 }
 
-void BatchEngine::live_slots(std::vector<int>* live) const
-{
-    live->clear();
-    for (int s = 0; s < capacity_; ++s) {
-        const Slot& S = slots_[s];
-        if (S.used && !S.finished && S.it < hdesc_[s].itmax) live->push_back(s);
-    }
-}
-
-// Picks the resident sampling blocks per SM (and the samples-per-thread cap
-// that sets lanes per cube) by timing sampling-only launches of this batch's
-// first iteration; the choice is kept for the life of the engine.
-cudaError_t BatchEngine::autotune(const std::vector<int>& live)
+// Picks the resident sampling blocks per SM (capped by each class's
+// occupancy) and the samples-per-thread cap that sets lanes per cube, by
+// timing sampling-only launches of a subset of this batch's first
+// iteration; the choice is kept for the life of the engine.
+cudaError_t BatchEngine::autotune(const std::vector<int>& live, unsigned mask)
 {
     if (tuned_) return cudaSuccess;
+    int occ_hi = 1;
+    for (int c = 0; c < kNumClasses; ++c)
+        if (mask >> c & 1u) occ_hi = std::max(occ_hi, occ_[c]);
     std::vector<int> bps_list;
-    if (opts_.blocks_per_sm > 0) bps_list.push_back(std::min(opts_.blocks_per_sm, occ_max_));
-    else for (int b = 1; b <= occ_max_; ++b) bps_list.push_back(b);
-    std::vector<int> cap_list = opts_.lanes_per_cube > 0 ? std::vector<int>{lanes_cap_} : std::vector<int>{16, 64, 256};
-    // a subset of the batch (every k-th integral) keeps tuning cheap
+    if (opts_.blocks_per_sm > 0) bps_list.push_back(std::min(opts_.blocks_per_sm, occ_hi));
+    else for (int b = 1; b <= occ_hi; ++b) bps_list.push_back(b);
+    std::vector<int> cap_list =
+        opts_.lanes_per_cube > 0 ? std::vector<int>{lanes_cap_} : std::vector<int>{16, 64, 256};
+    // a subset of the batch (every k-th integral, class order kept) keeps tuning cheap
     std::vector<int> sub;
     const size_t stride = std::max<size_t>(1, live.size() / 256);
     for (size_t i = 0; i < live.size(); i += stride) sub.push_back(live[i]);
@@ -426,21 +500,24 @@ cudaError_t BatchEngine::autotune(const std::vector<int>& live)
         lanes_cap_ = cap;
         for (int s : sub) {
             hdesc_[s].lanes = (uint32_t)choose_lanes(slots_[s].p);
-            if ((e = cudaMemcpyAsync((BatchDesc*)desc_.ptr + s, &hdesc_[s], sizeof(BatchDesc), cudaMemcpyHostToDevice,
-                                     stream_)))
+            if ((e = cudaMemcpyAsync((BatchDesc*)desc_.ptr + s, &hdesc_[s], sizeof(BatchDesc),
+                                     cudaMemcpyHostToDevice, stream_)))
                 break;
         }
         if (e) break;
         for (int bps : bps_list) {
-            const int blocks = bps * num_sms_;
+            tuned_bps_ = bps;
             int nseg = 0;
             if ((e = cudaStreamSynchronize(stream_))) break;  // pinned staging reuse
-            partition(sub, blocks, &nseg);
-            if ((e = upload_partition(sub, blocks, nseg))) break;
+            partition(sub, &nseg);
+            if ((e = upload_partition(sub, nseg))) break;
             float ms = 0.f;
-            for (int rep = 0; rep < 2; ++rep) {  // first launch warms up
+            for (int rep = 0; rep < 2; ++rep) {  // the first launch warms up
                 cudaEventRecord(e0, stream_);
-                if ((e = launch_vsample_batch(mixed_, sample_args(), blocks, smem_bytes(), stream_))) break;
+                for (int c = 0; c < kNumClasses && !e; ++c)
+                    if (mask >> c & 1u)
+                        e = launch_vsample_batch(c, mixed_, sample_args(c), class_blocks(c), smem_bytes(c), stream_);
+                if (e) break;
                 cudaEventRecord(e1, stream_);
                 if ((e = cudaEventSynchronize(e1))) break;
                 cudaEventElapsedTime(&ms, e0, e1);
@@ -460,8 +537,7 @@ cudaError_t BatchEngine::autotune(const std::vector<int>& live)
     lanes_cap_ = best_cap;
     tuned_bps_ = best_bps;
     tuned_ = true;
-    // final lanes for every resident integral
-    for (int s = 0; s < capacity_; ++s) {
+    for (int s = 0; s < capacity_; ++s) {  // final lanes for every resident integral
         if (!slots_[s].used) continue;
         hdesc_[s].lanes = (uint32_t)choose_lanes(slots_[s].p);
         if ((e = cudaMemcpyAsync((BatchDesc*)desc_.ptr + s, &hdesc_[s], sizeof(BatchDesc), cudaMemcpyHostToDevice,
@@ -477,16 +553,16 @@ cudaError_t BatchEngine::step(int* ran)
     cudaError_t e = flush_admissions();
     if (e) return e;
     std::vector<int> live;
-    live_slots(&live);
+    unsigned mask = 0;
+    live_slots(&live, &mask);
     if (live.empty()) return cudaSuccess;
-    if ((e = autotune(live))) return e;
-    const int blocks = tuned_bps_ * num_sms_;
-    if ((e = capture(blocks))) return e;
+    if ((e = autotune(live, mask))) return e;
+    if ((e = capture(mask))) return e;
     int nseg = 0;
-    partition(live, blocks, &nseg);
-    if ((e = upload_partition(live, blocks, nseg))) return e;
+    partition(live, &nseg);
+    if ((e = upload_partition(live, nseg))) return e;
     if (exec_) e = cudaGraphLaunch(exec_, stream_);
-    else e = enqueue_iteration(blocks);
+    else e = enqueue_iteration(mask);
     if (e) return e;
     for (int s : live) slots_[s].it += 1;
     *ran = (int)live.size();

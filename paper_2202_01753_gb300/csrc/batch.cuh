@@ -1,34 +1,28 @@
-// batch.cuh -- the persistent batched sampling kernel: one launch samples one
-// iteration of every live integral of a batch.  The host lays the live
-// integrals' samples end to end and cuts that line into one equal,
+// batch.cuh -- the persistent batched sampling kernels: one launch per class
+// of integrals (integrand family x groups of four axes) samples one
+// iteration of every live integral of that class.  The host lays the class's
+// live integrals' samples end to end and cuts that line into one equal,
 // cube-aligned chunk per block; a block therefore samples a few segments
 // (runs of cubes of one integral each), in order.  Per segment it stages that
 // integral's grid and family constants in shared memory, samples with the
 // same per-sample code as the single-integral kernel (vsample.cuh), and
 // writes the segment's partial sums and, in adjusting iterations, its
 // partial histogram.  The refinement launch (batch.cu) reduces an integral's
-// segments in their fixed order.
+// segments in their fixed order.  One kernel per class keeps each one fully
+// inlined with the register budget of the single-integral kernel.
 #pragma once
 
 #include "vsample.cuh"
 
 namespace mc {
 
-template <int FAM, bool MIXED>
-__device__ __forceinline__ void batch_segment(const BatchView& v, const BatchDesc& sd,
-                                              const typename Prec<MIXED>::Cell* cells,
-                                              typename Prec<MIXED>::H* hist, const BatchSeg& seg, uint32_t it,
-                                              CubeSums& acc)
+template <int FAM, bool MIXED, int NB4>
+__global__ void __launch_bounds__(kVsThreads, 2)
+vsample_batch_kernel(const __grid_constant__ BatchArgs a)
 {
-    if (seg.adjust)
-        sample_cubes<FAM, MIXED, true>(v, cells, hist, seg.c0, seg.c1 - seg.c0, 0, 1, it, sd.lanes, sd.p, acc);
-    else
-        sample_cubes<FAM, MIXED, false>(v, cells, hist, seg.c0, seg.c1 - seg.c0, 0, 1, it, sd.lanes, sd.p, acc);
-}
-
-template <bool MIXED>
-__global__ void __launch_bounds__(kVsThreads) vsample_batch_kernel(const __grid_constant__ BatchArgs a)
-{
+    if constexpr (FAM == MCUBES_F_COSMO6 && NB4 != 2) {
+        return;  // six axes only: never launched
+    } else {
     using Cell = typename Prec<MIXED>::Cell;
     using HT = typename Prec<MIXED>::H;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -55,17 +49,12 @@ __global__ void __launch_bounds__(kVsThreads) vsample_batch_kernel(const __grid_
         const BatchView v{d, nb, sd.g, sd.gmagic, sd.key0, sd.key1, sd.phi_scale, sd.phi_scale_f, sd.fam};
         const uint32_t it = a.st[seg.slot].it;
         CubeSums acc;
-        switch (sd.family) {
-        case MCUBES_F_CONST: batch_segment<MCUBES_F_CONST, MIXED>(v, sd, cells, hist, seg, it, acc); break;
-        case MCUBES_F_GAUSS: batch_segment<MCUBES_F_GAUSS, MIXED>(v, sd, cells, hist, seg, it, acc); break;
-        case MCUBES_F_CORNER: batch_segment<MCUBES_F_CORNER, MIXED>(v, sd, cells, hist, seg, it, acc); break;
-        case MCUBES_F_OSC: batch_segment<MCUBES_F_OSC, MIXED>(v, sd, cells, hist, seg, it, acc); break;
-        case MCUBES_F_PRODPEAK: batch_segment<MCUBES_F_PRODPEAK, MIXED>(v, sd, cells, hist, seg, it, acc); break;
-        case MCUBES_F_C0: batch_segment<MCUBES_F_C0, MIXED>(v, sd, cells, hist, seg, it, acc); break;
-        case MCUBES_F_DISCONT: batch_segment<MCUBES_F_DISCONT, MIXED>(v, sd, cells, hist, seg, it, acc); break;
-        case MCUBES_F_COSMO6: batch_segment<MCUBES_F_COSMO6, MIXED>(v, sd, cells, hist, seg, it, acc); break;
-        default: break;
-        }
+        if (seg.adjust)
+            sample_cubes<FAM, MIXED, true, NB4>(v, cells, hist, seg.c0, seg.c1 - seg.c0, seg.perm_k, 0, 1, it,
+                                                sd.lanes, sd.p, acc);
+        else
+            sample_cubes<FAM, MIXED, false, NB4>(v, cells, hist, seg.c0, seg.c1 - seg.c0, seg.perm_k, 0, 1, it,
+                                                 sd.lanes, sd.p, acc);
         block_write_sums(acc, red, a.seg_part + 3 * (size_t)si);
         if (seg.adjust) {
             __syncthreads();
@@ -73,25 +62,51 @@ __global__ void __launch_bounds__(kVsThreads) vsample_batch_kernel(const __grid_
             for (uint32_t i = threadIdx.x; i < d * nb; i += blockDim.x) out[i] = hist[i];
         }
     }
+    }
 }
 
-template <bool MIXED>
-cudaError_t launch_vsample_batch_prec(const BatchArgs& a, int grid, size_t smem, cudaStream_t s)
+template <int FAM, bool MIXED>
+inline auto vsample_batch_kernel_ptr(int nb4)
 {
-    auto k = vsample_batch_kernel<MIXED>;
+    using K = void (*)(BatchArgs);
+    if (nb4 <= 1) return (K)vsample_batch_kernel<FAM, MIXED, 1>;
+    if (nb4 == 2) return (K)vsample_batch_kernel<FAM, MIXED, 2>;
+    return (K)vsample_batch_kernel<FAM, MIXED, 3>;
+}
+
+template <int FAM>
+cudaError_t launch_vsample_batch_family(bool mixed, int nb4, const BatchArgs& a, int grid, size_t smem,
+                                        cudaStream_t s)
+{
+    auto k = mixed ? vsample_batch_kernel_ptr<FAM, true>(nb4) : vsample_batch_kernel_ptr<FAM, false>(nb4);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, kVsThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <bool MIXED>
-cudaError_t vsample_batch_occupancy_prec(size_t smem, int* blocks)
+template <int FAM>
+cudaError_t vsample_batch_occupancy_family(bool mixed, int nb4, size_t smem, int* blocks)
 {
-    auto k = vsample_batch_kernel<MIXED>;
+    auto k = mixed ? vsample_batch_kernel_ptr<FAM, true>(nb4) : vsample_batch_kernel_ptr<FAM, false>(nb4);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, kVsThreads, smem);
 }
 
 }  // namespace mc
+
+// Instantiates a family's batched kernels and their launchers
+// (launch_vsample_batch_<name>, vsample_batch_occupancy_<name>).
+#define MC_INSTANTIATE_BATCH_FAMILY(FAM, NAME)                                                        \
+    namespace mc {                                                                                    \
+    cudaError_t launch_vsample_batch_##NAME(bool mixed, int nb4, const BatchArgs& a, int grid,        \
+                                            size_t smem, cudaStream_t s)                              \
+    {                                                                                                 \
+        return launch_vsample_batch_family<FAM>(mixed, nb4, a, grid, smem, s);                        \
+    }                                                                                                 \
+    cudaError_t vsample_batch_occupancy_##NAME(bool mixed, int nb4, size_t smem, int* blocks)         \
+    {                                                                                                 \
+        return vsample_batch_occupancy_family<FAM>(mixed, nb4, smem, blocks);                         \
+    }                                                                                                 \
+    }

@@ -74,17 +74,19 @@ private:
     };
 
     void release();
-    size_t smem_bytes() const;
+    size_t smem_bytes(int cls) const;
+    int class_blocks(int cls) const;
     int choose_lanes(long long p) const;
     cudaError_t flush_admissions();
-    void live_slots(std::vector<int>* live) const;
-    void partition(const std::vector<int>& live, int blocks, int* nseg);
-    cudaError_t upload_partition(const std::vector<int>& live, int blocks, int nseg);
-    BatchArgs sample_args() const;
+    // live slots grouped by class (class order, slot order within a class)
+    void live_slots(std::vector<int>* live, unsigned* class_mask) const;
+    void partition(const std::vector<int>& live, int* nseg);
+    cudaError_t upload_partition(const std::vector<int>& live, int nseg);
+    BatchArgs sample_args(int cls) const;
     BatchRefineArgs refine_args() const;
-    cudaError_t enqueue_iteration(int blocks);
-    cudaError_t capture(int blocks);
-    cudaError_t autotune(const std::vector<int>& live);
+    cudaError_t enqueue_iteration(unsigned class_mask);
+    cudaError_t capture(unsigned class_mask);
+    cudaError_t autotune(const std::vector<int>& live, unsigned class_mask);
     cudaError_t refresh();
 
     int device_;
@@ -92,7 +94,9 @@ private:
     int num_sms_;
     mcubes_opts opts_;
     bool mixed_;
-    int capacity_ = 0, itcap_ = 0, occ_max_ = 1;
+    int capacity_ = 0, itcap_ = 0;
+    int occ_[kNumClasses] = {0};   // resident blocks per SM of each class's kernel
+    int bmax_ = 0;                 // most blocks any class launches
     bool tuned_ = false;
     int tuned_bps_ = 1, lanes_cap_ = 64;
 
@@ -107,7 +111,8 @@ private:
     BatchState* h_states_ = nullptr; // pinned read-back
     cudaGraph_t graph_ = nullptr;
     cudaGraphExec_t exec_ = nullptr;
-    int graph_blocks_ = 0;
+    unsigned graph_mask_ = 0;      // classes the captured graph launches
+    int graph_bps_ = 0;
 };
 
 }  // namespace mc

@@ -1,0 +1,4 @@
+// Batched sampling kernels for the gauss integrand family (see batch.cuh).
+#include "batch.cuh"
+
+MC_INSTANTIATE_BATCH_FAMILY(MCUBES_F_GAUSS, gauss)

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <numeric>
 #include <vector>
 
 #include "batch_engine.h"
@@ -21,14 +22,14 @@ cudaError_t launch_vsample_prodpeak(bool, bool, const VsArgs&, int, size_t, cuda
 cudaError_t launch_vsample_c0(bool, bool, const VsArgs&, int, size_t, cudaStream_t);
 cudaError_t launch_vsample_discont(bool, bool, const VsArgs&, int, size_t, cudaStream_t);
 cudaError_t launch_vsample_cosmo6(bool, bool, const VsArgs&, int, size_t, cudaStream_t);
-cudaError_t occupancy_const(bool, bool, size_t, int*);
-cudaError_t occupancy_gauss(bool, bool, size_t, int*);
-cudaError_t occupancy_corner(bool, bool, size_t, int*);
-cudaError_t occupancy_osc(bool, bool, size_t, int*);
-cudaError_t occupancy_prodpeak(bool, bool, size_t, int*);
-cudaError_t occupancy_c0(bool, bool, size_t, int*);
-cudaError_t occupancy_discont(bool, bool, size_t, int*);
-cudaError_t occupancy_cosmo6(bool, bool, size_t, int*);
+cudaError_t occupancy_const(bool, bool, int, size_t, int*);
+cudaError_t occupancy_gauss(bool, bool, int, size_t, int*);
+cudaError_t occupancy_corner(bool, bool, int, size_t, int*);
+cudaError_t occupancy_osc(bool, bool, int, size_t, int*);
+cudaError_t occupancy_prodpeak(bool, bool, int, size_t, int*);
+cudaError_t occupancy_c0(bool, bool, int, size_t, int*);
+cudaError_t occupancy_discont(bool, bool, int, size_t, int*);
+cudaError_t occupancy_cosmo6(bool, bool, int, size_t, int*);
 
 cudaError_t launch_vsample(int family, bool mixed, bool adjust, const VsArgs& a, int grid, size_t smem,
                            cudaStream_t s)
@@ -46,17 +47,17 @@ cudaError_t launch_vsample(int family, bool mixed, bool adjust, const VsArgs& a,
     }
 }
 
-cudaError_t vsample_occupancy(int family, bool mixed, bool adjust, size_t smem, int* blocks)
+cudaError_t vsample_occupancy(int family, bool mixed, bool adjust, int d, size_t smem, int* blocks)
 {
     switch (family) {
-    case MCUBES_F_CONST: return occupancy_const(mixed, adjust, smem, blocks);
-    case MCUBES_F_GAUSS: return occupancy_gauss(mixed, adjust, smem, blocks);
-    case MCUBES_F_CORNER: return occupancy_corner(mixed, adjust, smem, blocks);
-    case MCUBES_F_OSC: return occupancy_osc(mixed, adjust, smem, blocks);
-    case MCUBES_F_PRODPEAK: return occupancy_prodpeak(mixed, adjust, smem, blocks);
-    case MCUBES_F_C0: return occupancy_c0(mixed, adjust, smem, blocks);
-    case MCUBES_F_DISCONT: return occupancy_discont(mixed, adjust, smem, blocks);
-    case MCUBES_F_COSMO6: return occupancy_cosmo6(mixed, adjust, smem, blocks);
+    case MCUBES_F_CONST: return occupancy_const(mixed, adjust, d, smem, blocks);
+    case MCUBES_F_GAUSS: return occupancy_gauss(mixed, adjust, d, smem, blocks);
+    case MCUBES_F_CORNER: return occupancy_corner(mixed, adjust, d, smem, blocks);
+    case MCUBES_F_OSC: return occupancy_osc(mixed, adjust, d, smem, blocks);
+    case MCUBES_F_PRODPEAK: return occupancy_prodpeak(mixed, adjust, d, smem, blocks);
+    case MCUBES_F_C0: return occupancy_c0(mixed, adjust, d, smem, blocks);
+    case MCUBES_F_DISCONT: return occupancy_discont(mixed, adjust, d, smem, blocks);
+    case MCUBES_F_COSMO6: return occupancy_cosmo6(mixed, adjust, d, smem, blocks);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -186,6 +187,17 @@ bool geometry(int d, long long ncall, long long g_override, int nb, long long* g
     *m = (long long)mm;
     *p = pp;
     return true;
+}
+
+// Multiplier of the cube order of a range of n cubes (see sample_cubes):
+// the integer nearest n times the golden-ratio fraction that is coprime to n.
+uint64_t cube_permutation(uint64_t n)
+{
+    if (n <= 2) return 1;
+    uint64_t k = (uint64_t)std::llround(0.6180339887498949 * (double)n);
+    if (k < 1) k = 1;
+    while (std::gcd(k, n) != 1) k = (k + 1 < n) ? k + 1 : 1;
+    return k;
 }
 
 void philox_round_keys(uint64_t seed, uint32_t rk[10][2])
@@ -444,8 +456,8 @@ mcubes_status mcubes_setup(mcubes_ctx* c, int id, const double* params, int npar
     MC_CHECK(c, cudaDeviceGetAttribute(&smem_limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     if (c->smem_adj + 1024 > (size_t)smem_limit) return MCUBES_EINVAL;  // grid + histogram must fit on chip
     int occ_adj = 0, occ_noadj = 0;
-    MC_CHECK(c, vsample_occupancy(id, c->mixed, true, c->smem_adj, &occ_adj));
-    MC_CHECK(c, vsample_occupancy(id, c->mixed, false, c->smem_noadj, &occ_noadj));
+    MC_CHECK(c, vsample_occupancy(id, c->mixed, true, d, c->smem_adj, &occ_adj));
+    MC_CHECK(c, vsample_occupancy(id, c->mixed, false, d, c->smem_noadj, &occ_noadj));
     if (occ_adj < 1 || occ_noadj < 1) return MCUBES_EINVAL;
     if (c->opts.blocks_per_sm > 0) {
         occ_adj = std::min(occ_adj, c->opts.blocks_per_sm);
@@ -480,6 +492,7 @@ mcubes_status mcubes_setup(mcubes_ctx* c, int id, const double* params, int npar
     a.lanes = (uint32_t)c->lanes;
     a.cube_begin = 0;
     a.cube_end = (uint64_t)m;
+    a.perm_k = cube_permutation((uint64_t)m);
     philox_round_keys(c->opts.seed, a.rk);
     for (int j = 0; j < d; ++j) {
         a.lo[j] = lo[j];
@@ -656,6 +669,7 @@ mcubes_status mcubes_sample_range(mcubes_ctx* c, unsigned it, int adjust, long l
     a.it_fixed = it;
     a.cube_begin = (uint64_t)cube_begin;
     a.cube_end = (uint64_t)cube_end;
+    a.perm_k = cube_permutation((uint64_t)(cube_end - cube_begin));
     const bool adj = adjust != 0;
     const int grid = adj ? c->grid_adj : c->grid_noadj;
     const size_t smem = adj ? c->smem_adj : c->smem_noadj;

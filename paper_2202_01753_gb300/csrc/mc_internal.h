@@ -59,6 +59,7 @@ struct VsArgs {
     uint32_t d, nb, g, gmagic;  // gmagic = floor((2^32-1)/g)
     uint32_t p, lanes;          // samples per cube, threads per cube (power of two <= 32)
     uint64_t cube_begin, cube_end;
+    uint64_t perm_k;          // cube order: logical i -> cube_begin + (i perm_k mod n), gcd(perm_k, n) = 1
     uint32_t rk[10][2];       // Philox round keys (key + r * Weyl constants)
     double lo[kDMax];
     double scale[kDMax];      // hi - lo
@@ -104,6 +105,7 @@ struct BatchSeg {
     uint32_t slot;
     uint32_t adjust;
     uint64_t c0, c1;
+    uint64_t perm_k;            // cube order within the segment (see sample_cubes)
     uint64_t hist_off;          // element offset of the segment's partial histogram
 };
 
@@ -111,7 +113,7 @@ struct BatchArgs {
     const BatchDesc* desc;
     const BatchState* st;
     const BatchSeg* segs;
-    const uint32_t* blk_seg;    // block b samples segments [blk_seg[b], blk_seg[b+1])
+    const uint32_t* blk_seg;    // block b samples segments [blk_seg[b], blk_seg[b+1]) (this class's table)
     double* seg_part;           // [segment][3] partial sums
     void* seg_hist;             // partial histograms (float in mixed, double in fp64)
 };
@@ -129,8 +131,11 @@ struct BatchRefineArgs {
     double alpha;
 };
 
-cudaError_t launch_vsample_batch(bool mixed, const BatchArgs& a, int grid, size_t smem, cudaStream_t s);
-cudaError_t vsample_batch_occupancy(bool mixed, size_t smem, int* blocks_per_sm);
+// Batched kernels are instantiated per class: family x nb4 = ceil(d / 4).
+constexpr int kNumClasses = MCUBES_F_COUNT * 3;
+__host__ __device__ constexpr int batch_class(int family, int d) { return family * 3 + (d + 3) / 4 - 1; }
+cudaError_t launch_vsample_batch(int cls, bool mixed, const BatchArgs& a, int grid, size_t smem, cudaStream_t s);
+cudaError_t vsample_batch_occupancy(int cls, bool mixed, size_t smem, int* blocks_per_sm);
 cudaError_t launch_refine_batch(const BatchRefineArgs& a, int capacity, cudaStream_t s);
 cudaError_t launch_init_slots(const BatchDesc* desc, BatchState* st, const uint32_t* slots, int count,
                               cudaStream_t s);
@@ -151,7 +156,8 @@ struct RefineArgs {
 cudaError_t launch_vsample(int family, bool mixed, bool adjust, const VsArgs& a, int grid,
                            size_t smem, cudaStream_t s);
 size_t vsample_smem_bytes(bool mixed, bool adjust, int d, int nb);
-cudaError_t vsample_occupancy(int family, bool mixed, bool adjust, size_t smem, int* blocks_per_sm);
+cudaError_t vsample_occupancy(int family, bool mixed, bool adjust, int d, size_t smem, int* blocks_per_sm);
+uint64_t cube_permutation(uint64_t n);
 
 cudaError_t launch_refine(const RefineArgs& a, cudaStream_t s);
 cudaError_t launch_reduce_range(const double* part, const void* part_hist, int hist_is_float,

@@ -99,7 +99,7 @@ extern "C" mcubes_status mcubes_sample_range_noalloc(
             break;
         }
         if (smem + 1024 > (size_t)smem_limit) { st = MCUBES_EINVAL; break; }
-        if (vsample_occupancy(integrand_id, mixed, adj, smem, &occ) != cudaSuccess || occ < 1) {
+        if (vsample_occupancy(integrand_id, mixed, adj, d, smem, &occ) != cudaSuccess || occ < 1) {
             st = MCUBES_ECUDA;
             break;
         }
@@ -125,6 +125,7 @@ extern "C" mcubes_status mcubes_sample_range_noalloc(
         a.lanes = (uint32_t)lanes;
         a.cube_begin = (uint64_t)cube_begin;
         a.cube_end = (uint64_t)cube_end;
+        a.perm_k = cube_permutation((uint64_t)(cube_end - cube_begin));
         philox_round_keys(seed, a.rk);
         for (int j = 0; j < d; ++j) {
             a.lo[j] = lo[j];

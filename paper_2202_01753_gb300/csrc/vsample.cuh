@@ -56,19 +56,20 @@ __device__ __forceinline__ void stage_grid(typename Prec<MIXED>::Cell* cells, ty
 
 // One sample: random words -> exact bin position -> map -> integrand.
 // Returns F = f(x) * J and leaves the flat histogram index of every axis in
-// idx.  A provides d, nb, g, gmagic, phi_scale (2^-33/(g nb)), phi_scale_f
+// idx (16 bits each, two per word).  A provides d, nb, g, gmagic, phi_scale (2^-33/(g nb)), phi_scale_f
 // (1/(g nb)) and fam, and sample_words(a, counter) its Philox block.
-template <int FAM, bool MIXED, class A>
+template <int FAM, bool MIXED, int NB4, class A>
 __device__ __forceinline__ typename Prec<MIXED>::R
 sample_point(const A& a, const typename Prec<MIXED>::Cell* cells, uint32_t c, uint32_t s, uint32_t it,
-             const uint32_t (&nbc)[kDMax], uint32_t (&idx)[kDMax])
+             const uint32_t (&nbc)[4 * NB4], uint32_t (&idx)[2 * NB4])
 {
     using R = typename Prec<MIXED>::R;
     using Fam = Family<FAM, R>;
+    constexpr int DN = 4 * NB4;  // axes handled by this instantiation (d <= DN)
     const uint32_t d = a.d, nb = a.nb;
-    uint32_t w[kDMax];
+    uint32_t w[DN];
 #pragma unroll
-    for (int b = 0; b < kDMax / 4; ++b) {
+    for (int b = 0; b < NB4; ++b) {
         if (4 * b < (int)d) {
             const uint4 r = sample_words(a, make_uint4(s, c, it, (uint32_t)b));
             w[4 * b + 0] = r.x;
@@ -81,7 +82,7 @@ sample_point(const A& a, const typename Prec<MIXED>::Cell* cells, uint32_t c, ui
     Fam::begin(fs);
     R jac = R(1);
 #pragma unroll
-    for (int j = 0; j < kDMax; ++j) {
+    for (int j = 0; j < DN; ++j) {
         if (j < (int)d) {
             const BinPos bp = bin_pos(w[j], nbc[j], nb, a.g, a.gmagic);
             const uint32_t flat = (uint32_t)j * nb + bp.k;
@@ -96,7 +97,9 @@ sample_point(const A& a, const typename Prec<MIXED>::Cell* cells, uint32_t c, ui
             }
             jac *= cell.y;
             Fam::add(fs, j, x, a.fam);
-            idx[j] = flat;
+            // flat histogram indices (< 2^16) packed two per register
+            if (j & 1) idx[j >> 1] |= flat << 16;
+            else idx[j >> 1] = flat;
         }
     }
     return Fam::end(fs, d, a.fam) * jac;
@@ -113,31 +116,42 @@ struct CubeSums {
 };
 
 // Samples cubes [cube_lo, cube_lo + ncubes) of one integral.  The block takes
-// groups of (blockDim / lanes) consecutive cubes: group0, group0 + gstride, ...
-template <int FAM, bool MIXED, bool ADJ, class A>
+// groups of (blockDim / lanes) logical cube indices: group0, group0 + gstride,
+// ...; logical index i is cube cube_lo + (i * perm_k mod ncubes), a bijection
+// of the range (gcd(perm_k, ncubes) = 1) that gives the lanes of a warp
+// cubes with unrelated digits on every axis, so that their samples spread
+// over all bins instead of crowding the same few (fewer shared-memory atomic
+// conflicts and bank conflicts).
+template <int FAM, bool MIXED, bool ADJ, int NB4, class A>
 __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIXED>::Cell* cells,
                                              typename Prec<MIXED>::H* hist, uint64_t cube_lo, uint64_t ncubes,
-                                             uint64_t group0, uint64_t gstride, uint32_t it, uint32_t lanes,
-                                             uint32_t p, CubeSums& acc)
+                                             uint64_t perm_k, uint64_t group0, uint64_t gstride, uint32_t it,
+                                             uint32_t lanes, uint32_t p, CubeSums& acc)
 {
     using R = typename Prec<MIXED>::R;
     using HT = typename Prec<MIXED>::H;
+    constexpr int DN = 4 * NB4;
     const uint32_t d = a.d, nb = a.nb;
     const uint32_t L = lanes;
     const uint32_t seg_lane = threadIdx.x & (L - 1u);
     const uint32_t cubes_per_group = blockDim.x / L;
     const R inv_p = R(1) / R(p);
     const R inv_var_den = inv_p / R(p - 1);   // 1 / (p (p-1))
+    const uint64_t first = group0 * cubes_per_group + threadIdx.x / L;
+    uint64_t off = ncubes ? (first % ncubes) * perm_k % ncubes : 0;               // physical offset of `first`
+    const uint64_t step = ncubes ? (gstride * cubes_per_group % ncubes) * perm_k % ncubes : 0;
     for (uint64_t base = group0 * cubes_per_group; base < ncubes; base += gstride * cubes_per_group) {
         const uint64_t ci = base + threadIdx.x / L;
         const bool valid = ci < ncubes;
-        const uint32_t c = (uint32_t)(cube_lo + (valid ? ci : 0));
+        const uint32_t c = (uint32_t)(cube_lo + (valid ? off : 0));
+        off += step;
+        if (off >= ncubes) off -= ncubes;
         // sub-cube digits (axis 0 fastest), kept as nb * digit
-        uint32_t nbc[kDMax];
+        uint32_t nbc[DN];
         {
             uint32_t rest = c;
 #pragma unroll
-            for (int j = 0; j < kDMax; ++j) {
+            for (int j = 0; j < DN; ++j) {
                 if (j < (int)d) {
                     uint32_t q = __umulhi(rest, a.gmagic);
                     uint32_t r = rest - q * a.g;
@@ -153,8 +167,8 @@ __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIX
         uint32_t n = 0;
         if (valid) {
             for (uint32_t s = seg_lane; s < p; s += L) {
-                uint32_t idx[kDMax];
-                const R F = sample_point<FAM, MIXED>(a, cells, c, s, it, nbc, idx);
+                uint32_t idx[2 * NB4];
+                const R F = sample_point<FAM, MIXED, NB4>(a, cells, c, s, it, nbc, idx);
                 if (n == 0) K = F;
                 const R z = F - K;
                 S1 += z;
@@ -163,8 +177,8 @@ __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIX
                 if constexpr (ADJ) {
                     const HT F2 = (HT)(F * F);
 #pragma unroll
-                    for (int j = 0; j < kDMax; ++j)
-                        if (j < (int)d) atomicAdd(&hist[idx[j]], F2);
+                    for (int j = 0; j < DN; ++j)
+                        if (j < (int)d) atomicAdd(&hist[(idx[j >> 1] >> (16 * (j & 1))) & 0xFFFFu], F2);
                 }
             }
         }
@@ -239,10 +253,18 @@ __device__ __forceinline__ void block_write_sums(const CubeSums& acc, double (*r
     }
 }
 
-template <int FAM, bool MIXED, bool ADJ>
-__global__ void __launch_bounds__(kVsThreads)
+// Resident blocks per SM the register allocation is bounded for: three
+// (80 registers) where that costs no significant spilling, else two.
+template <bool MIXED, int NB4>
+constexpr int vsample_min_blocks() { return (MIXED && NB4 <= 2) ? 3 : 2; }
+
+template <int FAM, bool MIXED, bool ADJ, int NB4>
+__global__ void __launch_bounds__(kVsThreads, vsample_min_blocks<MIXED, NB4>())
 vsample_kernel(const __grid_constant__ VsArgs a)
 {
+    if constexpr (FAM == MCUBES_F_COSMO6 && NB4 != 2) {
+        return;  // six axes only: never launched
+    } else {
     using Cell = typename Prec<MIXED>::Cell;
     using HT = typename Prec<MIXED>::H;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -263,29 +285,38 @@ vsample_kernel(const __grid_constant__ VsArgs a)
     __syncthreads();
 
     CubeSums acc;
-    sample_cubes<FAM, MIXED, ADJ>(a, cells, hist, a.cube_begin, a.cube_end - a.cube_begin, blockIdx.x, gridDim.x,
-                                  it, a.lanes, a.p, acc);
+    sample_cubes<FAM, MIXED, ADJ, NB4>(a, cells, hist, a.cube_begin, a.cube_end - a.cube_begin, a.perm_k, blockIdx.x,
+                                       gridDim.x, it, a.lanes, a.p, acc);
     block_write_sums(acc, red, a.part + 3 * (size_t)blockIdx.x);
     if constexpr (ADJ) {
         __syncthreads();
         HT* out = reinterpret_cast<HT*>(a.part_hist) + (size_t)blockIdx.x * d * nb;
         for (uint32_t i = threadIdx.x; i < d * nb; i += blockDim.x) out[i] = hist[i];
     }
+    }
+}
+
+template <int FAM, bool MIXED, bool ADJ>
+inline auto vsample_kernel_nb4(int d)
+{
+    using K = void (*)(VsArgs);
+    if (d <= 4) return (K)vsample_kernel<FAM, MIXED, ADJ, 1>;
+    if (d <= 8) return (K)vsample_kernel<FAM, MIXED, ADJ, 2>;
+    return (K)vsample_kernel<FAM, MIXED, ADJ, 3>;
 }
 
 template <int FAM>
-inline auto vsample_kernel_ptr(bool mixed, bool adjust)
+inline auto vsample_kernel_ptr(bool mixed, bool adjust, int d)
 {
-    using K = void (*)(VsArgs);
-    if (mixed) return adjust ? (K)vsample_kernel<FAM, true, true> : (K)vsample_kernel<FAM, true, false>;
-    return adjust ? (K)vsample_kernel<FAM, false, true> : (K)vsample_kernel<FAM, false, false>;
+    if (mixed) return adjust ? vsample_kernel_nb4<FAM, true, true>(d) : vsample_kernel_nb4<FAM, true, false>(d);
+    return adjust ? vsample_kernel_nb4<FAM, false, true>(d) : vsample_kernel_nb4<FAM, false, false>(d);
 }
 
 template <int FAM>
 cudaError_t launch_vsample_family(bool mixed, bool adjust, const VsArgs& a, int grid, size_t smem,
                                   cudaStream_t s)
 {
-    auto k = vsample_kernel_ptr<FAM>(mixed, adjust);
+    auto k = vsample_kernel_ptr<FAM>(mixed, adjust, (int)a.d);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, kVsThreads, smem, s>>>(a);
@@ -293,9 +324,9 @@ cudaError_t launch_vsample_family(bool mixed, bool adjust, const VsArgs& a, int 
 }
 
 template <int FAM>
-cudaError_t occupancy_family(bool mixed, bool adjust, size_t smem, int* blocks)
+cudaError_t occupancy_family(bool mixed, bool adjust, int d, size_t smem, int* blocks)
 {
-    auto k = vsample_kernel_ptr<FAM>(mixed, adjust);
+    auto k = vsample_kernel_ptr<FAM>(mixed, adjust, d);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, kVsThreads, smem);
@@ -310,8 +341,8 @@ cudaError_t occupancy_family(bool mixed, bool adjust, size_t smem, int* blocks)
     {                                                                                             \
         return launch_vsample_family<FAM>(mixed, adjust, a, grid, smem, s);                       \
     }                                                                                             \
-    cudaError_t occupancy_##NAME(bool mixed, bool adjust, size_t smem, int* blocks)               \
+    cudaError_t occupancy_##NAME(bool mixed, bool adjust, int d, size_t smem, int* blocks)        \
     {                                                                                             \
-        return occupancy_family<FAM>(mixed, adjust, smem, blocks);                                \
+        return occupancy_family<FAM>(mixed, adjust, d, smem, blocks);                             \
     }                                                                                             \
     }

@@ -58,7 +58,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="cosmo6", choices=sorted(W.CONFIGS) + ["batch4096"])
+    ap.add_argument("--config", default="cosmo6", choices=sorted(W.CONFIGS) + ["batch4096", "serve"])
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the Poisson stream")
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--batch-n", type=int, default=4096)
     ap.add_argument("--seq-sample", type=int, default=96, help="integrals timed one by one in plain FP64")
     ap.add_argument("--ncall", type=float, default=None, help="override calls per iteration (profiling)")
@@ -388,8 +390,74 @@ def batch_arm(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# serving: a Poisson stream of requests through the continuous-batching
+# server, p50/p99 latency and integrals/s, against plain FP64 one by one
+# ---------------------------------------------------------------------------
+def serve_arm(args):
+    import numpy as np
+    import torch
+
+    from paper_2202_01753_gb300 import build, mcubes
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    build.build()
+    stream = W.serving_stream(rate=args.serve_rate, duration=args.serve_seconds)
+    ws = [w for _, w in stream]
+    arrival = np.array([t for t, _ in stream])
+    reqs = [dict(fid=w.fid, params=w.params, lo=w.lo, hi=w.hi, ncall=w.ncall, itmax=w.itmax, rel_tol=w.rel_tol,
+                 seed=w.seed) for w in ws]
+    ctx = mcubes.Context(local, precision="mixed")
+    srv = mcubes.Server(ctx, itcap=max(w.itmax for w in ws))
+    srv.run_stream(reqs[:200], arrival[:200] - arrival[0])         # warm-up: autotune, graph capture
+    clocks = ClockSampler(local)
+    clocks.start()
+    res, lat, wall = srv.run_stream(reqs, arrival)
+    clk = clocks.stop()
+    # capacity: the same requests all offered at once
+    t0 = time.perf_counter()
+    res_sat, _, wall_sat = srv.run_stream(reqs, np.zeros(len(reqs)))
+    srv.close()
+    ctx.close()
+    # plain FP64, one request at a time, on an evenly spaced sample
+    idx = list(range(0, len(ws), max(1, len(ws) // args.seq_sample)))[: args.seq_sample]
+    solo = mcubes.Context(local, precision="fp64")
+    t_seq, rel = 0.0, []
+    for i in idx:
+        w = ws[i]
+        solo.set_opts(seed=w.seed)
+        t0 = time.perf_counter()
+        r = solo.integrate(w.fid, w.params, w.lo, w.hi, w.ncall, w.itmax, w.rel_tol)
+        t_seq += time.perf_counter() - t0
+        rel.append(abs(res[i]["estimate"] - r["estimate"]) / max(abs(r["estimate"]), r["sigma"]))
+    solo.close()
+    conv = [r["converged"] for r in res]
+    achieved_rel = [r["sigma"] / abs(r["estimate"]) for r in res if r["estimate"] != 0]
+    line = {
+        "metric": "integrals per second (served)", "value": len(ws) / wall, "unit": "integrals/s", "n_gpus": 1,
+        "steps": 1, "warmup": 1, "ms_per_step": 1e3 * wall, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "serving", "requests": len(ws), "offered_per_s": args.serve_rate,
+                   "seconds": args.serve_seconds, "ncall": ws[0].ncall, "itmax": ws[0].itmax,
+                   "rel_tol": "log-uniform [1e-5, 1e-3]", "d": "3..12", "precision": "mixed"},
+        "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99)),
+                       "max": 1e3 * float(lat.max())},
+        "saturated_integrals_per_s": len(ws) / wall_sat,
+        "converged_fraction": float(np.mean(conv)),
+        "median_achieved_rel_err": float(np.median(achieved_rel)),
+        "sequential_fp64": {"integrals_per_s": len(idx) / t_seq, "sample": f"{len(idx)} requests",
+                            "max_rel_diff_of_estimates": max(rel), "median_rel_diff": statistics.median(rel)},
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
+    if args.config == "serve":
+        return serve_arm(args)
     if args.config == "batch4096":
         return batch_arm(args)
     if args.impl == "reference":

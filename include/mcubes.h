@@ -172,6 +172,55 @@ mcubes_status mcubes_integrate(mcubes_ctx* ctx, int integrand_id, const double* 
 mcubes_status mcubes_integrate_batch(mcubes_ctx* ctx, int n, const mcubes_request* reqs,
                                      mcubes_result* outs);
 
+/* ---- continuous-batching server ------------------------------------------
+ * A server keeps up to `capacity` integration requests resident on the GPU,
+ * each with its own grid, running sums and iteration index, and advances all
+ * of them by one iteration per step: one persistent sampling launch per
+ * integrand class and one refinement launch, replayed as a CUDA graph.
+ * Requests submitted while others run wait in a FIFO queue and are admitted
+ * as slots free up; finished requests (converged, itmax reached, or failed)
+ * leave at once.  A request's samples do not depend on what else is
+ * resident, so its result equals a solo run up to the grouping of partial
+ * sums.  Uses the context's stream, precision, nbins, ita (as a count per
+ * request) and alpha.  One host thread at a time per server. */
+typedef struct mcubes_server mcubes_server;
+
+/* Capacity is chosen from a device-memory budget: each slot holds a
+ * double-double grid and a histogram for MCUBES_DMAX axes and a history of
+ * itcap iterations, plus its share of the per-iteration partials
+ * (mcubes_server_stats reports the bytes per slot).  budget_bytes = 0 means
+ * 4096 slots.  Errors: EINVAL, ENOMEM, ECUDA. */
+mcubes_status mcubes_server_create(mcubes_server** out, mcubes_ctx* ctx, long long budget_bytes, int itcap);
+mcubes_status mcubes_server_destroy(mcubes_server* srv);
+
+/* Queues one request (host arrays, copied); tag identifies its result.
+ * EINVAL if the request is invalid (nothing is queued). */
+mcubes_status mcubes_server_submit(mcubes_server* srv, const mcubes_request* req, long long tag);
+
+/* Admits queued requests into free slots, runs one iteration of every
+ * resident request and retires the finished ones; blocks until the
+ * iteration is done.  *ran receives the number of requests iterated. */
+mcubes_status mcubes_server_step(mcubes_server* srv, int* ran);
+
+/* Copies up to cap finished results (and their tags) not yet returned;
+ * *n receives how many were copied. */
+mcubes_status mcubes_server_poll(mcubes_server* srv, long long* tags, mcubes_result* results, int cap, int* n);
+
+/* queued: waiting for a slot; resident: on the GPU; completed: finished
+ * since creation; capacity: slots; slot_bytes: device bytes per slot. */
+mcubes_status mcubes_server_stats(mcubes_server* srv, long long* queued, long long* resident,
+                                  long long* completed, long long* capacity, long long* slot_bytes);
+
+/* Serves a timed stream in real time: request i (host array reqs) arrives
+ * arrival_s[i] seconds after the call starts (non-decreasing); the server
+ * queues arrivals, admits, steps and retires until every request is done.
+ * results[i] receives request i's result and latency_s[i] the time from its
+ * arrival to the end of the step that finished it; *wall_s the duration of
+ * the whole call.  Errors: EINVAL, ENOMEM, ECUDA. */
+mcubes_status mcubes_server_run_stream(mcubes_server* srv, int n, const mcubes_request* reqs,
+                                       const double* arrival_s, mcubes_result* results, double* latency_s,
+                                       double* wall_s);
+
 /* ---- step-level interface (the pieces of mcubes_integrate) -------------- */
 
 /* Validates one integral, computes its geometry, sizes the device buffers,

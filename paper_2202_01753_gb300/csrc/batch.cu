@@ -230,7 +230,15 @@ int BatchEngine::choose_lanes(long long p) const
     return L;
 }
 
-mcubes_status BatchEngine::admit(const mcubes_request& r, long long tag, int* slot_out)
+size_t BatchEngine::slot_bytes(const mcubes_opts& o, int itcap)
+{
+    const size_t bins = (size_t)kDMax * o.nbins;
+    const size_t elem = o.precision == MCUBES_MIXED ? sizeof(float) : sizeof(double);
+    return sizeof(double) * (3 * bins + 2 * (size_t)itcap) + sizeof(BatchDesc) + sizeof(BatchState) +
+           bins * elem + sizeof(BatchSeg) + 3 * sizeof(double) + 3 * sizeof(uint32_t);
+}
+
+mcubes_status BatchEngine::validate(const mcubes_request& r) const
 {
     const int d = r.d, nb = opts_.nbins;
     if (d < 1 || d > MCUBES_DMAX || r.ncall < 2 || r.itmax < 1 || r.itmax > itcap_ || !r.lo || !r.hi)
@@ -243,6 +251,18 @@ mcubes_status BatchEngine::admit(const mcubes_request& r, long long tag, int* sl
     long long g, m, p;
     if (!geometry(d, r.ncall, opts_.g_override, nb, &g, &m, &p)) return MCUBES_EINVAL;
     if (occ_[batch_class(r.integrand_id, d)] < 1) return MCUBES_EINVAL;
+    return MCUBES_OK;
+}
+
+mcubes_status BatchEngine::admit(const mcubes_request& r, long long tag, int* slot_out)
+{
+    const mcubes_status vst = validate(r);
+    if (vst != MCUBES_OK) return vst;
+    const int d = r.d, nb = opts_.nbins;
+    FamParams fp;
+    integrand_prepare(r.integrand_id, r.params, r.nparams, d, &fp);
+    long long g, m, p;
+    geometry(d, r.ncall, opts_.g_override, nb, &g, &m, &p);
     if (free_.empty()) return MCUBES_ENOMEM;
     const int slot = free_.back();
     free_.pop_back();

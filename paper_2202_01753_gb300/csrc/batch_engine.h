@@ -47,10 +47,18 @@ public:
     int free_slots() const { return (int)free_.size(); }
     int resident() const;
 
+    // Checks one request against this engine (options, itcap) without
+    // admitting it.
+    mcubes_status validate(const mcubes_request& r) const;
+
     // Validates one request and places it in a free slot (its grid and state
     // are initialised on the device at the next step).  tag identifies it in
     // finished().  EINVAL: invalid request; ENOMEM: no free slot.
     mcubes_status admit(const mcubes_request& r, long long tag, int* slot = nullptr);
+
+    // Device bytes one slot occupies (its grid, histogram, history, state
+    // and its share of the per-iteration partials), for itcap iterations.
+    static size_t slot_bytes(const mcubes_opts& opts, int itcap);
 
     // One iteration of every resident, unfinished integral (graph replay),
     // then a read-back of which ones have finished.  *ran = integrals iterated.

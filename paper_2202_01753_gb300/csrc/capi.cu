@@ -9,7 +9,7 @@
 #include <numeric>
 #include <vector>
 
-#include "batch_engine.h"
+#include "ctx_internal.h"
 
 using namespace mc;
 
@@ -212,47 +212,6 @@ void philox_round_keys(uint64_t seed, uint32_t rk[10][2])
 }
 
 }  // namespace mc
-
-// ---------------------------------------------------------------------------
-// context
-// ---------------------------------------------------------------------------
-namespace {
-
-struct EventPair {
-    cudaEvent_t a = nullptr, b = nullptr;
-};
-
-}  // namespace
-
-struct mcubes_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    mcubes_opts opts{};
-    int num_sms = 0;
-    char cuda_err[256] = {0};
-
-    // current problem
-    bool ready = false;
-    int fid = 0, d = 0, nb = 0, itmax = 0, ita = 0;
-    long long ncall = 0, g = 0, m = 0, p = 0;
-    bool mixed = false;
-    int lanes = 1;
-    int grid_adj = 0, grid_noadj = 0;
-    size_t smem_adj = 0, smem_noadj = 0;
-    int it_enqueued = 0;
-    VsArgs vs{};
-    RefineArgs rf{};
-
-    DevBuf grid, hist, part, part_hist, state, range_out;
-
-    BatchEngine* engine = nullptr;  // batched path, created on first use
-
-    bool timing = false;
-    std::vector<EventPair> ev_sample, ev_refine;
-    size_t n_sample = 0, n_refine = 0;
-    std::vector<EventPair> pool;
-};
 
 static mcubes_status cuda_fail(mcubes_ctx* c, cudaError_t e)
 {

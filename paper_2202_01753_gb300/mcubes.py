@@ -25,7 +25,8 @@ EXPORTED = [
     "mcubes_integrate_batch", "mcubes_setup", "mcubes_iterate", "mcubes_result_get",
     "mcubes_trace_get", "mcubes_grid_get", "mcubes_grid_set", "mcubes_hist_get",
     "mcubes_sample_range", "mcubes_geometry_get", "mcubes_timing_reset", "mcubes_timing_get",
-    "mcubes_sample_range_noalloc",
+    "mcubes_sample_range_noalloc", "mcubes_server_create", "mcubes_server_destroy", "mcubes_server_submit",
+    "mcubes_server_step", "mcubes_server_poll", "mcubes_server_stats", "mcubes_server_run_stream",
 ]
 
 
@@ -100,6 +101,15 @@ def lib():
                                                        P(ctypes.c_int)]),
                 "mcubes_timing_reset": (ctypes.c_int, [ctx, ctypes.c_int]),
                 "mcubes_timing_get": (ctypes.c_int, [ctx, dp, P(ctypes.c_int), dp, P(ctypes.c_int)]),
+                "mcubes_server_create": (ctypes.c_int, [P(ctypes.c_void_p), ctx, ll, ctypes.c_int]),
+                "mcubes_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+                "mcubes_server_submit": (ctypes.c_int, [ctypes.c_void_p, P(mcubes_request), ll]),
+                "mcubes_server_step": (ctypes.c_int, [ctypes.c_void_p, P(ctypes.c_int)]),
+                "mcubes_server_poll": (ctypes.c_int, [ctypes.c_void_p, P(ll), P(mcubes_result), ctypes.c_int,
+                                                      P(ctypes.c_int)]),
+                "mcubes_server_stats": (ctypes.c_int, [ctypes.c_void_p, P(ll), P(ll), P(ll), P(ll), P(ll)]),
+                "mcubes_server_run_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, P(mcubes_request), dp,
+                                                            P(mcubes_result), dp, dp]),
                 "mcubes_sample_range_noalloc": (ctypes.c_int, [
                     ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, dp, dp, ll, ctypes.c_int, ll,
                     ctypes.c_uint64, ctypes.c_int, ctypes.c_uint, ctypes.c_int, ll, ll, ctypes.c_void_p,
@@ -288,3 +298,71 @@ class Context:
         self._check(lib().mcubes_timing_get(self._h, ctypes.byref(sm), ctypes.byref(sn), ctypes.byref(rm),
                                             ctypes.byref(rn)), "mcubes_timing_get")
         return dict(sample_ms=sm.value, sample_launches=sn.value, refine_ms=rm.value, refine_launches=rn.value)
+
+
+def _requests(requests):
+    """ctypes array of mcubes_request from dicts (fid, params, lo, hi, ncall,
+    itmax, rel_tol, abs_tol, seed); returns (array, arrays kept alive)."""
+    reqs = list(requests)
+    keep = []
+    arr = (mcubes_request * len(reqs))()
+    for i, r in enumerate(reqs):
+        p, lo, hi = _f64(r["params"]), _f64(r["lo"]), _f64(r["hi"])
+        keep += [p, lo, hi]
+        arr[i] = mcubes_request(r["fid"], _dp(p), len(p), len(lo), _dp(lo), _dp(hi), int(r["ncall"]),
+                                int(r["itmax"]), float(r.get("rel_tol", 0.0)), float(r.get("abs_tol", 0.0)),
+                                int(r.get("seed", 0)))
+    return arr, keep
+
+
+class Server:
+    """mcubes_server: continuous batching of integration requests on one context."""
+
+    def __init__(self, ctx: Context, budget_bytes: int = 0, itcap: int = 32):
+        self._h = ctypes.c_void_p()
+        self.ctx = ctx
+        ctx._check(lib().mcubes_server_create(ctypes.byref(self._h), ctx._h, int(budget_bytes), itcap),
+                   "mcubes_server_create")
+
+    def close(self):
+        if self._h:
+            lib().mcubes_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, request, tag):
+        arr, keep = _requests([request])
+        self.ctx._check(lib().mcubes_server_submit(self._h, arr, int(tag)), "mcubes_server_submit")
+
+    def step(self):
+        ran = ctypes.c_int()
+        self.ctx._check(lib().mcubes_server_step(self._h, ctypes.byref(ran)), "mcubes_server_step")
+        return ran.value
+
+    def poll(self, cap=65536):
+        tags = (ctypes.c_longlong * cap)()
+        res = (mcubes_result * cap)()
+        n = ctypes.c_int()
+        self.ctx._check(lib().mcubes_server_poll(self._h, tags, res, cap, ctypes.byref(n)), "mcubes_server_poll")
+        return [(tags[i], res[i].as_dict()) for i in range(n.value)]
+
+    def stats(self):
+        v = [ctypes.c_longlong() for _ in range(5)]
+        self.ctx._check(lib().mcubes_server_stats(self._h, *[ctypes.byref(x) for x in v]), "mcubes_server_stats")
+        return dict(zip(["queued", "resident", "completed", "capacity", "slot_bytes"], [x.value for x in v]))
+
+    def run_stream(self, requests, arrival_s):
+        arr, keep = _requests(requests)
+        n = len(keep) // 3
+        arrival = _f64(arrival_s)
+        res = (mcubes_result * n)()
+        lat = np.zeros(n)
+        wall = ctypes.c_double()
+        self.ctx._check(lib().mcubes_server_run_stream(self._h, n, arr, _dp(arrival), res, _dp(lat),
+                                                        ctypes.byref(wall)), "mcubes_server_run_stream")
+        return [r.as_dict() for r in res], lat, wall.value

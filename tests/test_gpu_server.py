@@ -1,0 +1,130 @@
+"""The continuous-batching server: requests admitted while others are on the
+GPU, their iterations co-batched, finished ones retired at once.  Each
+result must equal the same request run alone (same seed, same precision)
+within the batch tolerances: requests draw the same samples either way, so
+only the grouping of partial sums differs."""
+import numpy as np
+import pytest
+
+import closed_forms as CF
+from paper_2202_01753_gb300 import mcubes
+from paper_2202_01753_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RTOL = {"fp64": 1e-10, "mixed": 2e-4}
+
+
+def _reqs(n, seed, itmax=8, rel=True):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n):
+        d = int(rng.integers(3, 13))
+        fam = int(rng.choice([W.F_GAUSS, W.F_CORNER, W.F_OSC]))
+        w = W.random_integral(rng, d, fam, int(10 ** rng.uniform(4, 5)), itmax, seed=9000 + i)
+        if rel:
+            w.rel_tol = float(10 ** rng.uniform(-4, -2))
+        out.append(w)
+    return out
+
+
+def _dict(w):
+    return dict(fid=w.fid, params=w.params, lo=w.lo, hi=w.hi, ncall=w.ncall, itmax=w.itmax, rel_tol=w.rel_tol,
+                abs_tol=w.abs_tol, seed=w.seed)
+
+
+def _solo(make_ctx, w, precision):
+    ctx = make_ctx(seed=w.seed, precision=precision)
+    r = ctx.integrate(w.fid, w.params, w.lo, w.hi, w.ncall, w.itmax, w.rel_tol, w.abs_tol)
+    ctx.close()
+    return r
+
+
+def _check(w, got, solo, precision):
+    assert got["status"] == solo["status"]
+    assert got["iterations"] == solo["iterations"]
+    assert got["converged"] == solo["converged"]
+    scale = max(abs(solo["estimate"]), solo["sigma"])
+    assert abs(got["estimate"] - solo["estimate"]) <= RTOL[precision] * scale
+    assert got["sigma"] == pytest.approx(solo["sigma"], rel=10 * RTOL[precision])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_requests_admitted_mid_flight_match_solo(gpu_ctx_factory, precision):
+    ws = _reqs(40, seed=21)
+    ctx = gpu_ctx_factory(precision=precision)
+    srv = mcubes.Server(ctx, itcap=16)
+    for i, w in enumerate(ws[:20]):
+        srv.submit(_dict(w), i)
+    results = {}
+    steps = 0
+    while len(results) < len(ws):
+        if steps == 2:                       # the second half arrives while the first runs
+            for i, w in enumerate(ws[20:], start=20):
+                srv.submit(_dict(w), i)
+        srv.step()
+        steps += 1
+        for tag, r in srv.poll():
+            results[tag] = r
+        assert steps < 100
+    st = srv.stats()
+    assert st["completed"] == len(ws) and st["resident"] == 0 and st["queued"] == 0
+    srv.close()
+    ctx.close()
+    for i, w in enumerate(ws):
+        _check(w, results[i], _solo(gpu_ctx_factory, w, precision), precision)
+
+
+def test_memory_budget_queues_requests(gpu_ctx_factory):
+    ws = _reqs(12, seed=22, rel=False)
+    ctx = gpu_ctx_factory(precision="mixed")
+    probe = mcubes.Server(ctx, itcap=8)
+    slot_bytes = probe.stats()["slot_bytes"]
+    probe.close()
+    srv = mcubes.Server(ctx, budget_bytes=5 * slot_bytes + 1, itcap=8)
+    assert srv.stats()["capacity"] == 5
+    for i, w in enumerate(ws):
+        srv.submit(_dict(w), i)
+    srv.step()
+    st = srv.stats()
+    assert st["resident"] == 5 and st["queued"] == 7
+    results = {}
+    while len(results) < len(ws):
+        srv.step()
+        results.update(dict(srv.poll()))
+    srv.close()
+    ctx.close()
+    for i, w in enumerate(ws):
+        _check(w, results[i], _solo(gpu_ctx_factory, w, "mixed"), "mixed")
+
+
+def test_timed_stream(gpu_ctx_factory):
+    stream = W.serving_stream(rate=2000.0, duration=0.15, draw_seed=23)
+    ws = [w.scaled(20_000, itmax=8) for _, w in stream]
+    arrival = np.array([t for t, _ in stream])
+    ctx = gpu_ctx_factory(precision="mixed")
+    srv = mcubes.Server(ctx, itcap=8)
+    res, lat, wall = srv.run_stream([_dict(w) for w in ws], arrival)
+    srv.close()
+    ctx.close()
+    assert len(res) == len(ws) > 100
+    assert np.all(lat > 0) and wall >= arrival[-1]
+    assert all(r["iterations"] >= 2 for r in res)
+    z = np.array([abs(r["estimate"] - CF.exact(w)) / r["sigma"] for r, w in zip(res, ws)])
+    assert np.mean(z < 4) > 0.95
+    for i in range(0, len(ws), max(1, len(ws) // 8)):
+        _check(ws[i], res[i], _solo(gpu_ctx_factory, ws[i], "mixed"), "mixed")
+
+
+def test_invalid_submission_is_rejected(gpu_ctx_factory):
+    ctx = gpu_ctx_factory()
+    srv = mcubes.Server(ctx, itcap=4)
+    w = _reqs(1, seed=24)[0]
+    bad = _dict(w)
+    bad["itmax"] = 5                          # beyond the server's itcap
+    with pytest.raises(mcubes.McubesError) as e:
+        srv.submit(bad, 0)
+    assert e.value.status == mcubes.EINVAL
+    assert srv.stats()["queued"] == 0
+    srv.close()
+    ctx.close()

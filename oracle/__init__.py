@@ -81,7 +81,7 @@ def _lib():
                                            ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
                                            ctypes.c_double, ctypes.c_uint64, ctypes.c_double,
                                            ctypes.c_double, dp, ctypes.POINTER(ctypes.c_int),
-                                           ctypes.POINTER(ctypes.c_int), i64p, dp, dp, dp, dp]
+                                           ctypes.POINTER(ctypes.c_int), i64p, dp, dp, dp, dp, ctypes.c_int]
             _lib_handle = h
     return _lib_handle
 
@@ -99,7 +99,7 @@ class _Problem(ctypes.Structure):
                 ("d", ctypes.c_int), ("nb", ctypes.c_int),
                 ("lo", ctypes.POINTER(ctypes.c_double)), ("hi", ctypes.POINTER(ctypes.c_double)),
                 ("g", ctypes.c_int64), ("m", ctypes.c_int64), ("p", ctypes.c_int64),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("one_dim", ctypes.c_int)]
 
 
 # --------------------------------------------------------------------------
@@ -162,7 +162,7 @@ def integrand(fid, params, x):
 class Problem:
     """One integral: family id, parameters, box, calls per iteration."""
 
-    def __init__(self, fid, params, lo, hi, ncall, nb=500, g_override=0, seed=0):
+    def __init__(self, fid, params, lo, hi, ncall, nb=500, g_override=0, seed=0, one_dim=False):
         self.fid = fid
         self.params = _f64(params)
         self.lo = _f64(lo)
@@ -172,8 +172,9 @@ class Problem:
         self.seed = seed
         self.ncall = ncall
         self.g, self.m, self.p = geometry(self.d, ncall, g_override, nb)
+        self.one_dim = bool(one_dim)
         self._c = _Problem(fid, _dp(self.params), self.d, nb, _dp(self.lo), _dp(self.hi),
-                           self.g, self.m, self.p, seed)
+                           self.g, self.m, self.p, seed, int(one_dim))
 
     @property
     def n_samples(self):
@@ -184,7 +185,8 @@ class Problem:
 
         Returns (sums, C, H): sums = [sum of cube means, sum of cube mean
         variances, sum of |cube means|]; C = [d][nb] per-bin sum of F^2 (adjust
-        only); H = [d][nb] per-bin hit counts (adjust and hits only).
+        only); H = [d][nb] per-bin hit counts (adjust and hits only).  With
+        one_dim (m-Cubes1D, Sec. 3) only row 0 of C and H is filled.
         """
         cube_end = self.m if cube_end is None else cube_end
         B = _f64(B).reshape(-1)
@@ -223,8 +225,9 @@ def weighted(I_it, var_it, rel_tol=0.0, abs_tol=0.0):
 
 
 def integrate(fid, params, lo, hi, ncall, itmax, ita=None, nb=500, g_override=0, alpha=1.5,
-              seed=0, rel_tol=0.0, abs_tol=0.0):
-    """The whole m-Cubes driver (Alg. 2). Returns a dict."""
+              seed=0, rel_tol=0.0, abs_tol=0.0, one_dim=False):
+    """The whole m-Cubes driver (Alg. 2), or with one_dim the m-Cubes1D
+    variant (Sec. 3: one grid shared by all axes). Returns a dict."""
     lo = _f64(lo)
     hi = _f64(hi)
     p = _f64(params)
@@ -241,7 +244,7 @@ def integrate(fid, params, lo, hi, ncall, itmax, ita=None, nb=500, g_override=0,
     st = _lib().oracle_integrate(fid, _dp(p), d, _dp(lo), _dp(hi), ncall, itmax, ita, nb, g_override,
                                  alpha, seed, rel_tol, abs_tol, _dp(res), ctypes.byref(iters),
                                  ctypes.byref(conv), geom.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
-                                 _dp(tI), _dp(tV), _dp(B), _dp(C))
+                                 _dp(tI), _dp(tV), _dp(B), _dp(C), int(one_dim))
     n = iters.value
     return dict(status=st, estimate=res[0], sigma=res[1], chi2_dof=res[2], iterations=n,
                 converged=bool(conv.value), g=int(geom[0]), m=int(geom[1]), p=int(geom[2]),

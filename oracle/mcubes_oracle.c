@@ -22,7 +22,9 @@
  *   - the grid refinement ("Adjust-Bin-Bounds", Alg. 2) is Lepage's
  *     smoothing, compression with exponent alpha, and equal-share rebinning;
  *   - iterations are combined with inverse-variance weights ("Weighted-
- *     Estimates", Alg. 2) and chi^2 per degree of freedom.
+ *     Estimates", Alg. 2) and chi^2 per degree of freedom;
+ *   - the m-Cubes1D variant (Sec. 3) keeps the histogram of axis 0 only,
+ *     rebins that axis, and gives its boundaries to every axis.
  *
  * Compile with -ffp-contract=off: the only floating-point decisions that feed
  * an integer (none: the bin index is computed in exact integer arithmetic)
@@ -359,6 +361,10 @@ static double ks_val(const ksum *a) { return a->s + a->c; }
 /* are the grid's double-double right edges ([d][nb]; Blo may be NULL).     */
 /* Returns OR_ENONFINITE if any F is not finite.                             */
 /* ------------------------------------------------------------------------ */
+/* one_dim != 0 selects the m-Cubes1D variant (Sec. 3, "The m-Cubes1D     */
+/* variant"): every axis shares one set of bin boundaries, so only axis 0  */
+/* keeps a histogram: C[0][k_0] (and H[0][k_0]) alone are added to; the    */
+/* map itself is unchanged (the caller passes a grid whose rows are equal).*/
 typedef struct {
     int id;
     const double *params;
@@ -366,6 +372,7 @@ typedef struct {
     const double *lo, *hi;
     int64_t g, m, p;
     uint64_t seed;
+    int one_dim;
 } oracle_problem;
 
 int oracle_vsample(const oracle_problem *pb, const double *B, const double *Blo, uint32_t it, int adjust,
@@ -406,7 +413,8 @@ int oracle_vsample(const oracle_problem *pb, const double *B, const double *Blo,
             if (!isfinite(v)) status = OR_ENONFINITE;
             F[s] = v;
             if (adjust) {
-                for (int j = 0; j < d; ++j) {
+                const int hist_axes = pb->one_dim ? 1 : d;
+                for (int j = 0; j < hist_axes; ++j) {
                     if (Cs) ks_add(&Cs[j * nb + kbin[j]], v * v);
                     if (H) H[j * nb + kbin[j]] += 1;
                 }
@@ -551,12 +559,15 @@ void oracle_weighted(int n, const double *I_it, const double *var_it, double rel
 /* (itmax entries) = per-iteration estimate and variance, B_out ([d][nb])   */
 /* = final grid, C_out ([d][nb]) = histogram of the last adjusting          */
 /* iteration.                                                                */
+/* one_dim != 0 runs the m-Cubes1D variant (Sec. 3): the histogram of axis  */
+/* 0 alone is kept, that axis is rebinned, and its new boundaries become    */
+/* every axis's boundaries, so that all axes always share one grid.         */
 /* ------------------------------------------------------------------------ */
 int oracle_integrate(int id, const double *params, int d, const double *lo, const double *hi,
                      int64_t ncall, int itmax, int ita, int nb, int64_t g_override,
                      double alpha, uint64_t seed, double rel_tol, double abs_tol,
                      double *res, int *iters_out, int *conv_out, int64_t *geom_out,
-                     double *trace_I, double *trace_var, double *B_out, double *C_out)
+                     double *trace_I, double *trace_var, double *B_out, double *C_out, int one_dim)
 {
     if (itmax < 1 || d < 1 || d > OR_DMAX || nb < 2 || nb > OR_NBMAX) return OR_EINVAL;
     if (oracle_nparams(id, d) < 0) return OR_EINVAL;
@@ -572,7 +583,7 @@ int oracle_integrate(int id, const double *params, int d, const double *lo, cons
     double *hV = (double *)malloc(sizeof(double) * itmax);
     if (!B || !Blo || !C || !hI || !hV) { free(B); free(Blo); free(C); free(hI); free(hV); return OR_ENOMEM; }
     oracle_init_grid(d, nb, B, Blo);
-    oracle_problem pb = {id, params, d, nb, lo, hi, g, m, p, seed};
+    oracle_problem pb = {id, params, d, nb, lo, hi, g, m, p, seed, one_dim};
     double est = 0, sig = 0, chi2 = 0;
     int conv = 0, n = 0;
     st = OR_OK;
@@ -592,9 +603,14 @@ int oracle_integrate(int id, const double *params, int d, const double *lo, cons
         oracle_weighted(n, hI, hV, rel_tol, abs_tol, &est, &sig, &chi2, &conv);
         if (adjust) {
             if (C_out) memcpy(C_out, C, sizeof(double) * d * nb);
-            for (int j = 0; j < d; ++j) {
+            const int rebinned = one_dim ? 1 : d;
+            for (int j = 0; j < rebinned; ++j) {
                 int r = oracle_rebin_axis(nb, alpha, C + (size_t)j * nb, B + (size_t)j * nb, Blo + (size_t)j * nb);
                 if (r == OR_ENONFINITE) st = OR_ENONFINITE;
+            }
+            for (int j = rebinned; j < d; ++j) {   /* m-Cubes1D: the shared boundaries */
+                memcpy(B + (size_t)j * nb, B, sizeof(double) * nb);
+                memcpy(Blo + (size_t)j * nb, Blo, sizeof(double) * nb);
             }
             if (st) break;
         }

@@ -137,6 +137,9 @@ mcubes_status mcubes_create_on_stream(mcubes_ctx** out, int device, const mcubes
 /* Replaces the options of an existing context (takes effect at the next setup). */
 mcubes_status mcubes_set_opts(mcubes_ctx* ctx, const mcubes_opts* opts);
 
+/* Copies the context's current options to *out.  Errors: EINVAL (null). */
+mcubes_status mcubes_get_opts(mcubes_ctx* ctx, mcubes_opts* out);
+
 /* Releases the context and all its device memory. NULL is accepted. */
 mcubes_status mcubes_destroy(mcubes_ctx* ctx);
 
@@ -256,6 +259,40 @@ mcubes_status mcubes_grid_set(mcubes_ctx* ctx, const double* B, long long count)
  * adjusting iteration. */
 mcubes_status mcubes_hist_get(mcubes_ctx* ctx, double* C, long long count);
 
+/* ---- checkpoint / resume ------------------------------------------------
+ * The paper has no counterpart: these serialise the state of the current
+ * problem so that a long run can stop and continue in another process.
+ * The checkpoint holds the problem as given to mcubes_setup (integrand id,
+ * params, box, ncall, itmax, tolerances), the context's options, the bin
+ * grid with the low parts of its double-double edges, the number of
+ * iterations enqueued, and the device iteration state (index, flags,
+ * weighted result and per-iteration history).  Layout: a fixed header
+ * (magic "MCUBESCK", format version, byte sizes) followed by the grid and
+ * the iteration state as native-endian doubles and integers; it is meant
+ * for the same library build, not as an interchange format.
+ *
+ * mcubes_state_size: *bytes receives the size of the current problem's
+ *   checkpoint.  Errors: EINVAL (null), ESTATE (no setup).
+ * mcubes_state_export: waits for the context's stream, then writes the
+ *   checkpoint to buf (host, cap bytes; caller-owned).  Errors: EINVAL (null
+ *   or cap too small), ESTATE, ECUDA.
+ * mcubes_state_import: replaces the context's options and problem with the
+ *   checkpoint's (as mcubes_set_opts + mcubes_setup would), then restores
+ *   its grid and iteration state; mcubes_iterate then continues with the
+ *   next iteration.  On the same GPU model, the continued run's results,
+ *   trace and grid are bit-identical to those of an uninterrupted run (the
+ *   launch shape derives from the options and the SM count).  Errors:
+ *   EINVAL (null, wrong magic or version, inconsistent sizes, an invalid
+ *   problem or grid), ENOMEM, ECUDA; on error the context has no problem. */
+mcubes_status mcubes_state_size(mcubes_ctx* ctx, long long* bytes);
+/* The current problem's integrand id, dimension, bins per axis, itmax and
+ * the number of iterations enqueued so far (any pointer may be NULL).
+ * Errors: EINVAL (null ctx), ESTATE (no setup). */
+mcubes_status mcubes_problem_get(mcubes_ctx* ctx, int* integrand_id, int* d, int* nb, int* itmax,
+                                 int* iterations_enqueued);
+mcubes_status mcubes_state_export(mcubes_ctx* ctx, void* buf, long long cap);
+mcubes_status mcubes_state_import(mcubes_ctx* ctx, const void* buf, long long size);
+
 /* One sampling pass (Alg. 3) over sub-cubes [cube_begin, cube_end) of
  * iteration `it` with the current grid, leaving the context's state
  * untouched; blocks.  sums (host, 3 values) receives the sum over those
@@ -305,6 +342,16 @@ mcubes_status mcubes_sample_range_noalloc(int device, int integrand_id, const do
                                           unsigned it, int adjust, long long cube_begin, long long cube_end,
                                           const double* d_grid, double* d_sums, double* d_hist,
                                           void* cuda_stream);
+
+/* Diagnostic: evaluates, element-wise over n doubles of the device array
+ * d_in into d_out (device), the library's double-precision logarithm
+ * (which = 0) or exponential (1) -- table-driven with fixed-point series,
+ * used by the FP64 integrands -- or CUDA's log (2) or exp (3), on
+ * cuda_stream (NULL = legacy default stream); returns without waiting.
+ * The paper has no counterpart; this exists to test accuracy.
+ * Errors: EINVAL, ECUDA. */
+mcubes_status mcubes_selftest_fxmath(int which, long long n, const double* d_in, double* d_out,
+                                     void* cuda_stream);
 
 /* Geometry of the current setup: sub-cubes per axis, sub-cubes, samples per
  * sub-cube, lanes per cube and sampling blocks chosen. */

@@ -280,7 +280,7 @@ mcubes_status BatchEngine::admit(const mcubes_request& r, long long tag, int* sl
     D.ita = opts_.ita < 0 ? r.itmax : std::min(opts_.ita, r.itmax);
     D.itmax = r.itmax;
     D.m = (uint64_t)m;
-    D.phi_scale = std::ldexp(1.0 / ((double)g * nb), -33);
+    D.jac0 = jacobian_scale(g, nb, d);
     D.phi_scale_f = (float)(1.0 / ((double)g * nb));
     for (int j = 0; j < d; ++j) {
         D.lo[j] = r.lo[j];

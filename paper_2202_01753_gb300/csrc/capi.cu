@@ -200,6 +200,15 @@ uint64_t cube_permutation(uint64_t n)
     return k;
 }
 
+// Constant factor of the FP64 kernels' Jacobian: their cells hold the bin
+// width over g, and each axis contributes nb * width to J.
+double jacobian_scale(long long g, long long nb, int d)
+{
+    double j = 1.0;
+    for (int i = 0; i < d; ++i) j *= (double)g * (double)nb;
+    return j;
+}
+
 void philox_round_keys(uint64_t seed, uint32_t rk[10][2])
 {
     uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
@@ -347,6 +356,13 @@ mcubes_status mcubes_set_opts(mcubes_ctx* c, const mcubes_opts* o)
     return MCUBES_OK;
 }
 
+mcubes_status mcubes_get_opts(mcubes_ctx* c, mcubes_opts* out)
+{
+    if (!c || !out) return MCUBES_EINVAL;
+    *out = c->opts;
+    return MCUBES_OK;
+}
+
 mcubes_status mcubes_destroy(mcubes_ctx* c)
 {
     if (!c) return MCUBES_OK;
@@ -457,7 +473,7 @@ mcubes_status mcubes_setup(mcubes_ctx* c, int id, const double* params, int npar
         a.lo[j] = lo[j];
         a.scale[j] = hi[j] - lo[j];
     }
-    a.phi_scale = std::ldexp(1.0 / ((double)g * nb), -33);
+    a.jac0 = jacobian_scale(g, nb, d);
     a.phi_scale_f = (float)(1.0 / ((double)g * nb));
     a.nb_f = (float)nb;
     a.fam = fp;
@@ -485,6 +501,11 @@ mcubes_status mcubes_setup(mcubes_ctx* c, int id, const double* params, int npar
     MC_CHECK(c, launch_init_grid((double*)c->grid.ptr, (double*)c->grid.ptr + (size_t)d * nb, d, nb, c->stream));
     MC_CHECK(c, cudaMemsetAsync(c->hist.ptr, 0, sizeof(double) * d * nb, c->stream));
     MC_CHECK(c, cudaStreamSynchronize(c->stream));  // hst lives on this stack frame
+    c->prob_params.assign(params, params + std::max(nparams, 0));
+    c->prob_lo.assign(lo, lo + d);
+    c->prob_hi.assign(hi, hi + d);
+    c->rel_tol = rel_tol;
+    c->abs_tol = abs_tol;
     c->it_enqueued = 0;
     c->ready = true;
     return MCUBES_OK;

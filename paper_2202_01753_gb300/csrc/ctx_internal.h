@@ -20,8 +20,10 @@ struct mcubes_ctx {
     int num_sms = 0;
     char cuda_err[256] = {0};
 
-    // current problem
+    // current problem (as given to mcubes_setup, kept for checkpoints)
     bool ready = false;
+    std::vector<double> prob_params, prob_lo, prob_hi;
+    double rel_tol = 0.0, abs_tol = 0.0;
     int fid = 0, d = 0, nb = 0, itmax = 0, ita = 0;
     long long ncall = 0, g = 0, m = 0, p = 0;
     bool mixed = false;

@@ -5,6 +5,7 @@
 
 #include <cstdint>
 
+#include "fx_math.cuh"
 #include "mc_internal.h"
 
 namespace mc {
@@ -93,7 +94,7 @@ __device__ __forceinline__ uint4 sample_words(const VsArgs& a, uint4 ctr) { retu
 // constants stay in shared memory).
 struct BatchView {
     uint32_t d, nb, g, gmagic, key0, key1;
-    double phi_scale;
+    double jac0;
     float phi_scale_f;
     const FamParams& fam;
 };
@@ -137,12 +138,24 @@ __device__ __forceinline__ BinPos bin_pos(uint32_t w, uint32_t nb_c, uint32_t nb
     return b;
 }
 
-// phi scaled by `scale`: (r 2^33 + a_lo) * scale, with scale = 2^-33 / g for
-// phi itself (the numerator is exact below 2^53); the kernels fold 1/nb in.
-__device__ __forceinline__ double bin_phi_f64(const BinPos& b, double scale)
+// g phi = r + a_lo 2^-33 as a double, built from the integer numerator
+// r 2^33 + a_lo with integer operations only (exact below 2^53, rounded to
+// nearest above): no FP64 conversion or multiply in the sampling loop.
+__device__ __forceinline__ double bin_gphi_f64(const BinPos& b)
 {
-    const uint64_t num = ((uint64_t)b.r << 33) | ((uint64_t)b.ahi << 32) | (uint64_t)b.alo;
-    return __ull2double_rn(num) * scale;
+    const uint64_t num = ((uint64_t)b.r << 33) | ((uint64_t)b.ahi << 32) | (uint64_t)b.alo;  // < 2^63
+    const int lz = __clzll((long long)num);
+    uint64_t m;  // num with its leading one moved to bit 52 (bit 53 after a rounding carry)
+    if (lz >= 11) {
+        m = num << (lz - 11);
+    } else {
+        const int sh = 11 - lz;
+        m = (num + (1ull << (sh - 1))) >> sh;
+    }
+    // value 2^(63 - lz - 33) (m / 2^52): biased exponent 1053 - lz, stored as
+    // (exponent - 1) << 52 plus m, whose leading one adds the missing 1
+    const uint64_t bits = ((uint64_t)(1052 - lz) << 52) + m;
+    return num ? __longlong_as_double((long long)bits) : 0.0;
 }
 
 // the same in single precision: (r + a_lo 2^-33) * scale, scale = 1/g for phi
@@ -168,8 +181,9 @@ __device__ __forceinline__ float bin_phi_f32(const BinPos& b, float scale)
 // ---------------------------------------------------------------------------
 template <typename R> struct RealOps;
 template <> struct RealOps<double> {
-    __device__ static double exp_(double v) { return exp(v); }
-    __device__ static double log_(double v) { return log(v); }
+    // fixed-point table-driven versions: a few FP64 operations instead of tens
+    __device__ static double exp_(double v) { return fx::fx_exp(v); }
+    __device__ static double log_(double v) { return fx::fx_log(v); }
     __device__ static double cos_(double v) { return cos(v); }
     __device__ static double rcp(double v) { return 1.0 / v; }
     __device__ static double par(const FamParams& f, int i) { return f.c[i]; }

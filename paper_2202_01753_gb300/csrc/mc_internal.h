@@ -63,8 +63,8 @@ struct VsArgs {
     uint32_t rk[10][2];       // Philox round keys (key + r * Weyl constants)
     double lo[kDMax];
     double scale[kDMax];      // hi - lo
-    double phi_scale;         // 2^-33 / (g nb): bin numerator -> phi / nb
-    float phi_scale_f;        // 1 / (g nb)
+    double jac0;              // (g nb)^d: FP64 cells hold width / g, so J = jac0 prod(cell widths)
+    float phi_scale_f;        // 1 / (g nb): mixed cells hold nb width, so x = left + (nb width)(g phi)/(g nb)
     float nb_f;
     FamParams fam;
 };
@@ -80,7 +80,7 @@ struct BatchDesc {
     uint32_t key0, key1;        // Philox key = the integral's own seed
     int family, ita, itmax, pad;
     uint64_t m;
-    double phi_scale;           // 2^-33 / (g nb)
+    double jac0;                // (g nb)^d
     float phi_scale_f;          // 1 / (g nb)
     float pad2;
     double lo[kDMax];
@@ -158,6 +158,7 @@ cudaError_t launch_vsample(int family, bool mixed, bool adjust, const VsArgs& a,
 size_t vsample_smem_bytes(bool mixed, bool adjust, int d, int nb);
 cudaError_t vsample_occupancy(int family, bool mixed, bool adjust, int d, size_t smem, int* blocks_per_sm);
 uint64_t cube_permutation(uint64_t n);
+double jacobian_scale(long long g, long long nb, int d);  // (g nb)^d
 
 cudaError_t launch_refine(const RefineArgs& a, cudaStream_t s);
 cudaError_t launch_reduce_range(const double* part, const void* part_hist, int hist_is_float,

@@ -131,7 +131,7 @@ extern "C" mcubes_status mcubes_sample_range_noalloc(
             a.lo[j] = lo[j];
             a.scale[j] = hi[j] - lo[j];
         }
-        a.phi_scale = std::ldexp(1.0 / ((double)g * nbins), -33);
+        a.jac0 = jacobian_scale(g, nbins, d);
         a.phi_scale_f = (float)(1.0 / ((double)g * nbins));
         a.nb_f = (float)nbins;
         a.fam = fp;

@@ -24,22 +24,22 @@ namespace mc {
 template <bool MIXED> struct Prec;
 template <> struct Prec<false> {
     using R = double;
-    using Cell = double2;  // (x left edge, nb * x width): x = left + (nb*width)(phi/nb), J factor = nb*width
+    using Cell = double2;  // (x left edge, x width / g): x = left + (width/g)(g phi), J factor = (g nb)(width/g)
     using H = double;
 };
 template <> struct Prec<true> {
     using R = float;
-    using Cell = float2;
+    using Cell = float2;   // (x left edge, nb * x width): x = left + (nb width)(phi/nb), J factor = nb width
     using H = float;
 };
 
 // Stages the grid of all axes into shared-memory cells and clears the
 // histogram.  grid/grid_lo: [d][nb] double-double right edges (unit cube);
-// lo/scale: the box's lower corner and hi - lo.
+// lo/scale: the box's lower corner and hi - lo; g: sub-cubes per axis.
 template <bool MIXED, bool ADJ, class Arr>
 __device__ __forceinline__ void stage_grid(typename Prec<MIXED>::Cell* cells, typename Prec<MIXED>::H* hist,
                                            const double* grid, const double* grid_lo, const Arr& lo,
-                                           const Arr& scale, uint32_t d, uint32_t nb)
+                                           const Arr& scale, uint32_t d, uint32_t nb, uint32_t g)
 {
     for (uint32_t i = threadIdx.x; i < d * nb; i += blockDim.x) {
         const uint32_t j = i / nb, k = i - j * nb;
@@ -47,16 +47,16 @@ __device__ __forceinline__ void stage_grid(typename Prec<MIXED>::Cell* cells, ty
         const DD left = k ? DD{grid[i - 1], grid_lo[i - 1]} : DD{0.0, 0.0};
         const DD wd = dd_add(right, DD{-left.hi, -left.lo});
         const double xl = lo[j] + scale[j] * left.hi;
-        const double xwn = scale[j] * (wd.hi + wd.lo) * (double)nb;
-        if constexpr (MIXED) cells[i] = make_float2((float)xl, (float)xwn);
-        else cells[i] = make_double2(xl, xwn);
+        const double xw = scale[j] * (wd.hi + wd.lo);
+        if constexpr (MIXED) cells[i] = make_float2((float)xl, (float)(xw * (double)nb));
+        else cells[i] = make_double2(xl, xw / (double)g);
         if constexpr (ADJ) hist[i] = typename Prec<MIXED>::H(0);
     }
 }
 
 // One sample: random words -> exact bin position -> map -> integrand.
 // Returns F = f(x) * J and leaves the flat histogram index of every axis in
-// idx (16 bits each, two per word).  A provides d, nb, g, gmagic, phi_scale (2^-33/(g nb)), phi_scale_f
+// idx (16 bits each, two per word).  A provides d, nb, g, gmagic, jac0 ((g nb)^d), phi_scale_f
 // (1/(g nb)) and fam, and sample_words(a, counter) its Philox block.
 template <int FAM, bool MIXED, int NB4, class A>
 __device__ __forceinline__ typename Prec<MIXED>::R
@@ -80,7 +80,9 @@ sample_point(const A& a, const typename Prec<MIXED>::Cell* cells, uint32_t c, ui
     }
     typename Fam::S fs;
     Fam::begin(fs);
-    R jac = R(1);
+    R jac;
+    if constexpr (MIXED) jac = 1.0f;
+    else jac = a.jac0;
 #pragma unroll
     for (int j = 0; j < DN; ++j) {
         if (j < (int)d) {
@@ -92,8 +94,7 @@ sample_point(const A& a, const typename Prec<MIXED>::Cell* cells, uint32_t c, ui
                 const float phin = bin_phi_f32(bp, a.phi_scale_f);   // phi / nb
                 x = fmaf(cell.y, phin, cell.x);
             } else {
-                const double phin = bin_phi_f64(bp, a.phi_scale);     // phi / nb
-                x = fma(cell.y, phin, cell.x);
+                x = fma(cell.y, bin_gphi_f64(bp), cell.x);            // (width/g)(g phi)
             }
             jac *= cell.y;
             Fam::add(fs, j, x, a.fam);
@@ -281,7 +282,7 @@ vsample_kernel(const __grid_constant__ VsArgs a)
 
     Cell* cells = reinterpret_cast<Cell*>(smem);
     HT* hist = reinterpret_cast<HT*>(smem + cell_bytes(MIXED) * d * nb);
-    stage_grid<MIXED, ADJ>(cells, hist, a.grid, a.grid_lo, a.lo, a.scale, d, nb);
+    stage_grid<MIXED, ADJ>(cells, hist, a.grid, a.grid_lo, a.lo, a.scale, d, nb, a.g);
     __syncthreads();
 
     CubeSums acc;

@@ -1,0 +1,89 @@
+"""Generates csrc/fx_tables.h: the tables of the fixed-point logarithm and
+exponential used by the double-precision kernels (csrc/fx_math.cuh).
+
+Table-driven reduction after P. T. P. Tang, "Table-driven implementation of
+the logarithm function in IEEE floating-point arithmetic", ACM TOMS 16(4),
+1990, and "Table-driven implementation of the exponential function in IEEE
+floating-point arithmetic", ACM TOMS 15(2), 1989:
+
+* log: c_j = 1 + (j + 1/2)/256 for j = 0..255; 1/c_j as an unsigned Q63
+  integer and ln(c_j) as an unsigned Q64 fraction; ln 2 to 128 bits.
+* exp: 2^(j/256) for j = 0..255 as unsigned Q62 integers.
+
+Values are computed with 60-digit mpmath arithmetic and rounded once.
+Run from the repository root: python -m paper_2202_01753_gb300.gen_fx_tables
+"""
+from __future__ import annotations
+
+import os
+
+import mpmath
+
+OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc", "fx_tables.h")
+
+
+def _dd(x):
+    hi = float(x)
+    lo = float(x - mpmath.mpf(hi))
+    return hi, lo
+
+
+def tables():
+    mpmath.mp.dps = 60
+    inv_c, log_q64, exp2 = [], [], []
+    for j in range(256):
+        c = 1 + (mpmath.mpf(j) + mpmath.mpf("0.5")) / 256
+        inv_c.append(int(mpmath.nint(2 ** 63 / c)))
+        log_q64.append(int(mpmath.nint(2 ** 64 * mpmath.log(c))))
+        exp2.append(int(mpmath.nint(2 ** 62 * mpmath.power(2, mpmath.mpf(j) / 256))))
+    ln2 = mpmath.log(2)
+    return inv_c, log_q64, exp2, ln2
+
+
+def render():
+    inv_c, log_q64, exp2, ln2 = tables()
+    mpmath.mp.dps = 60
+    # ln 2 as a 128-bit binary fraction (two 64-bit words)
+    ln2_q128 = int(mpmath.floor(ln2 * 2 ** 128))
+    ln2_w1, ln2_w2 = ln2_q128 >> 64, ln2_q128 & (2 ** 64 - 1)
+    # ln 2 / 256 split for the exponential's Cody-Waite reduction: n * hi must
+    # be exact for |n| < 2^19, so hi keeps 34 significant bits
+    c = ln2 / 256
+    c_hi = float(mpmath.floor(c * 2 ** 42) / 2 ** 42)
+    c_lo = float(c - mpmath.mpf(c_hi))
+    lines = [
+        "// fx_tables.h -- generated by paper_2202_01753_gb300/gen_fx_tables.py (do not edit).",
+        "// Tables of the fixed-point logarithm and exponential (fx_math.cuh).",
+        "#pragma once",
+        "",
+        "#include <cstdint>",
+        "",
+        "namespace mc {",
+        "namespace fx {",
+        "",
+        f"constexpr uint64_t kLn2W1 = 0x{ln2_w1:016x}ull;  // ln 2 = (W1 + W2 2^-64) 2^-64",
+        f"constexpr uint64_t kLn2W2 = 0x{ln2_w2:016x}ull;",
+        f"constexpr double kLn2Over256Hi = {c_hi!r};",
+        f"constexpr double kLn2Over256Lo = {c_lo!r};",
+        f"constexpr double k256OverLn2 = {float(256 / ln2)!r};",
+        "",
+        "// 1 / c_j, c_j = 1 + (j + 1/2)/256, as Q63",
+        "__device__ const uint64_t kLogInvC[256] = {",
+    ]
+    for i in range(0, 256, 4):
+        lines.append("    " + ", ".join(f"0x{v:016x}ull" for v in inv_c[i:i + 4]) + ",")
+    lines += ["};", "", "// ln c_j as Q64 (a binary fraction; 0 < ln c_j < ln 2)",
+              "__device__ const uint64_t kLogCQ64[256] = {"]
+    for i in range(0, 256, 4):
+        lines.append("    " + ", ".join(f"0x{v:016x}ull" for v in log_q64[i:i + 4]) + ",")
+    lines += ["};", "", "// 2^(j/256) as Q62", "__device__ const uint64_t kExp2[256] = {"]
+    for i in range(0, 256, 4):
+        lines.append("    " + ", ".join(f"0x{v:016x}ull" for v in exp2[i:i + 4]) + ",")
+    lines += ["};", "", "}  // namespace fx", "}  // namespace mc", ""]
+    return "\n".join(lines)
+
+
+if __name__ == "__main__":
+    with open(OUT, "w") as f:
+        f.write(render())
+    print(OUT)

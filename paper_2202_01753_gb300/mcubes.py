@@ -27,6 +27,8 @@ EXPORTED = [
     "mcubes_sample_range", "mcubes_geometry_get", "mcubes_timing_reset", "mcubes_timing_get",
     "mcubes_sample_range_noalloc", "mcubes_server_create", "mcubes_server_destroy", "mcubes_server_submit",
     "mcubes_server_step", "mcubes_server_poll", "mcubes_server_stats", "mcubes_server_run_stream",
+    "mcubes_selftest_fxmath", "mcubes_state_size", "mcubes_state_export", "mcubes_state_import",
+    "mcubes_problem_get", "mcubes_get_opts",
 ]
 
 
@@ -110,6 +112,14 @@ def lib():
                 "mcubes_server_stats": (ctypes.c_int, [ctypes.c_void_p, P(ll), P(ll), P(ll), P(ll), P(ll)]),
                 "mcubes_server_run_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, P(mcubes_request), dp,
                                                             P(mcubes_result), dp, dp]),
+                "mcubes_get_opts": (ctypes.c_int, [ctx, P(mcubes_opts)]),
+                "mcubes_state_size": (ctypes.c_int, [ctx, P(ll)]),
+                "mcubes_state_export": (ctypes.c_int, [ctx, ctypes.c_void_p, ll]),
+                "mcubes_state_import": (ctypes.c_int, [ctx, ctypes.c_void_p, ll]),
+                "mcubes_problem_get": (ctypes.c_int, [ctx, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int),
+                                                      P(ctypes.c_int), P(ctypes.c_int)]),
+                "mcubes_selftest_fxmath": (ctypes.c_int, [ctypes.c_int, ll, ctypes.c_void_p, ctypes.c_void_p,
+                                                          ctypes.c_void_p]),
                 "mcubes_sample_range_noalloc": (ctypes.c_int, [
                     ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, dp, dp, ll, ctypes.c_int, ll,
                     ctypes.c_uint64, ctypes.c_int, ctypes.c_uint, ctypes.c_int, ll, ll, ctypes.c_void_p,
@@ -269,6 +279,29 @@ class Context:
     def set_grid(self, B):
         B = _f64(B).reshape(-1)
         self._check(lib().mcubes_grid_set(self._h, _dp(B), B.size), "mcubes_grid_set")
+
+    def problem(self):
+        v = [ctypes.c_int() for _ in range(5)]
+        self._check(lib().mcubes_problem_get(self._h, *[ctypes.byref(x) for x in v]), "mcubes_problem_get")
+        return dict(zip(["fid", "d", "nb", "itmax", "enqueued"], [x.value for x in v]))
+
+    def state_export(self):
+        """Checkpoint of the current problem (waits for the stream) as bytes."""
+        n = ctypes.c_longlong()
+        self._check(lib().mcubes_state_size(self._h, ctypes.byref(n)), "mcubes_state_size")
+        buf = ctypes.create_string_buffer(n.value)
+        self._check(lib().mcubes_state_export(self._h, buf, n.value), "mcubes_state_export")
+        return buf.raw
+
+    def state_import(self, blob):
+        """Restores a checkpoint made by state_export: options, problem, grid and iteration state."""
+        buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+        self._check(lib().mcubes_state_import(self._h, buf, len(blob)), "mcubes_state_import")
+        o = mcubes_opts()
+        self._check(lib().mcubes_get_opts(self._h, ctypes.byref(o)), "mcubes_get_opts")
+        self.opts = o
+        pr = self.problem()
+        self.d, self.nb = pr["d"], pr["nb"]
 
     def hist(self):
         C = np.zeros(self.d * self.nb)

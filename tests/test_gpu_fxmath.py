@@ -1,0 +1,64 @@
+"""Accuracy of the library's double-precision log and exp (table-driven,
+fixed-point series; used by the FP64 integrands) against 40-digit
+references and against CUDA's own functions."""
+import math
+
+import mpmath
+import numpy as np
+import pytest
+
+from paper_2202_01753_gb300 import mcubes
+
+pytestmark = pytest.mark.gpu
+
+
+def _eval(torch, which, xs):
+    d_in = torch.tensor(xs, dtype=torch.float64, device="cuda")
+    d_out = torch.empty_like(d_in)
+    st = mcubes.lib().mcubes_selftest_fxmath(which, len(xs), d_in.data_ptr(), d_out.data_ptr(),
+                                             torch.cuda.current_stream().cuda_stream)
+    assert st == mcubes.OK
+    torch.cuda.synchronize()
+    return d_out.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def torch_cuda(gpu_ctx_factory):
+    import torch
+    return torch
+
+
+def test_log_accuracy(torch_cuda):
+    rng = np.random.default_rng(3)
+    xs = np.concatenate([np.exp(rng.uniform(-700, 700, 3000)), rng.uniform(0.01, 5.0, 3000),
+                         1.0 + rng.uniform(-1e-3, 1e-3, 500), [1.0, 2.0, 0.5, 0.05, 1e-300, 1.7e308]])
+    got = _eval(torch_cuda, 0, xs)
+    cuda = _eval(torch_cuda, 2, xs)
+    mpmath.mp.dps = 40
+    for x, g, c in zip(xs[::3], got[::3], cuda[::3]):
+        ref = mpmath.log(mpmath.mpf(float(x)))
+        err = abs(mpmath.mpf(float(g)) - ref)
+        assert err <= math.ulp(float(ref)) * 1.01 + 2.0 ** -58, (x, g, float(ref))
+    # against CUDA's log: within 2 ulp plus the absolute term everywhere
+    tol = 2 * np.spacing(np.abs(cuda)) + 2.0 ** -57
+    assert np.all(np.abs(got - cuda) <= tol)
+    # outside the fast range it defers to CUDA's log
+    special = np.array([0.0, -1.0, np.inf, np.nan, 1e-310])
+    g, c = _eval(torch_cuda, 0, special), _eval(torch_cuda, 2, special)
+    assert np.array_equal(np.isnan(g), np.isnan(c)) and np.all((g == c) | np.isnan(g))
+
+
+def test_exp_accuracy(torch_cuda):
+    rng = np.random.default_rng(4)
+    ys = np.concatenate([rng.uniform(-707.9, 708.9, 3000), rng.uniform(-3, 3, 3000),
+                         rng.uniform(-1e-6, 1e-6, 500), [0.0, 1.0, -1.0, 0.0013, -700.0, 700.0]])
+    got = _eval(torch_cuda, 1, ys)
+    cuda = _eval(torch_cuda, 3, ys)
+    mpmath.mp.dps = 40
+    for y, g in zip(ys[::3], got[::3]):
+        ref = mpmath.exp(mpmath.mpf(float(y)))
+        assert abs(mpmath.mpf(float(g)) - ref) / ref <= 2.0 ** -52, (y, g, float(ref))
+    assert np.all(np.abs(got - cuda) <= 2 * np.spacing(np.abs(cuda)))
+    special = np.array([-800.0, 800.0, -np.inf, np.inf, np.nan, -708.5, 709.5])
+    g, c = _eval(torch_cuda, 1, special), _eval(torch_cuda, 3, special)
+    assert np.array_equal(np.isnan(g), np.isnan(c)) and np.all((g == c) | np.isnan(g))

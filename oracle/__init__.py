@@ -28,7 +28,9 @@ OK, EINVAL, ENOMEM, ENONFINITE, ENOCONV = 0, 1, 2, 4, 5
 DMAX, NBMAX = 12, 1024
 
 # integrand family ids (same values as the CUDA library's registry)
-F_CONST, F_GAUSS, F_CORNER, F_OSC, F_PRODPEAK, F_C0, F_DISCONT, F_COSMO6 = range(8)
+F_CONST, F_GAUSS, F_CORNER, F_OSC, F_PRODPEAK, F_C0, F_DISCONT, F_COSMO6, F_TABLE = range(9)
+
+_tables_keep = []   # the arrays the C oracle points to
 
 _lock = threading.Lock()
 _lib_handle = None
@@ -74,6 +76,10 @@ def _lib():
             h.oracle_vsample.argtypes = [ctypes.c_void_p, dp, dp, ctypes.c_uint32, ctypes.c_int,
                                          ctypes.c_uint64, ctypes.c_uint64, dp, dp,
                                          ctypes.POINTER(ctypes.c_uint64)]
+            ip = ctypes.POINTER(ctypes.c_int)
+            h.oracle_set_tables.argtypes = [ctypes.c_int, ip, ip, ip, dp, dp, dp, dp,
+                                            ctypes.POINTER(ctypes.POINTER(ctypes.c_double))]
+            h.oracle_table_params.argtypes = [dp, ctypes.c_int, ctypes.c_int]
             h.oracle_rebin_axis.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp, dp]
             h.oracle_weighted.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double,
                                           dp, dp, dp, ctypes.POINTER(ctypes.c_int)]
@@ -146,6 +152,39 @@ def bin_of(c, w, g, nb):
     phi = ctypes.c_double()
     _lib().oracle_bin_of(c, w, g, nb, ctypes.byref(k), ctypes.byref(phi))
     return k.value, phi.value
+
+
+def set_tables(tables):
+    """Interpolation tables of the TABLE family (Sec. 6.1's stateful
+    integrands): a list of dicts with ndim (1 or 2), values (n0 or n0 x n1
+    array, row-major) and the knot ranges lo, hi (scalars, or pairs for 2-D)."""
+    global _tables_keep
+    n = len(tables)
+    nd = (ctypes.c_int * max(n, 1))()
+    n0 = (ctypes.c_int * max(n, 1))()
+    n1 = (ctypes.c_int * max(n, 1))()
+    lo0, hi0, lo1, hi1 = (np.zeros(max(n, 1)) for _ in range(4))
+    vals = (ctypes.POINTER(ctypes.c_double) * max(n, 1))()
+    keep = []
+    for t, tb in enumerate(tables):
+        v = _f64(tb["values"])
+        keep.append(v)
+        nd[t] = int(tb["ndim"])
+        lo, hi = np.atleast_1d(tb["lo"]).astype(float), np.atleast_1d(tb["hi"]).astype(float)
+        n0[t] = v.shape[0]
+        n1[t] = v.shape[1] if nd[t] == 2 else 1
+        lo0[t], hi0[t] = lo[0], hi[0]
+        lo1[t], hi1[t] = (lo[1], hi[1]) if nd[t] == 2 else (0.0, 1.0)
+        vals[t] = _dp(v)
+    st = _lib().oracle_set_tables(n, nd, n0, n1, _dp(lo0), _dp(hi0), _dp(lo1), _dp(hi1), vals)
+    if st != OK:
+        raise ValueError("oracle_set_tables rejected the tables")
+    _tables_keep = keep
+
+
+def table_params_ok(params, d):
+    p = _f64(params)
+    return bool(_lib().oracle_table_params(_dp(p), len(p), d))
 
 
 def nparams(fid, d):

@@ -53,6 +53,69 @@
 #define OR_F_C0 5
 #define OR_F_DISCONT 6
 #define OR_F_COSMO6 7
+#define OR_F_TABLE 8
+
+/* ------------------------------------------------------------------------ */
+/* Interpolation tables of the TABLE family (the paper's stateful           */
+/* integrands, Sec. 6.1: integrands that read tabulated data at run time).  */
+/* A table holds values at uniformly spaced knots: n0 knots over            */
+/* [lo0, hi0] (and n1 over [lo1, hi1] for a 2-D table, values row-major,    */
+/* v[i0 * n1 + i1]).  Its value at a point is the linear (bilinear)         */
+/* interpolant of the knot values, the point first clamped into the table's */
+/* range.  The oracle keeps pointers to the caller's arrays.                */
+/* ------------------------------------------------------------------------ */
+#define OR_TABLES_MAX 16
+typedef struct {
+    int ndim, n0, n1;
+    double lo0, hi0, lo1, hi1;
+    const double *v;
+} or_table;
+static or_table g_tables[OR_TABLES_MAX];
+static int g_ntables = 0;
+
+int oracle_set_tables(int n, const int *ndim, const int *n0, const int *n1, const double *lo0,
+                      const double *hi0, const double *lo1, const double *hi1, const double *const *values)
+{
+    if (n < 0 || n > OR_TABLES_MAX) return OR_EINVAL;
+    for (int t = 0; t < n; ++t) {
+        if ((ndim[t] != 1 && ndim[t] != 2) || n0[t] < 2 || (ndim[t] == 2 && n1[t] < 2)) return OR_EINVAL;
+        if (!(lo0[t] < hi0[t]) || (ndim[t] == 2 && !(lo1[t] < hi1[t])) || !values[t]) return OR_EINVAL;
+    }
+    for (int t = 0; t < n; ++t) {
+        or_table tb = {ndim[t], n0[t], ndim[t] == 2 ? n1[t] : 1, lo0[t], hi0[t], lo1[t], hi1[t], values[t]};
+        g_tables[t] = tb;
+    }
+    g_ntables = n;
+    return OR_OK;
+}
+
+/* cell index and fraction of x on n knots over [lo, hi]: x clamped, then   */
+/* u = (x - lo) / h with h = (hi - lo)/(n - 1), i = floor(u) (at most n-2), */
+/* t = u - i.  (The interpolant is continuous at the knots, so which of two */
+/* cells a point on a knot is given to does not change the value.)          */
+static void table_cell(double x, int n, double lo, double hi, int *i, double *t)
+{
+    if (x < lo) x = lo;
+    if (x > hi) x = hi;
+    double h = (hi - lo) / (double)(n - 1);
+    double u = (x - lo) / h;
+    int k = (int)floor(u);
+    if (k > n - 2) k = n - 2;
+    if (k < 0) k = 0;
+    *i = k;
+    *t = u - (double)k;
+}
+
+static double table_value(const or_table *tb, double xa, double xb)
+{
+    int i, k;
+    double t, s;
+    table_cell(xa, tb->n0, tb->lo0, tb->hi0, &i, &t);
+    if (tb->ndim == 1) return (1.0 - t) * tb->v[i] + t * tb->v[i + 1];
+    table_cell(xb, tb->n1, tb->lo1, tb->hi1, &k, &s);
+    const double *r0 = tb->v + (size_t)i * tb->n1, *r1 = r0 + tb->n1;
+    return (1.0 - t) * (1.0 - s) * r0[k] + t * (1.0 - s) * r1[k] + (1.0 - t) * s * r0[k + 1] + t * s * r1[k + 1];
+}
 
 /* ------------------------------------------------------------------------ */
 /* Double-double numbers (an unevaluated sum hi + lo; Dekker 1971, Knuth     */
@@ -257,6 +320,8 @@ static void map_axis(const double *Bj, const double *Blj, int nb, double lo, dou
 /*   COSMO6   [a_1..6, mu, s, r, t]    f = prod x^-a * LN(x3) LN(x4)         */
 /*                                         * exp(-(x1+x2-r)^2/(2 t^2)),      */
 /*            LN(z) = exp(-(ln z - mu)^2/(2 s^2)) / (z s sqrt(2 pi))         */
+/*   TABLE    [c, nf, (tab, a, b) x nf] f = c prod_q T_tab_q(x_a_q [, x_b_q]) */
+/*            (axes 0-based; b = -1 for a 1-D table; 1 <= nf <= 10)          */
 /* ------------------------------------------------------------------------ */
 int oracle_nparams(int id, int d)
 {
@@ -267,8 +332,27 @@ int oracle_nparams(int id, int d)
     case OR_F_OSC: return 1 + d;
     case OR_F_PRODPEAK: case OR_F_C0: case OR_F_DISCONT: return 2 * d;
     case OR_F_COSMO6: return d == 6 ? 10 : -1;
+    case OR_F_TABLE: return 0;  /* variable: 2 + 3 nf, checked by oracle_table_params */
     default: return -1;
     }
+}
+
+/* The TABLE family's params (count np) against the tables set: returns 1   */
+/* if every factor names a table of the right dimension and valid axes.    */
+int oracle_table_params(const double *par, int np, int d)
+{
+    if (np < 2) return 0;
+    int nf = (int)par[1];
+    if ((double)nf != par[1] || nf < 1 || nf > 10 || np != 2 + 3 * nf) return 0;
+    for (int q = 0; q < nf; ++q) {
+        double tq = par[2 + 3 * q], aq = par[3 + 3 * q], bq = par[4 + 3 * q];
+        int t = (int)tq, a = (int)aq, b = (int)bq;
+        if ((double)t != tq || (double)a != aq || (double)b != bq) return 0;
+        if (t < 0 || t >= g_ntables || a < 0 || a >= d) return 0;
+        if (g_tables[t].ndim == 1 && b != -1) return 0;
+        if (g_tables[t].ndim == 2 && (b < 0 || b >= d || b == a)) return 0;
+    }
+    return 1;
 }
 
 double oracle_integrand(int id, const double *par, int d, const double *x)
@@ -326,6 +410,16 @@ double oracle_integrand(int id, const double *par, int d, const double *x)
         }
         double z = x[0] + x[1] - r;
         f *= exp(-(z * z) / (2.0 * t * t));
+        return f;
+    }
+    case OR_F_TABLE: {
+        double f = par[0];
+        int nf = (int)par[1];
+        for (int q = 0; q < nf; ++q) {
+            const or_table *tb = &g_tables[(int)par[2 + 3 * q]];
+            int a = (int)par[3 + 3 * q], b = (int)par[4 + 3 * q];
+            f *= table_value(tb, x[a], b >= 0 ? x[b] : 0.0);
+        }
         return f;
     }
     default:
@@ -571,6 +665,10 @@ int oracle_integrate(int id, const double *params, int d, const double *lo, cons
 {
     if (itmax < 1 || d < 1 || d > OR_DMAX || nb < 2 || nb > OR_NBMAX) return OR_EINVAL;
     if (oracle_nparams(id, d) < 0) return OR_EINVAL;
+    if (id == OR_F_TABLE) {
+        if (!(params[1] >= 1.0 && params[1] <= 10.0)) return OR_EINVAL;
+        if (!oracle_table_params(params, 2 + 3 * (int)params[1], d)) return OR_EINVAL;
+    }
     for (int j = 0; j < d; ++j) if (!(lo[j] < hi[j]) || !isfinite(lo[j]) || !isfinite(hi[j])) return OR_EINVAL;
     int64_t g, m, p;
     int st = oracle_geometry(d, ncall, g_override, nb, &g, &m, &p);

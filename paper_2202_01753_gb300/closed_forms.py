@@ -1,9 +1,11 @@
-"""Exact values of the test integrals, written from the mathematics.
+"""Exact values of the synthetic workloads' integrals, written from the
+mathematics (the true values of the paper's test suite, eqs. 1-6 of Sec. 5,
+and of the other families), for accuracy measurements and tests.
 
-These are independent of the oracle: every family's integral over a box is a
-product of one-dimensional integrals or follows by inclusion-exclusion, and
-the closed forms themselves are pinned by brute-force midpoint sums in
-test_closed_forms.py.
+These are independent of both the oracle and the CUDA path: every family's
+integral over a box is a product of one-dimensional integrals or follows by
+inclusion-exclusion, and the closed forms themselves are pinned by
+brute-force midpoint sums in tests/test_closed_forms.py.
 """
 from __future__ import annotations
 
@@ -15,7 +17,7 @@ import mpmath
 import numpy as np
 from scipy import integrate
 
-from paper_2202_01753_gb300 import workloads as W
+from . import workloads as W
 
 
 def gauss(params, lo, hi):
@@ -108,11 +110,61 @@ def cosmo6(params, lo, hi):
     return v
 
 
+def table_weights(n, tlo, thi, a, b):
+    """w_i = integral over [a, b] of the i-th piecewise-linear basis function
+    ("hat") of n uniform knots on [tlo, thi], extended by constants outside
+    the knot range, so that the integral of the linear interpolant of knot
+    values v over [a, b] is sum_i w_i v_i."""
+    h = (thi - tlo) / (n - 1)
+    k = tlo + h * np.arange(n - 1)                  # left knot of every cell
+    ta = np.clip((a - k) / h, 0.0, 1.0)
+    tb = np.clip((b - k) / h, 0.0, 1.0)
+    left = h * ((tb - tb ** 2 / 2) - (ta - ta ** 2 / 2))   # integral of 1 - t over the clipped cell
+    right = h * (tb ** 2 / 2 - ta ** 2 / 2)                # integral of t
+    w = np.zeros(n)
+    w[:-1] += left
+    w[1:] += right
+    w[0] += max(0.0, min(b, tlo) - a)                # constant extension below the range
+    w[-1] += max(0.0, b - max(a, thi))               # and above it
+    return w
+
+
+def table(params, lo, hi, tables):
+    """c prod_q T_q over a box, each axis used by at most one factor: the
+    product of the factors' integrals (exact for the linear and bilinear
+    interpolants, by their basis-function weights) and of the free axes'
+    lengths."""
+    d = len(lo)
+    c, nf = params[0], int(params[1])
+    used = set()
+    v = c
+    for q in range(nf):
+        t, a, b = int(params[2 + 3 * q]), int(params[3 + 3 * q]), int(params[4 + 3 * q])
+        tb = tables[t]
+        vals = np.asarray(tb["values"], dtype=np.float64)
+        axes = [a] if b < 0 else [a, b]
+        assert not used.intersection(axes), "closed form needs disjoint factor axes"
+        used.update(axes)
+        tlo, thi = np.atleast_1d(tb["lo"]), np.atleast_1d(tb["hi"])
+        w0 = table_weights(vals.shape[0], tlo[0], thi[0], lo[a], hi[a])
+        if b < 0:
+            v *= float(w0 @ vals)
+        else:
+            w1 = table_weights(vals.shape[1], tlo[1], thi[1], lo[b], hi[b])
+            v *= float(w0 @ (vals @ w1))
+    for j in range(d):
+        if j not in used:
+            v *= hi[j] - lo[j]
+    return v
+
+
 EXACT = {W.F_GAUSS: gauss, W.F_CORNER: corner, W.F_OSC: osc, W.F_PRODPEAK: prodpeak, W.F_C0: c0,
          W.F_DISCONT: discont, W.F_CONST: const, W.F_COSMO6: cosmo6}
 
 
 def exact(w: W.Workload) -> float:
+    if w.fid == W.F_TABLE:
+        return table(list(w.params), list(w.lo), list(w.hi), w.meta["tables"])
     return EXACT[w.fid](list(w.params), list(w.lo), list(w.hi))
 
 

@@ -15,9 +15,10 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-F_CONST, F_GAUSS, F_CORNER, F_OSC, F_PRODPEAK, F_C0, F_DISCONT, F_COSMO6 = range(8)
+F_CONST, F_GAUSS, F_CORNER, F_OSC, F_PRODPEAK, F_C0, F_DISCONT, F_COSMO6, F_TABLE = range(9)
 FAMILY_NAMES = {F_CONST: "const", F_GAUSS: "gauss", F_CORNER: "corner", F_OSC: "osc",
-                F_PRODPEAK: "prodpeak", F_C0: "c0", F_DISCONT: "discont", F_COSMO6: "cosmo6"}
+                F_PRODPEAK: "prodpeak", F_C0: "c0", F_DISCONT: "discont", F_COSMO6: "cosmo6",
+                F_TABLE: "table"}
 
 
 @dataclass
@@ -132,6 +133,40 @@ def batch4096(n: int = 4096, draw_seed: int = 2205, itmax: int = 10) -> list[Wor
         ncall = int(round(10 ** rng.uniform(4.0, 7.0)))
         out.append(random_integral(rng, d, fam, ncall, itmax, seed=1000 + i))
     return out
+
+
+def table6(seed: int = 0, draw_seed: int = 2207, n2: int = 4096, n1: int = 1 << 20,
+           ncall: int = 10 ** 8, itmax: int = 20) -> Workload:
+    """d=6 integrand that reads interpolation tables (a stand-in for the
+    paper's stateful cosmology integrand of Sec. 6.1, whose tables are not
+    available): f = T0(x1, x2) T1(x3) T2(x4) T3(x5, x6) on [0,1]^6 with
+      T0  n2 x n2 knots: Gaussian bump (centre ~U[0.3,0.7]^2, width 0.08) + 0.05
+      T1  n1 knots: power law (x + 0.05)^-a, a ~ U[0.2, 0.8]
+      T2  n1 knots: log-normal peak, median ~U[0.3, 0.6], shape 0.3
+      T3  n2 x n2 knots: Gaussian ridge along x5 + x6 = r, r ~ U[0.8, 1.2], width 0.03
+    The tables are returned in meta["tables"] (values as float64 arrays)."""
+    rng = np.random.Generator(np.random.PCG64(draw_seed))
+    cx, cy = rng.uniform(0.3, 0.7, size=2)
+    a = rng.uniform(0.2, 0.8)
+    med = rng.uniform(0.3, 0.6)
+    r = rng.uniform(0.8, 1.2)
+    k2 = np.linspace(0.0, 1.0, n2)
+    k1 = np.linspace(0.0, 1.0, n1)
+    X, Y = np.meshgrid(k2, k2, indexing="ij")
+    t0 = np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (2 * 0.08 ** 2)) + 0.05
+    t3 = np.exp(-((X + Y - r) ** 2) / (2 * 0.03 ** 2)) + 1e-3
+    del X, Y
+    t1 = (k1 + 0.05) ** -a
+    z = np.maximum(k1, 1e-6)
+    t2 = np.exp(-(np.log(z / med) ** 2) / (2 * 0.3 ** 2)) / z + 1e-3
+    tables = [dict(ndim=2, values=t0, lo=(0.0, 0.0), hi=(1.0, 1.0)),
+              dict(ndim=1, values=t1, lo=0.0, hi=1.0),
+              dict(ndim=1, values=t2, lo=0.0, hi=1.0),
+              dict(ndim=2, values=t3, lo=(0.0, 0.0), hi=(1.0, 1.0))]
+    params = np.array([1.0, 4.0, 0, 0, 1, 1, 2, -1, 2, 3, -1, 3, 4, 5], dtype=np.float64)
+    lo, hi = _box(6, 0.0, 1.0)
+    return Workload("table6_fp64", F_TABLE, params, lo, hi, ncall=ncall, itmax=itmax, seed=seed,
+                    meta={"tables": tables, "table_bytes": sum(t["values"].nbytes for t in tables)})
 
 
 def serving_stream(rate: float = 2000.0, duration: float = 60.0, draw_seed: int = 2206):

@@ -6,7 +6,7 @@ import os
 import numpy as np
 import pytest
 
-import closed_forms as CF
+from paper_2202_01753_gb300 import closed_forms as CF
 from paper_2202_01753_gb300 import workloads as W
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "table1_true_values.txt")

@@ -11,7 +11,7 @@ the grid adaptation.  Tolerances below are those levels with margin.
 import numpy as np
 import pytest
 
-import closed_forms as CF
+from paper_2202_01753_gb300 import closed_forms as CF
 import oracle
 from paper_2202_01753_gb300 import mcubes
 from paper_2202_01753_gb300 import workloads as W

@@ -1,0 +1,125 @@
+"""Parity of the CUDA m-Cubes1D variant (Sec. 3: one set of bin boundaries
+shared by all axes, histogram and rebinning of axis 0 only) with the
+oracle's variant, through the C ABI, under the tolerances of the m-Cubes
+parity tests: estimates within 1e-12 of their conditioning scale, variances
+within 1e-12 relative, grids within 1e-12 absolute, the axis-0 histogram
+within 1e-12 relative; the rows of the device grid stay bitwise equal."""
+import numpy as np
+import pytest
+
+from paper_2202_01753_gb300 import closed_forms as CF
+import oracle
+from paper_2202_01753_gb300 import mcubes
+from paper_2202_01753_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12
+MIXED_BOUND = 2e-5
+
+
+def _oracle(w):
+    return oracle.integrate(w.fid, w.params, w.lo, w.hi, w.ncall, w.itmax, nb=w.nb, seed=w.seed,
+                            rel_tol=w.rel_tol, abs_tol=w.abs_tol, one_dim=True)
+
+
+def _gpu(make_ctx, w, precision="fp64", **opts):
+    ctx = make_ctx(nbins=w.nb, seed=w.seed, precision=precision, one_dim=1, **opts)
+    res = ctx.integrate(w.fid, w.params, w.lo, w.hi, w.ncall, w.itmax, w.rel_tol, w.abs_tol)
+    I, V = ctx.trace()
+    out = dict(res=res, I=I, V=V, grid=ctx.grid(), hist=ctx.hist())
+    ctx.close()
+    return out
+
+
+def _scale(w, o):
+    pb = oracle.Problem(w.fid, w.params, w.lo, w.hi, w.ncall, nb=w.nb, seed=w.seed)
+    sums, _, _, _ = pb.vsample(oracle.init_grid(pb.d, pb.nb), 0, False, 0, min(pb.m, 2000))
+    return max(np.max(np.abs(o["trace_I"])), sums[2] / min(pb.m, 2000))
+
+
+@pytest.mark.parametrize("name,d,ncall", [("f2", 4, 60_000), ("f4", 5, 80_000), ("f5", 3, 60_000),
+                                          ("f3", 3, 40_000), ("f4", 1, 5_000), ("f2", 8, 200_000)])
+def test_onedim_parity(gpu_ctx_factory, name, d, ncall):
+    w = W.suite(name, d, ncall=ncall, itmax=6, seed=5)
+    o = _oracle(w)
+    g = _gpu(gpu_ctx_factory, w)
+    assert g["res"]["iterations"] == o["iterations"]
+    s = _scale(w, o)
+    np.testing.assert_allclose(g["I"], o["trace_I"], rtol=0, atol=RTOL * s)
+    np.testing.assert_allclose(g["V"], o["trace_var"], rtol=RTOL, atol=0)
+    np.testing.assert_allclose(g["grid"], o["grid"], rtol=0, atol=1e-12)
+    assert all(np.array_equal(g["grid"][j], g["grid"][0]) for j in range(d))
+    np.testing.assert_allclose(g["hist"][0], o["hist"][0], rtol=1e-12, atol=1e-300)
+    assert not g["hist"][1:].any()
+    assert g["res"]["estimate"] == pytest.approx(o["estimate"], abs=RTOL * s)
+    assert g["res"]["sigma"] == pytest.approx(o["sigma"], rel=RTOL)
+
+
+def test_onedim_sample_range_matches_oracle(gpu_ctx_factory):
+    """One adjusting pass over a ragged cube range on a non-uniform shared grid."""
+    w = W.suite("f2", 6, ncall=300_000)
+    ctx = gpu_ctx_factory(nbins=w.nb, seed=w.seed, one_dim=1)
+    ctx.setup(w.fid, w.params, w.lo, w.hi, w.ncall, w.itmax)
+    rng = np.random.default_rng(3)
+    row = np.cumsum(rng.uniform(0.1, 1.0, w.nb))
+    row /= row[-1]
+    row[-1] = 1.0
+    B = np.tile(row, (6, 1))
+    ctx.set_grid(B)
+    pb = oracle.Problem(w.fid, w.params, w.lo, w.hi, w.ncall, nb=w.nb, seed=w.seed, one_dim=True)
+    c0, c1 = 1234, pb.m - 777
+    sums, C = ctx.sample_range(2, True, c0, c1)
+    osums, oC, _, _ = pb.vsample(B, 2, True, c0, c1)
+    np.testing.assert_allclose(sums[:2], osums[:2], rtol=1e-12)
+    np.testing.assert_allclose(C[0], oC[0], rtol=1e-12, atol=1e-300)
+    assert not C[1:].any()
+    with pytest.raises(mcubes.McubesError) as e:      # rows must be equal
+        B2 = B.copy()
+        B2[3, 10] = 0.5 * (B2[3, 9] + B2[3, 10])
+        ctx.set_grid(B2)
+    assert e.value.status == mcubes.EINVAL
+    ctx.close()
+
+
+def test_onedim_mixed_bound(gpu_ctx_factory):
+    w = W.suite("f4", 6, ncall=400_000, itmax=5, seed=9)
+    o = _oracle(w)
+    g = _gpu(gpu_ctx_factory, w, precision="mixed")
+    err = np.max(np.abs(g["I"] - o["trace_I"])) / _scale(w, o)
+    assert err < MIXED_BOUND, err
+    assert abs(g["res"]["estimate"] - CF.exact(w)) < 5 * g["res"]["sigma"]
+
+
+def test_onedim_resume_is_bit_identical(gpu_ctx_factory):
+    w = W.suite("f5", 4, ncall=100_000, itmax=6, seed=2)
+    full = _gpu(gpu_ctx_factory, w)
+    a = gpu_ctx_factory(nbins=w.nb, seed=w.seed, one_dim=1)
+    a.setup(w.fid, w.params, w.lo, w.hi, w.ncall, w.itmax)
+    a.iterate(2)
+    blob = a.state_export()
+    a.close()
+    b = gpu_ctx_factory()
+    b.state_import(blob)
+    assert b.opts.one_dim == 1
+    b.iterate(4)
+    assert b.result()["estimate"] == full["res"]["estimate"]
+    assert np.array_equal(b.grid(), full["grid"])
+    b.close()
+
+
+def test_onedim_rejections(gpu_ctx_factory):
+    ctx = gpu_ctx_factory(one_dim=1)
+    w = W.suite("f4", 3, ncall=10_000)
+    hi = w.hi.copy()
+    hi[1] = 2.0                                       # not a cube
+    with pytest.raises(mcubes.McubesError) as e:
+        ctx.integrate(w.fid, w.params, w.lo, hi, w.ncall, 2)
+    assert e.value.status == mcubes.EINVAL
+    with pytest.raises(mcubes.McubesError) as e:
+        ctx.integrate_batch([dict(fid=w.fid, params=w.params, lo=w.lo, hi=w.hi, ncall=w.ncall, itmax=2)])
+    assert e.value.status == mcubes.EINVAL
+    with pytest.raises(mcubes.McubesError) as e:
+        mcubes.Server(ctx, itcap=4)
+    assert e.value.status == mcubes.EINVAL
+    ctx.close()

@@ -6,7 +6,7 @@ only the grouping of partial sums differs."""
 import numpy as np
 import pytest
 
-import closed_forms as CF
+from paper_2202_01753_gb300 import closed_forms as CF
 from paper_2202_01753_gb300 import mcubes
 from paper_2202_01753_gb300 import workloads as W
 

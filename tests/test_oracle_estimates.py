@@ -3,7 +3,7 @@ invariants and statistics (Sec. 5.1's accuracy protocol, scaled down)."""
 import numpy as np
 import pytest
 
-import closed_forms as CF
+from paper_2202_01753_gb300 import closed_forms as CF
 import oracle
 from paper_2202_01753_gb300 import workloads as W
 

@@ -6,7 +6,7 @@ driver) or to the closed forms of the paper's symmetric integrands."""
 import numpy as np
 import pytest
 
-import closed_forms as CF
+from paper_2202_01753_gb300 import closed_forms as CF
 import oracle
 from paper_2202_01753_gb300 import workloads as W
 

@@ -9,6 +9,12 @@ plain double precision.  Metric: integrand evaluations per second.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--config cosmo6|gauss3|corner8|osc10] [--ncall C] [--no-cpu-baseline]
 
+Other lines: --config batch4096 (integrals/s of 4096 batched integrals at
+rel_tol 1e-4 against plain FP64 one by one), --config serve (Poisson stream
+through the continuous-batching server: p50/p99 latency, integrals/s),
+--config onedim (m-Cubes1D speed-up on the symmetric suite integrands),
+--config accuracy (the Sec. 5.1 tolerance sweep on f2..f6).
+
 Under torchrun (N > 1) every rank integrates its own independent copy of
 the workload (own seed) on its own GPU: weak scaling, no collective on the
 data path; the value is the samples of all ranks over the slowest rank's time.
@@ -32,11 +38,12 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 from paper_2202_01753_gb300 import workloads as W  # noqa: E402
+from paper_2202_01753_gb300 import closed_forms as CF  # noqa: E402
 
 # Work per sample of the sampling kernel, from the ncu captures summarised in
 # profiles/ (the per-unit figures of the roofline), keyed by (config,
-# precision).  "fp64": FP64 flops per sample (2 DFMA + DADD + DMUL) against the
-# FP64 pipe (2 DFMA/clk/SM on GB300, ncu peak_sustained); "issue": issued warp
+# precision).  "fp64": FP64 instructions per sample (DFMA + DADD + DMUL) against
+# the FP64 pipe (2 per clk per SM on GB300, ncu peak_sustained); "issue": issued warp
 # instructions per 32 samples against 4 issue slots/clk/SM.
 ROOFLINE_UNITS = {
     ("cosmo6", "fp64"): {"kind": "fp64", "per_sample": 56.40,
@@ -58,10 +65,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="cosmo6", choices=sorted(W.CONFIGS) + ["batch4096", "serve"])
+    ap.add_argument("--config", default="cosmo6",
+                    choices=sorted(W.CONFIGS) + ["batch4096", "serve", "onedim", "accuracy"])
+    ap.add_argument("--sweep-runs", type=int, default=100, help="seeds per tolerance level (accuracy sweep)")
+    ap.add_argument("--sweep-ncall0", type=float, default=1e5, help="calls per iteration at tau_rel = 1e-3")
+    ap.add_argument("--sweep-ncall-cap", type=float, default=1.1e8, help="largest calls per iteration")
+    ap.add_argument("--sweep-precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the Poisson stream")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--batch-n", type=int, default=4096)
+    ap.add_argument("--batch-rel-tol", type=float, default=1e-4, help="relative tolerance of every batched integral")
     ap.add_argument("--seq-sample", type=int, default=96, help="integrals timed one by one in plain FP64")
     ap.add_argument("--ncall", type=float, default=None, help="override calls per iteration (profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -71,6 +84,8 @@ def parse():
 
 def workload(args, rank):
     w = W.CONFIGS[args.config](seed=rank)
+    if w.fid == W.F_TABLE:
+        w.meta["tables_from"] = (args.config, {"seed": rank})
     if args.ncall:
         w = w.scaled(int(args.ncall))
     return w
@@ -150,23 +165,60 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU baseline: the oracle as it stands on a bounded sample of the workload
 # ---------------------------------------------------------------------------
+def _oracle_pass(job):
+    """One adjusting oracle pass over cubes [c0, c1) of a workload (runs in a
+    spawned worker process); returns (seconds, samples)."""
+    import oracle
+    spec, c0, c1 = job
+    if spec.get("tables_from"):                 # regenerate the (seeded) tables in this process
+        name, kw = spec["tables_from"]
+        oracle.set_tables(W.CONFIGS[name](**kw).meta["tables"])
+    pb = oracle.Problem(spec["fid"], spec["params"], spec["lo"], spec["hi"], spec["ncall"], nb=spec["nb"],
+                        g_override=spec["g_override"], seed=spec["seed"])
+    B = oracle.init_grid(pb.d, pb.nb)
+    t = time.perf_counter()
+    pb.vsample(B, 0, True, c0, c1)
+    return time.perf_counter() - t, (c1 - c0) * pb.p
+
+
 def cpu_oracle_rate(w, seconds):
-    import numpy as np
+    """The oracle's adjusting pass on the host: one core over a cube range
+    sized to about seconds/2, then every core (spawned processes, one cube
+    range each) for about seconds/2.  Returns a cpu_baseline object."""
+    import multiprocessing as mp
 
     import oracle
+    if w.fid == W.F_TABLE:
+        oracle.set_tables(w.meta["tables"])
     pb = oracle.Problem(w.fid, w.params, w.lo, w.hi, w.ncall, nb=w.nb, g_override=w.g_override, seed=w.seed)
     B = oracle.init_grid(pb.d, pb.nb)
-    # calibrate on a small range, then run one range sized to `seconds`
+    # calibrate on a small range, then one range sized to seconds / 2
     n0 = max(1, min(pb.m, 2000 if pb.p < 100 else 1))
     t = time.perf_counter()
     pb.vsample(B, 0, True, 0, n0)
     dt = max(time.perf_counter() - t, 1e-4)
-    n = int(min(pb.m, max(n0, n0 * seconds / dt)))
+    n = int(min(pb.m, max(n0, n0 * 0.5 * seconds / dt)))
     t = time.perf_counter()
     pb.vsample(B, 0, True, 0, n)
-    dt = time.perf_counter() - t
-    samples = n * pb.p
-    return samples / dt, samples, dt, n
+    dt1 = time.perf_counter() - t
+    rate1 = n * pb.p / dt1
+    cores = os.cpu_count() or 1
+    spec = dict(fid=w.fid, params=[float(v) for v in w.params], lo=[float(v) for v in w.lo],
+                hi=[float(v) for v in w.hi], ncall=w.ncall, nb=w.nb, g_override=w.g_override, seed=w.seed,
+                tables_from=w.meta.get("tables_from"))
+    per = max(1, min(n, pb.m // cores))
+    jobs = [(spec, i * per, (i + 1) * per) for i in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_pass, [(spec, 0, 1)] * cores)           # start-up and library load, untimed
+        t = time.perf_counter()
+        res = pool.map(_oracle_pass, jobs, chunksize=1)
+        dtn = time.perf_counter() - t
+    samples_n = sum(r[1] for r in res)
+    return {"value": samples_n / dtn, "unit": "evals/s", "cores": cores, "kind": "oracle",
+            "sample": f"one adjusting pass over cubes [0, {per * cores}) split into {cores} equal ranges, "
+                      f"one process per core ({samples_n} samples, {dtn:.1f} s)",
+            "single_core": {"value": rate1, "cores": 1,
+                            "sample": f"cubes [0, {n}) ({n * pb.p} samples, {dt1:.1f} s)"}}
 
 
 def reference_arm(args):
@@ -175,6 +227,8 @@ def reference_arm(args):
         return 0
     w = workload(args, 0)
     import oracle
+    if w.fid == W.F_TABLE:
+        oracle.set_tables(w.meta["tables"])
     pb = oracle.Problem(w.fid, w.params, w.lo, w.hi, w.ncall, nb=w.nb, g_override=w.g_override, seed=w.seed)
     B = oracle.init_grid(pb.d, pb.nb)
     # one step: one adjusting sampling pass of the oracle over a fixed cube range
@@ -224,6 +278,8 @@ def ours(args):
     prec = w.precision
     ctx = mcubes.Context(local, stream=stream.cuda_stream, nbins=w.nb, g_override=w.g_override, seed=w.seed,
                          precision=prec, ita=-1)
+    if w.fid == W.F_TABLE:
+        ctx.set_tables(w.meta["tables"])       # resident state, uploaded once before timing
     ctx.setup(w.fid, w.params, w.lo, w.hi, w.ncall, itmax=Wm + K)
     geom = ctx.geometry()
     N = geom["m"] * geom["p"]
@@ -258,6 +314,8 @@ def ours(args):
 
     # end to end through the public call with host buffers (copies inside)
     ctx2 = mcubes.Context(local, nbins=w.nb, g_override=w.g_override, seed=w.seed, precision=prec, ita=-1)
+    if w.fid == W.F_TABLE:
+        ctx2.set_tables(w.meta["tables"])
     ctx2.integrate(w.fid, w.params, w.lo, w.hi, w.ncall, 2)   # warm
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -302,9 +360,7 @@ def ours(args):
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        rate, samples, dt, n = cpu_oracle_rate(w, args.cpu_seconds)
-        cpu = {"value": rate, "unit": "evals/s", "cores": 1, "kind": "oracle",
-               "sample": f"one adjusting pass over cubes [0, {n}) ({samples} samples, {dt:.1f} s)"}
+        cpu = cpu_oracle_rate(w, args.cpu_seconds)
 
     line = {
         "metric": "integrand evaluations per second", "value": value, "unit": "evals/s", "n_gpus": world,
@@ -313,7 +369,9 @@ def ours(args):
         "config": {"workload": w.name, "d": w.d, "ncall": w.ncall, "g": geom["g"], "m": geom["m"], "p": geom["p"],
                    "samples_per_step": N, "nbins": w.nb, "precision": prec, "adjusting": True,
                    "lanes_per_cube": geom["lanes"], "blocks": geom["blocks"],
-                   "l2": "flushed between timed steps (256 MB write)"},
+                   "l2": "flushed between timed steps (256 MB write)",
+                   **({"table_bytes": w.meta["table_bytes"], "tables": "resident, uploaded once before timing"}
+                      if w.fid == W.F_TABLE else {})},
         "kernel": {"sample_ms_avg": avg_sample_ms, "refine_ms_avg": kt["refine_ms"] / max(kt["refine_launches"], 1),
                    "sample_launches": kt["sample_launches"], "refine_launches": kt["refine_launches"]},
         "roofline": roof,
@@ -346,8 +404,9 @@ def batch_arm(args):
     torch.cuda.set_device(local)
     build.build()
     ws = W.batch4096(n=args.batch_n)
-    reqs = [dict(fid=w.fid, params=w.params, lo=w.lo, hi=w.hi, ncall=w.ncall, itmax=w.itmax, seed=w.seed)
-            for w in ws]
+    tol = args.batch_rel_tol
+    reqs = [dict(fid=w.fid, params=w.params, lo=w.lo, hi=w.hi, ncall=w.ncall, itmax=w.itmax, rel_tol=tol,
+                 seed=w.seed) for w in ws]
     ctx = mcubes.Context(local, precision="mixed")
     ctx.integrate_batch(reqs[: min(64, len(reqs))])        # warm-up (autotune, graph capture)
     torch.cuda.synchronize()
@@ -363,25 +422,30 @@ def batch_arm(args):
     idx = list(range(0, len(ws), step))[: args.seq_sample]
     solo = mcubes.Context(local, precision="fp64")
     solo.integrate(ws[0].fid, ws[0].params, ws[0].lo, ws[0].hi, ws[0].ncall, 2)
-    t_seq, rel = 0.0, []
+    t_seq, rel, seq_conv = 0.0, [], []
     for i in idx:
         w = ws[i]
         solo.set_opts(seed=w.seed)
         t0 = time.perf_counter()
-        r = solo.integrate(w.fid, w.params, w.lo, w.hi, w.ncall, w.itmax)
+        r = solo.integrate(w.fid, w.params, w.lo, w.hi, w.ncall, w.itmax, tol)
         t_seq += time.perf_counter() - t0
+        seq_conv.append(r["converged"])
         rel.append(abs(out[i]["estimate"] - r["estimate"]) / max(abs(r["estimate"]), r["sigma"]))
     solo.close()
     seq_per_integral = t_seq / len(idx)
+    conv = [o["converged"] for o in out]
     samples = sum(o["samples_per_iter"] * o["iterations"] for o in out)
     line = {
         "metric": "integrals per second", "value": len(ws) / t_batch, "unit": "integrals/s", "n_gpus": 1,
         "steps": 1, "warmup": 1, "ms_per_step": 1e3 * t_batch, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": f"batch{len(ws)}", "integrals": len(ws), "iterations": ws[0].itmax,
-                   "samples_total": samples, "precision": "mixed"},
+        "config": {"workload": f"batch{len(ws)}", "integrals": len(ws), "itmax": ws[0].itmax,
+                   "rel_tol": tol, "samples_total": samples, "precision": "mixed"},
         "evals_per_s": samples / t_batch,
+        "converged_fraction": statistics.mean(conv),
         "sequential_fp64": {"integrals_per_s": 1.0 / seq_per_integral, "sample": f"{len(idx)} integrals",
+                            "converged_fraction": statistics.mean(seq_conv),
+                            "batched_converged_fraction_same_sample": statistics.mean([conv[i] for i in idx]),
                             "speedup_of_batched": seq_per_integral * len(ws) / t_batch,
                             "max_rel_diff_of_estimates": max(rel), "median_rel_diff": statistics.median(rel)},
         "clocks": clk,
@@ -454,10 +518,153 @@ def serve_arm(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# m-Cubes1D (Sec. 3): speed-up over m-Cubes on the suite's symmetric
+# integrands, per iteration and to a relative tolerance
+# ---------------------------------------------------------------------------
+def onedim_arm(args):
+    import math
+
+    import torch
+
+    from paper_2202_01753_gb300 import build, mcubes
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    build.build()
+    d = 6
+    names = ("f2", "f4", "f5")
+    ncall_iter = int(args.ncall or 1e8)
+    per_iter, to_tol, speedups = {}, [], []
+    ctxs = {v: mcubes.Context(local, precision="fp64", one_dim=v) for v in (0, 1)}
+    clocks = ClockSampler(local)
+    clocks.start()
+    for name in names:
+        w = W.suite(name, d, ncall=ncall_iter, itmax=10)
+        rates = {}
+        for v, ctx in ctxs.items():
+            ctx.setup(w.fid, w.params, w.lo, w.hi, w.ncall, 2)
+            ctx.iterate(2)                                   # warm-up
+            ctx.result()
+            ctx.setup(w.fid, w.params, w.lo, w.hi, w.ncall, w.itmax)
+            ctx.timing_reset(True)
+            ctx.iterate(w.itmax)
+            ctx.result()
+            kt = ctx.timing()
+            ctx.timing_reset(False)
+            g = ctx.geometry()
+            rates[v] = g["m"] * g["p"] * kt["sample_launches"] / (kt["sample_ms"] / 1e3)
+        per_iter[name] = {"mcubes_evals_per_s": rates[0], "mcubes1d_evals_per_s": rates[1],
+                          "speedup": rates[1] / rates[0]}
+        exact = CF.exact(W.suite(name, d))
+        for tau in (1e-3, 2e-4, 4e-5, 8e-6):
+            ws = W.suite(name, d, ncall=10 ** 7, itmax=60)
+            row = {"integrand": name, "tau": tau}
+            for v, ctx in ctxs.items():
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = ctx.integrate(ws.fid, ws.params, ws.lo, ws.hi, ws.ncall, ws.itmax, tau)
+                dt = time.perf_counter() - t0
+                key = "mcubes1d" if v else "mcubes"
+                row[key] = {"ms": 1e3 * dt, "iterations": r["iterations"], "converged": r["converged"],
+                            "true_rel_err": abs(r["estimate"] - exact) / abs(exact)}
+            if row["mcubes"]["converged"] and row["mcubes1d"]["converged"]:
+                row["speedup"] = row["mcubes"]["ms"] / row["mcubes1d"]["ms"]
+                speedups.append(row["speedup"])
+            to_tol.append(row)
+    clk = clocks.stop()
+    for ctx in ctxs.values():
+        ctx.close()
+    gmean = math.exp(sum(math.log(x) for x in speedups) / len(speedups)) if speedups else None
+    line = {
+        "metric": "m-Cubes1D speed-up over m-Cubes (time to relative tolerance)", "value": gmean, "unit": "x",
+        "n_gpus": 1, "steps": len(to_tol), "warmup": 1, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "suite f2/f4/f5, d=6, [0,1]^6", "precision": "fp64", "ncall_to_tol": 10 ** 7,
+                   "itmax_to_tol": 60, "ncall_per_iter_rate": ncall_iter},
+        "per_iteration": per_iter, "to_tolerance": to_tol, "clocks": clk,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# accuracy sweep (Sec. 5.1 protocol): f2..f6, tau_rel from 1e-3 divided by 5
+# per successful level down to 1e-9; 100 seeds per level run as one batch;
+# true relative error against the closed forms
+# ---------------------------------------------------------------------------
+ACCURACY_SUITE = (("f2", 6), ("f3", 3), ("f4", 5), ("f5", 8), ("f6", 6))
+
+
+def accuracy_arm(args):
+    import numpy as np
+    import torch
+
+    from paper_2202_01753_gb300 import build, mcubes
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    build.build()
+    runs, itmax, ncall_cap = args.sweep_runs, 20, int(args.sweep_ncall_cap)
+    ctx = mcubes.Context(local, precision=args.sweep_precision)
+    rows, t_total, n_total = [], 0.0, 0
+    clocks = ClockSampler(local)
+    clocks.start()
+    for name, d in ACCURACY_SUITE:
+        exact = CF.exact(W.suite(name, d))
+        ncall, tau = int(args.sweep_ncall0), 1e-3
+        while tau >= 1e-9:
+            while True:
+                ws = [W.suite(name, d, ncall=ncall, itmax=itmax, seed=1000 + r) for r in range(runs)]
+                reqs = [dict(fid=w.fid, params=w.params, lo=w.lo, hi=w.hi, ncall=w.ncall, itmax=itmax,
+                             rel_tol=tau, seed=w.seed) for w in ws]
+                t0 = time.perf_counter()
+                out = ctx.integrate_batch(reqs)
+                dt = time.perf_counter() - t0
+                conv = np.array([bool(o["converged"]) for o in out], dtype=bool)
+                if conv.mean() >= 0.9 or ncall * 4 > ncall_cap:
+                    break
+                ncall *= 4                      # more samples for a tighter tolerance (Sec. 5.1)
+            t_total += dt
+            n_total += runs
+            err = np.array([abs(o["estimate"] - exact) / abs(exact) for o in out])
+            chi = np.array([o["chi2_dof"] for o in out])
+            ok = conv & (chi < 5.0)                     # boolean mask: the runs the paper's plots keep
+            row = {"integrand": f"{name},d={d}", "tau": tau, "ncall": ncall, "runs": runs,
+                   "converged": float(conv.mean()), "converged_chi2_lt5": float(ok.mean()),
+                   "within_tau": float(np.mean(err[ok] <= tau)) if ok.any() else None,
+                   "median_true_rel_err": float(np.median(err[ok])) if ok.any() else None,
+                   "p90_true_rel_err": float(np.percentile(err[ok], 90)) if ok.any() else None,
+                   "median_iterations": float(np.median([o["iterations"] for o in out])),
+                   "seconds": dt, "integrals_per_s": runs / dt}
+            rows.append(row)
+            if conv.mean() < 0.9:
+                break                           # the level failed: the sweep of this integrand ends
+            tau /= 5.0
+    clk = clocks.stop()
+    ctx.close()
+    line = {
+        "metric": "accuracy sweep: true relative error vs requested tau_rel", "value": n_total / t_total,
+        "unit": "integrals/s", "n_gpus": 1, "steps": len(rows), "warmup": 0, "ms_per_step": None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.sweep_precision == "fp64" else "f32+f64", "data": "synthetic",
+        "config": {"workload": "paper suite f2-f6 (Sec. 5 eqs. 2-6)", "dims": dict(ACCURACY_SUITE), "runs": runs,
+                   "itmax": itmax, "nbins": 500, "ncall_start": int(args.sweep_ncall0), "ncall_cap": ncall_cap,
+                   "precision": args.sweep_precision, "batched": True},
+        "levels": rows, "clocks": clk,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
+    if args.config == "accuracy":
+        return accuracy_arm(args)
     if args.config == "serve":
         return serve_arm(args)
+    if args.config == "onedim":
+        return onedim_arm(args)
     if args.config == "batch4096":
         return batch_arm(args)
     if args.impl == "reference":

@@ -65,7 +65,12 @@ typedef enum {
  *   COSMO6   [a_1..6, mu, s, r, t]    d = 6 only:
  *            f = prod_i x_i^-a_i * LN(x_3) LN(x_4) * exp(-(x_1 + x_2 - r)^2 / (2 t^2)),
  *            LN(z) = exp(-(ln z - mu)^2 / (2 s^2)) / (z s sqrt(2 pi))
- * (indices 1-based as written; x_i > 0 is required for COSMO6). */
+ *   TABLE    [c, nf, (tab, a, b) x nf]  1 <= nf <= 10 factors:
+ *            f = c prod_q T_tab_q(x_a_q) (1-D table, b_q = -1) or T_tab_q(x_a_q, x_b_q) (2-D),
+ *            T the linear / bilinear interpolant of a table set with mcubes_tables_set
+ *            (Sec. 6.1: integrands that read tabulated data); axes a, b are 0-based;
+ *            single-integral entry points only (the batched ones reject it)
+ * (indices 1-based as written unless stated; x_i > 0 is required for COSMO6). */
 enum {
     MCUBES_F_CONST = 0,
     MCUBES_F_GAUSS = 1,
@@ -75,8 +80,23 @@ enum {
     MCUBES_F_C0 = 5,
     MCUBES_F_DISCONT = 6,
     MCUBES_F_COSMO6 = 7,
-    MCUBES_F_COUNT = 8
+    MCUBES_F_TABLE = 8,
+    MCUBES_F_COUNT = 9
 };
+
+#define MCUBES_TABLES_MAX 16  /* interpolation tables per context */
+
+/* One interpolation table of the TABLE family: values at uniformly spaced
+ * knots, n[0] knots over [lo[0], hi[0]] (and, for ndim 2, n[1] over
+ * [lo[1], hi[1]]; values row-major, values[i0 * n[1] + i1]).  The value at a
+ * point is the linear (bilinear) interpolant of the knot values, the point
+ * first clamped into the knot range. */
+typedef struct {
+    int ndim;              /* 1 or 2 */
+    int n[2];              /* knots per axis, >= 2 (n[1] unused for ndim 1) */
+    double lo[2], hi[2];   /* knot range per axis, lo < hi, finite */
+    const double* values;  /* host array of n[0] (x n[1]) finite values, caller-owned */
+} mcubes_table;
 
 #define MCUBES_DMAX 12        /* largest dimension */
 #define MCUBES_NBMAX 1024     /* largest number of bins per axis */
@@ -92,6 +112,12 @@ typedef struct {
     int precision;        /* mcubes_precision (default MCUBES_FP64) */
     int lanes_per_cube;   /* 0 = automatic; else a power of two 1..32: threads sharing one cube */
     int blocks_per_sm;    /* 0 = automatic (occupancy); else resident sampling blocks per SM */
+    int one_dim;          /* 1 = the m-Cubes1D variant (Sec. 3): every axis shares one set of bin
+                             boundaries, only axis 0 keeps a histogram and is rebinned, its new edges
+                             going to all axes.  Meant for fully symmetric integrands; the box must be
+                             a cube (same lo and hi on every axis, else EINVAL), grid_set needs equal
+                             rows, hist_get returns zero rows 1..d-1.  The batched entry points and the
+                             server reject it (EINVAL).  0 = m-Cubes (default). */
 } mcubes_opts;
 
 typedef struct {
@@ -258,6 +284,19 @@ mcubes_status mcubes_grid_set(mcubes_ctx* ctx, const double* B, long long count)
 /* Waits, then copies the per-bin sums of f^2 ([d][nb], host) of the last
  * adjusting iteration. */
 mcubes_status mcubes_hist_get(mcubes_ctx* ctx, double* C, long long count);
+
+/* Uploads interpolation tables for TABLE integrands into the context's
+ * device memory (global memory, read through the L1/L2 caches), replacing
+ * any earlier set; the host arrays are copied before return.  The tables
+ * are kept in double precision and, for the mixed-precision path, as a
+ * single-precision copy.  The call waits for the context's stream and ends
+ * the current problem (ESTATE until the next mcubes_setup): set tables
+ * first, then mcubes_setup / mcubes_integrate.  Checkpoints do not hold the
+ * tables: set the same ones on a context before importing a TABLE problem.
+ * ntables = 0 releases them.  Errors: EINVAL (ntables outside
+ * 0..MCUBES_TABLES_MAX, a bad ndim, knot count or range, a non-finite
+ * value, more than 2^31 values in one table), ENOMEM, ECUDA. */
+mcubes_status mcubes_tables_set(mcubes_ctx* ctx, int ntables, const mcubes_table* tables);
 
 /* ---- checkpoint / resume ------------------------------------------------
  * The paper has no counterpart: these serialise the state of the current

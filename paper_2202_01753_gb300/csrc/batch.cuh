@@ -42,11 +42,11 @@ vsample_batch_kernel(const __grid_constant__ BatchArgs a)
         const uint32_t d = sd.d, nb = sd.nb;
         Cell* cells = reinterpret_cast<Cell*>(smem);
         HT* hist = reinterpret_cast<HT*>(smem + cell_bytes(MIXED) * d * nb);
-        if (seg.adjust) stage_grid<MIXED, true>(cells, hist, sd.grid, sd.grid + d * nb, sd.lo, sd.scale, d, nb, sd.g);
-        else stage_grid<MIXED, false>(cells, hist, sd.grid, sd.grid + d * nb, sd.lo, sd.scale, d, nb, sd.g);
+        if (seg.adjust) stage_grid<MIXED, true>(cells, hist, sd.grid, sd.grid + d * nb, sd.lo, sd.scale, d, nb, sd.g, d);
+        else stage_grid<MIXED, false>(cells, hist, sd.grid, sd.grid + d * nb, sd.lo, sd.scale, d, nb, sd.g, d);
         __syncthreads();
 
-        const BatchView v{d, nb, sd.g, sd.gmagic, sd.key0, sd.key1, sd.jac0, sd.phi_scale_f, sd.fam};
+        const BatchView v{d, nb, sd.g, sd.gmagic, sd.key0, sd.key1, d, sd.jac0, sd.phi_scale_f, sd.fam};
         const uint32_t it = a.st[seg.slot].it;
         CubeSums acc;
         if (seg.adjust)

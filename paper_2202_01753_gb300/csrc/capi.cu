@@ -22,6 +22,7 @@ cudaError_t launch_vsample_prodpeak(bool, bool, const VsArgs&, int, size_t, cuda
 cudaError_t launch_vsample_c0(bool, bool, const VsArgs&, int, size_t, cudaStream_t);
 cudaError_t launch_vsample_discont(bool, bool, const VsArgs&, int, size_t, cudaStream_t);
 cudaError_t launch_vsample_cosmo6(bool, bool, const VsArgs&, int, size_t, cudaStream_t);
+cudaError_t launch_vsample_table(bool, bool, const VsArgs&, int, size_t, cudaStream_t);
 cudaError_t occupancy_const(bool, bool, int, size_t, int*);
 cudaError_t occupancy_gauss(bool, bool, int, size_t, int*);
 cudaError_t occupancy_corner(bool, bool, int, size_t, int*);
@@ -30,6 +31,7 @@ cudaError_t occupancy_prodpeak(bool, bool, int, size_t, int*);
 cudaError_t occupancy_c0(bool, bool, int, size_t, int*);
 cudaError_t occupancy_discont(bool, bool, int, size_t, int*);
 cudaError_t occupancy_cosmo6(bool, bool, int, size_t, int*);
+cudaError_t occupancy_table(bool, bool, int, size_t, int*);
 
 cudaError_t launch_vsample(int family, bool mixed, bool adjust, const VsArgs& a, int grid, size_t smem,
                            cudaStream_t s)
@@ -43,6 +45,7 @@ cudaError_t launch_vsample(int family, bool mixed, bool adjust, const VsArgs& a,
     case MCUBES_F_C0: return launch_vsample_c0(mixed, adjust, a, grid, smem, s);
     case MCUBES_F_DISCONT: return launch_vsample_discont(mixed, adjust, a, grid, smem, s);
     case MCUBES_F_COSMO6: return launch_vsample_cosmo6(mixed, adjust, a, grid, smem, s);
+    case MCUBES_F_TABLE: return launch_vsample_table(mixed, adjust, a, grid, smem, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -58,15 +61,16 @@ cudaError_t vsample_occupancy(int family, bool mixed, bool adjust, int d, size_t
     case MCUBES_F_C0: return occupancy_c0(mixed, adjust, d, smem, blocks);
     case MCUBES_F_DISCONT: return occupancy_discont(mixed, adjust, d, smem, blocks);
     case MCUBES_F_COSMO6: return occupancy_cosmo6(mixed, adjust, d, smem, blocks);
+    case MCUBES_F_TABLE: return occupancy_table(mixed, adjust, d, smem, blocks);
     default: return cudaErrorInvalidValue;
     }
 }
 
-size_t vsample_smem_bytes(bool mixed, bool adjust, int d, int nb)
+size_t vsample_smem_bytes(bool mixed, bool adjust, int d, int nb, int hist_d)
 {
     const size_t cell = mixed ? 8 : 16;  // float2 or double2 cells
     const size_t h = adjust ? (mixed ? 4 : 8) : 0;
-    return (size_t)d * nb * (cell + h);
+    return (size_t)d * nb * cell + (size_t)hist_d * nb * h;
 }
 
 // ---------------------------------------------------------------------------
@@ -87,13 +91,50 @@ int family_nparams(int id, int d)
     }
 }
 
-// Fills the kernel-side constants of one integrand (layout documented in
-// mc_device.cuh).  Returns false if the parameters are unusable.
-bool integrand_prepare(int id, const double* p, int np, int d, FamParams* out)
+// TABLE family: [c, nf, (tab, a, b) x nf] against the tables of the context
+// (host copies of their descriptors); fills the factor lists.
+static bool table_prepare(const double* p, int np, int d, FamParams* out, const TableDesc* host_tabs, int ntabs,
+                          const TableDesc* dev_tabs)
 {
-    if (family_nparams(id, d) < 0 || np != family_nparams(id, d)) return false;
+    if (np < 2 || ntabs < 1 || !host_tabs || !dev_tabs) return false;
+    const int nf = (int)p[1];
+    if ((double)nf != p[1] || nf < 1 || nf > kTabFactorsMax || np != 2 + 3 * nf) return false;
+    for (int q = 0; q < nf; ++q) {
+        const double tq = p[2 + 3 * q], aq = p[3 + 3 * q], bq = p[4 + 3 * q];
+        const int t = (int)tq, a = (int)aq, b = (int)bq;
+        if ((double)t != tq || (double)a != aq || (double)b != bq) return false;
+        if (t < 0 || t >= ntabs || a < 0 || a >= d) return false;
+        if (host_tabs[t].ndim == 1 && b != -1) return false;
+        if (host_tabs[t].ndim == 2 && (b < 0 || b >= d || b == a)) return false;
+        out->tid[q] = t;
+        out->ta[q] = a;
+        out->tb[q] = b;
+    }
+    out->nf = nf;
+    out->tabs = dev_tabs;
+    return true;
+}
+
+// Fills the kernel-side constants of one integrand (layout documented in
+// mc_device.cuh).  Returns false if the parameters are unusable.  TABLE
+// integrands need the context's tables (host descriptors and the device
+// array); without them they are rejected.
+bool integrand_prepare(int id, const double* p, int np, int d, FamParams* out, const TableDesc* host_tabs,
+                       int ntabs, const TableDesc* dev_tabs)
+{
     for (int i = 0; i < np; ++i)
         if (!std::isfinite(p[i])) return false;
+    out->nf = 0;
+    out->tabs = nullptr;
+    if (id == MCUBES_F_TABLE) {
+        if (!table_prepare(p, np, d, out, host_tabs, ntabs, dev_tabs)) return false;
+        for (int i = 0; i < kParMax; ++i) {
+            out->c[i] = i == 0 ? p[0] : 0.0;
+            out->cf[i] = (float)out->c[i];
+        }
+        return true;
+    }
+    if (family_nparams(id, d) < 0 || np != family_nparams(id, d)) return false;
     double c[kParMax];
     std::fill(c, c + kParMax, 0.0);
     const double pi = 3.14159265358979323846;
@@ -144,6 +185,11 @@ bool integrand_prepare(int id, const double* p, int np, int d, FamParams* out)
         out->cf[i] = (float)c[i];
     }
     return true;
+}
+
+bool integrand_prepare(int id, const double* p, int np, int d, FamParams* out)
+{
+    return integrand_prepare(id, p, np, d, out, nullptr, 0, nullptr);
 }
 
 // Geometry of Alg. 2: g = largest integer with g^d <= ncall/2 (>= 1), capped
@@ -244,6 +290,7 @@ static bool opts_valid(const mcubes_opts* o)
         return false;
     if (o->blocks_per_sm < 0 || o->blocks_per_sm > 32) return false;
     if (o->g_override < 0) return false;
+    if (o->one_dim != 0 && o->one_dim != 1) return false;
     return true;
 }
 
@@ -281,6 +328,7 @@ void mcubes_default_opts(mcubes_opts* o)
     o->precision = MCUBES_FP64;
     o->lanes_per_cube = 0;
     o->blocks_per_sm = 0;
+    o->one_dim = 0;
 }
 
 const char* mcubes_strerror(mcubes_status s)
@@ -405,7 +453,9 @@ mcubes_status mcubes_setup(mcubes_ctx* c, int id, const double* params, int npar
     if (!lo || !hi || (nparams > 0 && !params)) return MCUBES_EINVAL;
     if (!(rel_tol >= 0.0) || !(abs_tol >= 0.0)) return MCUBES_EINVAL;
     FamParams fp;
-    if (!integrand_prepare(id, params, nparams, d, &fp)) return MCUBES_EINVAL;
+    if (!integrand_prepare(id, params, nparams, d, &fp, c->tabs_host.data(), (int)c->tabs_host.size(),
+                           (const TableDesc*)c->tab_desc.ptr))
+        return MCUBES_EINVAL;
     for (int j = 0; j < d; ++j)
         if (!std::isfinite(lo[j]) || !std::isfinite(hi[j]) || !(lo[j] < hi[j])) return MCUBES_EINVAL;
     const int nb = c->opts.nbins;
@@ -423,10 +473,14 @@ mcubes_status mcubes_setup(mcubes_ctx* c, int id, const double* params, int npar
     c->m = m;
     c->p = p;
     c->mixed = c->opts.precision == MCUBES_MIXED;
+    c->hist_d = c->opts.one_dim ? 1 : d;
+    if (c->opts.one_dim)  // m-Cubes1D: one set of boundaries serves every axis, so the box must be a cube
+        for (int j = 1; j < d; ++j)
+            if (lo[j] != lo[0] || hi[j] != hi[0]) return MCUBES_EINVAL;
 
     // launch shapes
-    c->smem_adj = vsample_smem_bytes(c->mixed, true, d, nb);
-    c->smem_noadj = vsample_smem_bytes(c->mixed, false, d, nb);
+    c->smem_adj = vsample_smem_bytes(c->mixed, true, d, nb, c->hist_d);
+    c->smem_noadj = vsample_smem_bytes(c->mixed, false, d, nb, c->hist_d);
     int smem_limit = 0;
     MC_CHECK(c, cudaDeviceGetAttribute(&smem_limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     if (c->smem_adj + 1024 > (size_t)smem_limit) return MCUBES_EINVAL;  // grid + histogram must fit on chip
@@ -449,7 +503,7 @@ mcubes_status mcubes_setup(mcubes_ctx* c, int id, const double* params, int npar
     MC_CHECK(c, c->grid.reserve(2 * sizeof(double) * d * nb));  // high parts, then low parts
     MC_CHECK(c, c->hist.reserve(sizeof(double) * d * nb));
     MC_CHECK(c, c->part.reserve(sizeof(double) * 3 * grid_max));
-    MC_CHECK(c, c->part_hist.reserve(hist_elem * (size_t)grid_max * d * nb));
+    MC_CHECK(c, c->part_hist.reserve(hist_elem * (size_t)grid_max * c->hist_d * nb));
 
     // kernel arguments
     VsArgs& a = c->vs;
@@ -465,6 +519,7 @@ mcubes_status mcubes_setup(mcubes_ctx* c, int id, const double* params, int npar
     a.gmagic = (uint32_t)(0xFFFFFFFFu / (uint32_t)g);
     a.p = (uint32_t)p;
     a.lanes = (uint32_t)c->lanes;
+    a.hist_d = (uint32_t)c->hist_d;
     a.cube_begin = 0;
     a.cube_end = (uint64_t)m;
     a.perm_k = cube_permutation((uint64_t)m);
@@ -489,6 +544,7 @@ mcubes_status mcubes_setup(mcubes_ctx* c, int id, const double* params, int npar
     r.d = d;
     r.nb = nb;
     r.hist_is_float = c->mixed ? 1 : 0;
+    r.hist_d = c->hist_d;
     r.alpha = c->opts.alpha;
     r.m = (double)m;
 
@@ -629,6 +685,8 @@ mcubes_status mcubes_grid_set(mcubes_ctx* c, const double* B, long long count)
             prev = v;
         }
         if (prev != 1.0) return MCUBES_EINVAL;
+        if (c->hist_d == 1 && j > 0 && std::memcmp(B + (size_t)j * c->nb, B, sizeof(double) * c->nb) != 0)
+            return MCUBES_EINVAL;  // m-Cubes1D: every axis has the same boundaries
     }
     MC_CHECK(c, cudaSetDevice(c->device));
     MC_CHECK(c, cudaMemcpyAsync(c->grid.ptr, B, sizeof(double) * count, cudaMemcpyHostToDevice, c->stream));
@@ -655,11 +713,14 @@ mcubes_status mcubes_sample_range(mcubes_ctx* c, unsigned it, int adjust, long l
     const size_t smem = adj ? c->smem_adj : c->smem_noadj;
     MC_CHECK(c, launch_vsample(c->fid, c->mixed, adj, a, grid, smem, c->stream));
     double* out = (double*)c->range_out.ptr;
-    MC_CHECK(c, launch_reduce_range((const double*)c->part.ptr, c->part_hist.ptr, c->mixed ? 1 : 0, grid, c->d,
-                                    c->nb, adj ? 1 : 0, out, out + 3, c->stream));
+    MC_CHECK(c, launch_reduce_range((const double*)c->part.ptr, c->part_hist.ptr, c->mixed ? 1 : 0, grid,
+                                    c->hist_d, c->nb, adj ? 1 : 0, out, out + 3, c->stream));
     MC_CHECK(c, cudaMemcpyAsync(sums, out, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream));
-    if (adj && C)
-        MC_CHECK(c, cudaMemcpyAsync(C, out + 3, sizeof(double) * c->d * c->nb, cudaMemcpyDeviceToHost, c->stream));
+    if (adj && C) {
+        const size_t kept = (size_t)c->hist_d * c->nb, all = (size_t)c->d * c->nb;
+        MC_CHECK(c, cudaMemcpyAsync(C, out + 3, sizeof(double) * kept, cudaMemcpyDeviceToHost, c->stream));
+        std::memset(C + kept, 0, sizeof(double) * (all - kept));  // m-Cubes1D: no histogram on axes 1..d-1
+    }
     MC_CHECK(c, cudaStreamSynchronize(c->stream));
     return MCUBES_OK;
 }
@@ -714,6 +775,7 @@ mcubes_status mcubes_timing_get(mcubes_ctx* c, double* sample_ms, int* sample_la
 mcubes_status mcubes_integrate_batch(mcubes_ctx* c, int n, const mcubes_request* reqs, mcubes_result* outs)
 {
     if (!c || n < 0 || (n > 0 && (!reqs || !outs))) return MCUBES_EINVAL;
+    if (c->opts.one_dim) return MCUBES_EINVAL;  // the batched kernels keep a histogram per axis
     if (n == 0) return MCUBES_OK;
     if (n > 65535) return MCUBES_EINVAL;
     int itcap = 1;

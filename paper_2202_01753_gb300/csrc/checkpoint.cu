@@ -128,6 +128,7 @@ mcubes_status mcubes_state_export(mcubes_ctx* c, void* buf, long long cap)
     h.opts.precision = c->opts.precision;
     h.opts.lanes_per_cube = c->opts.lanes_per_cube;
     h.opts.blocks_per_sm = c->opts.blocks_per_sm;
+    h.opts.one_dim = c->opts.one_dim;
     std::memcpy(h.params, c->prob_params.data(), sizeof(double) * c->prob_params.size());
     std::memcpy(h.lo, c->prob_lo.data(), sizeof(double) * c->d);
     std::memcpy(h.hi, c->prob_hi.data(), sizeof(double) * c->d);

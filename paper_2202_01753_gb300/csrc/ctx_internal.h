@@ -27,6 +27,7 @@ struct mcubes_ctx {
     int fid = 0, d = 0, nb = 0, itmax = 0, ita = 0;
     long long ncall = 0, g = 0, m = 0, p = 0;
     bool mixed = false;
+    int hist_d = 0;   // axes with a histogram: d, or 1 in m-Cubes1D
     int lanes = 1;
     int grid_adj = 0, grid_noadj = 0;
     size_t smem_adj = 0, smem_noadj = 0;
@@ -35,6 +36,10 @@ struct mcubes_ctx {
     mc::RefineArgs rf{};
 
     mc::DevBuf grid, hist, part, part_hist, state, range_out;
+
+    // interpolation tables of TABLE integrands (mcubes_tables_set)
+    mc::DevBuf tab_v, tab_vf, tab_desc;
+    std::vector<mc::TableDesc> tabs_host;  // descriptors as uploaded (device pointers)
 
     mc::BatchEngine* engine = nullptr;  // batched path, created on first use
 

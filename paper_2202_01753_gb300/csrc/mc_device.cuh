@@ -94,6 +94,7 @@ __device__ __forceinline__ uint4 sample_words(const VsArgs& a, uint4 ctr) { retu
 // constants stay in shared memory).
 struct BatchView {
     uint32_t d, nb, g, gmagic, key0, key1;
+    uint32_t hist_d;  // axes with a histogram (d)
     double jac0;
     float phi_scale_f;
     const FamParams& fam;
@@ -302,6 +303,98 @@ template <typename R> struct Family<MCUBES_F_COSMO6, R> {
     {
         const R z = s.x12 - RealOps<R>::par(f, 8);
         return RealOps<R>::par(f, 10) * RealOps<R>::exp_(-(s.e + z * z * RealOps<R>::par(f, 9)));
+    }
+};
+
+// Interpolation tables (TABLE family): the point is clamped into the knot
+// range, u = (x - lo) s with s = (n - 1)/(hi - lo), cell i = floor(u) (at
+// most n - 2), t = u - i, and the value is (1 - t) v_i + t v_{i+1}
+// (bilinear: the same on both axes).  The interpolant is continuous at the
+// knots, so a point on a knot gives the same value from either cell.
+template <typename R> struct TabOps;
+template <> struct TabOps<double> {
+    __device__ static void cell(double x, double lo, double hi, double s, int n, int* i, double* t)
+    {
+        const double u = (fmin(fmax(x, lo), hi) - lo) * s;
+        const int k = min((int)u, n - 2);  // u >= 0: truncation is the floor
+        *i = k;
+        *t = u - (double)k;
+    }
+    __device__ static double interp1(const TableDesc& T, double x)
+    {
+        int i;
+        double t;
+        cell(x, T.lo0, T.hi0, T.s0, T.n0, &i, &t);
+        return (1.0 - t) * __ldg(T.v + i) + t * __ldg(T.v + i + 1);
+    }
+    __device__ static double interp2(const TableDesc& T, double x, double y)
+    {
+        int i, k;
+        double t, s;
+        cell(x, T.lo0, T.hi0, T.s0, T.n0, &i, &t);
+        cell(y, T.lo1, T.hi1, T.s1, T.n1, &k, &s);
+        const double* r0 = T.v + (size_t)i * T.n1 + k;
+        const double* r1 = r0 + T.n1;
+        return (1.0 - t) * (1.0 - s) * __ldg(r0) + t * (1.0 - s) * __ldg(r1) + (1.0 - t) * s * __ldg(r0 + 1) +
+               t * s * __ldg(r1 + 1);
+    }
+};
+template <> struct TabOps<float> {
+    __device__ static void cell(float x, float lo, float hi, float s, int n, int* i, float* t)
+    {
+        const float u = (fminf(fmaxf(x, lo), hi) - lo) * s;
+        const int k = min((int)u, n - 2);
+        *i = k;
+        *t = u - (float)k;
+    }
+    __device__ static float interp1(const TableDesc& T, float x)
+    {
+        int i;
+        float t;
+        cell(x, T.lo0f, T.hi0f, T.s0f, T.n0, &i, &t);
+        return (1.0f - t) * __ldg(T.vf + i) + t * __ldg(T.vf + i + 1);
+    }
+    __device__ static float interp2(const TableDesc& T, float x, float y)
+    {
+        int i, k;
+        float t, s;
+        cell(x, T.lo0f, T.hi0f, T.s0f, T.n0, &i, &t);
+        cell(y, T.lo1f, T.hi1f, T.s1f, T.n1, &k, &s);
+        const float* r0 = T.vf + (size_t)i * T.n1 + k;
+        const float* r1 = r0 + T.n1;
+        return (1.0f - t) * (1.0f - s) * __ldg(r0) + t * (1.0f - s) * __ldg(r1) + (1.0f - t) * s * __ldg(r0 + 1) +
+               t * s * __ldg(r1 + 1);
+    }
+};
+
+template <typename R> struct Family<MCUBES_F_TABLE, R> {
+    // the coordinates are kept (registers: every index below is a
+    // compile-time constant) and the factors evaluated at the end
+    struct S { R x[kDMax]; };
+    __device__ static void begin(S& s)
+    {
+#pragma unroll
+        for (int j = 0; j < kDMax; ++j) s.x[j] = R(0);
+    }
+    __device__ static void add(S& s, int j, R x, const FamParams&) { s.x[j] = x; }
+    __device__ static R sel(const S& s, int a)
+    {
+        R v = s.x[0];
+#pragma unroll
+        for (int j = 1; j < kDMax; ++j)
+            if (a == j) v = s.x[j];
+        return v;
+    }
+    __device__ static R end(const S& s, uint32_t, const FamParams& f)
+    {
+        R prod = RealOps<R>::par(f, 0);
+        for (int q = 0; q < f.nf; ++q) {
+            const TableDesc& T = f.tabs[f.tid[q]];
+            const R xa = sel(s, f.ta[q]);
+            if (f.tb[q] < 0) prod *= TabOps<R>::interp1(T, xa);
+            else prod *= TabOps<R>::interp2(T, xa, sel(s, f.tb[q]));
+        }
+        return prod;
     }
 };
 

@@ -39,11 +39,27 @@ struct DevState {
     double hist_V[kItMax];
 };
 
+// One interpolation table as the kernels read it (TABLE family): values in
+// double (v) and single (vf) precision, knots i at lo + i / s.
+struct TableDesc {
+    const double* v;
+    const float* vf;
+    int ndim, n0, n1, pad;
+    double lo0, hi0, s0, lo1, hi1, s1;   // s = (n - 1) / (hi - lo)
+    float lo0f, hi0f, s0f, lo1f, hi1f, s1f;
+};
+
+constexpr int kTabFactorsMax = 10;
+
 // Integrand constants in the form the kernels use (derived on the host from
 // the public params blob, see integrand_prepare in capi.cu).
 struct FamParams {
     double c[kParMax];
     float cf[kParMax];
+    // TABLE family: factor q reads table tid[q] at axes a[q] (and b[q] >= 0)
+    int nf;
+    int tid[kTabFactorsMax], ta[kTabFactorsMax], tb[kTabFactorsMax];
+    const TableDesc* tabs;   // device array of the context's tables
 };
 
 // Arguments of one sampling launch (Alg. 3).  Passed by value as a
@@ -58,6 +74,7 @@ struct VsArgs {
     uint32_t it_fixed;
     uint32_t d, nb, g, gmagic;  // gmagic = floor((2^32-1)/g)
     uint32_t p, lanes;          // samples per cube, threads per cube (power of two <= 32)
+    uint32_t hist_d;            // axes with a histogram: d, or 1 for m-Cubes1D (part_hist is [gridDim][hist_d][nb])
     uint64_t cube_begin, cube_end;
     uint64_t perm_k;          // cube order: logical i -> cube_begin + (i perm_k mod n), gcd(perm_k, n) = 1
     uint32_t rk[10][2];       // Philox round keys (key + r * Weyl constants)
@@ -132,7 +149,7 @@ struct BatchRefineArgs {
 };
 
 // Batched kernels are instantiated per class: family x nb4 = ceil(d / 4).
-constexpr int kNumClasses = MCUBES_F_COUNT * 3;
+constexpr int kNumClasses = MCUBES_F_TABLE * 3;  // families with batched kernels (not TABLE)
 __host__ __device__ constexpr int batch_class(int family, int d) { return family * 3 + (d + 3) / 4 - 1; }
 cudaError_t launch_vsample_batch(int cls, bool mixed, const BatchArgs& a, int grid, size_t smem, cudaStream_t s);
 cudaError_t vsample_batch_occupancy(int cls, bool mixed, size_t smem, int* blocks_per_sm);
@@ -145,9 +162,10 @@ struct RefineArgs {
     double* grid_lo;          // [d][nb] edge low parts
     double* hist;             // [d][nb] reduced histogram (written for read-back)
     const double* part;       // [nblocks][3]
-    const void* part_hist;    // [nblocks][d][nb]
+    const void* part_hist;    // [nblocks][hist_d][nb]
     DevState* st;
     int nblocks, d, nb, adjust, hist_is_float;
+    int hist_d;               // axes with a histogram: d, or 1 (m-Cubes1D: axis 0's new edges go to every axis)
     double alpha;
     double m;                 // number of cubes
 };
@@ -155,7 +173,7 @@ struct RefineArgs {
 // Launchers (one per integrand family translation unit).
 cudaError_t launch_vsample(int family, bool mixed, bool adjust, const VsArgs& a, int grid,
                            size_t smem, cudaStream_t s);
-size_t vsample_smem_bytes(bool mixed, bool adjust, int d, int nb);
+size_t vsample_smem_bytes(bool mixed, bool adjust, int d, int nb, int hist_d);
 cudaError_t vsample_occupancy(int family, bool mixed, bool adjust, int d, size_t smem, int* blocks_per_sm);
 uint64_t cube_permutation(uint64_t n);
 double jacobian_scale(long long g, long long nb, int d);  // (g nb)^d

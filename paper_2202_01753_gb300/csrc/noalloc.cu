@@ -91,7 +91,7 @@ extern "C" mcubes_status mcubes_sample_range_noalloc(
         double* part_hist = reinterpret_cast<double*>(scratch + kPartBytes);
         double* grid_lo = reinterpret_cast<double*>(scratch + kPartBytes + kHistBytes);
 
-        const size_t smem = vsample_smem_bytes(mixed, adj, d, nbins);
+        const size_t smem = vsample_smem_bytes(mixed, adj, d, nbins, d);
         int smem_limit = 0, sms = 0, occ = 0;
         if (cudaDeviceGetAttribute(&smem_limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
@@ -123,6 +123,7 @@ extern "C" mcubes_status mcubes_sample_range_noalloc(
         const long long resident = (long long)occ * sms * kVsThreads;
         while (lanes < 32 && 2 * lanes <= p && (m * lanes < 4 * resident || p / lanes > 64)) lanes *= 2;
         a.lanes = (uint32_t)lanes;
+        a.hist_d = (uint32_t)d;
         a.cube_begin = (uint64_t)cube_begin;
         a.cube_end = (uint64_t)cube_end;
         a.perm_k = cube_permutation((uint64_t)(cube_end - cube_begin));

@@ -16,7 +16,7 @@ __global__ void __launch_bounds__(kRefineThreads) refine_kernel(const __grid_con
     __shared__ double scratch[33];
     if (!*(volatile const int*)&a.st->active) return;  // iteration skipped after convergence
     DevState* st = a.st;
-    const int nrebin = a.adjust ? a.d : 0;
+    const int nrebin = a.adjust ? a.hist_d : 0;
     if ((int)blockIdx.x == nrebin) {
         const IterRecord r{&st->it, &st->done, &st->error, &st->n, &st->converged, &st->estimate, &st->sigma,
                            &st->chi2_dof, st->hist_I, st->hist_V, kItMax, st->rel_tol, st->abs_tol};
@@ -25,14 +25,15 @@ __global__ void __launch_bounds__(kRefineThreads) refine_kernel(const __grid_con
         const int ax = blockIdx.x;
         const size_t off = (size_t)ax * a.nb;
         const size_t elem = a.hist_is_float ? sizeof(float) : sizeof(double);
-        rebin_axis(static_cast<const char*>(a.part_hist) + off * elem, (size_t)a.d * a.nb, a.nblocks,
+        rebin_axis(static_cast<const char*>(a.part_hist) + off * elem, (size_t)a.hist_d * a.nb, a.nblocks,
                    a.hist_is_float != 0, a.nb, a.alpha, a.grid + off, a.grid_lo + off, a.hist + off, &st->error,
-                   &st->done, scratch);
+                   &st->done, scratch, a.hist_d == a.d ? 1 : a.d);
     }
 }
 
 // Sums of one sampling pass over a cube range (no state change): block
-// d (or 0) adds the partial sums, blocks 0..d-1 the histogram columns.
+// d (or 0) adds the partial sums, blocks 0..d-1 the histogram columns (d is
+// the number of axes with a histogram).
 __global__ void __launch_bounds__(kRefineThreads)
 reduce_range_kernel(const double* part, const void* part_hist, int hist_is_float, int nblocks, int d,
                     int nb, int adjust, double* out_sums, double* out_hist)
@@ -86,7 +87,7 @@ __global__ void init_grid_kernel(double* grid, double* grid_lo, int d, int nb)
 
 cudaError_t launch_refine(const RefineArgs& a, cudaStream_t s)
 {
-    const int blocks = (a.adjust ? a.d : 0) + 1;
+    const int blocks = (a.adjust ? a.hist_d : 0) + 1;
     refine_kernel<<<blocks, kRefineThreads, 0, s>>>(a);
     return cudaGetLastError();
 }

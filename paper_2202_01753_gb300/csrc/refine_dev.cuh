@@ -185,9 +185,12 @@ static __device__ void finalize_iteration(const double* part, int nparts, double
 // weight and the new bin widths keep full double precision.
 // The axis's histogram is the sum of nparts partials, element k of partial t
 // at parts[t * stride + k] (float or double).  grid/grid_lo are this axis's
-// edges (updated in place), hist_out receives the summed histogram.
+// edges (updated in place), hist_out receives the summed histogram.  The new
+// edges are also written to the ncopy - 1 rows that follow (nb apart): the
+// axes that share this axis's boundaries in m-Cubes1D (Sec. 3).
 static __device__ void rebin_axis(const void* parts, size_t stride, int nparts, bool is_float, int nb, double alpha,
-                           double* grid, double* grid_lo, double* hist_out, int* error, int* done, double* scratch)
+                           double* grid, double* grid_lo, double* hist_out, int* error, int* done, double* scratch,
+                           int ncopy = 1)
 {
     __shared__ double sC[kNbMax];
     __shared__ double sW[kNbMax];
@@ -270,12 +273,16 @@ static __device__ void rebin_axis(const void* parts, size_t stride, int nparts, 
         double frac = (rem.hi + rem.lo) / sW[k];
         frac = fmin(fmax(frac, 0.0), 1.0);
         const DD e = dd_add(left, dd_scale(width, frac));
-        out[i - 1] = e.hi;
-        out_lo[i - 1] = e.lo;
+        for (int r = 0; r < ncopy; ++r) {
+            out[(size_t)r * nb + i - 1] = e.hi;
+            out_lo[(size_t)r * nb + i - 1] = e.lo;
+        }
     }
     if (threadIdx.x == 0) {
-        out[nb - 1] = 1.0;
-        out_lo[nb - 1] = 0.0;
+        for (int r = 0; r < ncopy; ++r) {
+            out[(size_t)r * nb + nb - 1] = 1.0;
+            out_lo[(size_t)r * nb + nb - 1] = 0.0;
+        }
     }
 }
 

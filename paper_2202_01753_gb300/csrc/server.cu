@@ -53,6 +53,7 @@ extern "C" {
 mcubes_status mcubes_server_create(mcubes_server** out, mcubes_ctx* ctx, long long budget_bytes, int itcap)
 {
     if (!out || !ctx || budget_bytes < 0 || itcap < 1 || itcap > MCUBES_ITMAX_MAX) return MCUBES_EINVAL;
+    if (ctx->opts.one_dim) return MCUBES_EINVAL;  // the batched kernels keep a histogram per axis
     *out = nullptr;
     const size_t per_slot = BatchEngine::slot_bytes(ctx->opts, itcap);
     long long capacity = budget_bytes > 0 ? budget_bytes / (long long)per_slot : 4096;

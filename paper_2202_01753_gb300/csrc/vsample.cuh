@@ -34,13 +34,16 @@ template <> struct Prec<true> {
 };
 
 // Stages the grid of all axes into shared-memory cells and clears the
-// histogram.  grid/grid_lo: [d][nb] double-double right edges (unit cube);
-// lo/scale: the box's lower corner and hi - lo; g: sub-cubes per axis.
+// histogram ([hist_d][nb]).  grid/grid_lo: [d][nb] double-double right
+// edges (unit cube); lo/scale: the box's lower corner and hi - lo; g:
+// sub-cubes per axis.
 template <bool MIXED, bool ADJ, class Arr>
 __device__ __forceinline__ void stage_grid(typename Prec<MIXED>::Cell* cells, typename Prec<MIXED>::H* hist,
                                            const double* grid, const double* grid_lo, const Arr& lo,
-                                           const Arr& scale, uint32_t d, uint32_t nb, uint32_t g)
+                                           const Arr& scale, uint32_t d, uint32_t nb, uint32_t g, uint32_t hist_d)
 {
+    if constexpr (ADJ)
+        for (uint32_t i = threadIdx.x; i < hist_d * nb; i += blockDim.x) hist[i] = typename Prec<MIXED>::H(0);
     for (uint32_t i = threadIdx.x; i < d * nb; i += blockDim.x) {
         const uint32_t j = i / nb, k = i - j * nb;
         const DD right{grid[i], grid_lo[i]};
@@ -50,14 +53,13 @@ __device__ __forceinline__ void stage_grid(typename Prec<MIXED>::Cell* cells, ty
         const double xw = scale[j] * (wd.hi + wd.lo);
         if constexpr (MIXED) cells[i] = make_float2((float)xl, (float)(xw * (double)nb));
         else cells[i] = make_double2(xl, xw / (double)g);
-        if constexpr (ADJ) hist[i] = typename Prec<MIXED>::H(0);
     }
 }
 
 // One sample: random words -> exact bin position -> map -> integrand.
 // Returns F = f(x) * J and leaves the flat histogram index of every axis in
 // idx (16 bits each, two per word).  A provides d, nb, g, gmagic, jac0 ((g nb)^d), phi_scale_f
-// (1/(g nb)) and fam, and sample_words(a, counter) its Philox block.
+// (1/(g nb)), hist_d and fam, and sample_words(a, counter) its Philox block.
 template <int FAM, bool MIXED, int NB4, class A>
 __device__ __forceinline__ typename Prec<MIXED>::R
 sample_point(const A& a, const typename Prec<MIXED>::Cell* cells, uint32_t c, uint32_t s, uint32_t it,
@@ -133,6 +135,7 @@ __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIX
     using HT = typename Prec<MIXED>::H;
     constexpr int DN = 4 * NB4;
     const uint32_t d = a.d, nb = a.nb;
+    const uint32_t hist_d = a.hist_d;  // axes with a histogram: d, or 1 (m-Cubes1D, Sec. 3)
     const uint32_t L = lanes;
     const uint32_t seg_lane = threadIdx.x & (L - 1u);
     const uint32_t cubes_per_group = blockDim.x / L;
@@ -179,7 +182,7 @@ __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIX
                     const HT F2 = (HT)(F * F);
 #pragma unroll
                     for (int j = 0; j < DN; ++j)
-                        if (j < (int)d) atomicAdd(&hist[(idx[j >> 1] >> (16 * (j & 1))) & 0xFFFFu], F2);
+                        if (j < (int)hist_d) atomicAdd(&hist[(idx[j >> 1] >> (16 * (j & 1))) & 0xFFFFu], F2);
                 }
             }
         }
@@ -282,7 +285,7 @@ vsample_kernel(const __grid_constant__ VsArgs a)
 
     Cell* cells = reinterpret_cast<Cell*>(smem);
     HT* hist = reinterpret_cast<HT*>(smem + cell_bytes(MIXED) * d * nb);
-    stage_grid<MIXED, ADJ>(cells, hist, a.grid, a.grid_lo, a.lo, a.scale, d, nb, a.g);
+    stage_grid<MIXED, ADJ>(cells, hist, a.grid, a.grid_lo, a.lo, a.scale, d, nb, a.g, a.hist_d);
     __syncthreads();
 
     CubeSums acc;
@@ -291,8 +294,8 @@ vsample_kernel(const __grid_constant__ VsArgs a)
     block_write_sums(acc, red, a.part + 3 * (size_t)blockIdx.x);
     if constexpr (ADJ) {
         __syncthreads();
-        HT* out = reinterpret_cast<HT*>(a.part_hist) + (size_t)blockIdx.x * d * nb;
-        for (uint32_t i = threadIdx.x; i < d * nb; i += blockDim.x) out[i] = hist[i];
+        HT* out = reinterpret_cast<HT*>(a.part_hist) + (size_t)blockIdx.x * a.hist_d * nb;
+        for (uint32_t i = threadIdx.x; i < a.hist_d * nb; i += blockDim.x) out[i] = hist[i];
     }
     }
 }

@@ -28,14 +28,19 @@ EXPORTED = [
     "mcubes_sample_range_noalloc", "mcubes_server_create", "mcubes_server_destroy", "mcubes_server_submit",
     "mcubes_server_step", "mcubes_server_poll", "mcubes_server_stats", "mcubes_server_run_stream",
     "mcubes_selftest_fxmath", "mcubes_state_size", "mcubes_state_export", "mcubes_state_import",
-    "mcubes_problem_get", "mcubes_get_opts",
+    "mcubes_problem_get", "mcubes_get_opts", "mcubes_tables_set",
 ]
 
 
 class mcubes_opts(ctypes.Structure):
     _fields_ = [("nbins", ctypes.c_int), ("ita", ctypes.c_int), ("g_override", ctypes.c_longlong),
                 ("alpha", ctypes.c_double), ("seed", ctypes.c_uint64), ("precision", ctypes.c_int),
-                ("lanes_per_cube", ctypes.c_int), ("blocks_per_sm", ctypes.c_int)]
+                ("lanes_per_cube", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("one_dim", ctypes.c_int)]
+
+
+class mcubes_table(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int * 2), ("lo", ctypes.c_double * 2),
+                ("hi", ctypes.c_double * 2), ("values", ctypes.POINTER(ctypes.c_double))]
 
 
 class mcubes_result(ctypes.Structure):
@@ -113,6 +118,7 @@ def lib():
                 "mcubes_server_run_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, P(mcubes_request), dp,
                                                             P(mcubes_result), dp, dp]),
                 "mcubes_get_opts": (ctypes.c_int, [ctx, P(mcubes_opts)]),
+                "mcubes_tables_set": (ctypes.c_int, [ctx, ctypes.c_int, P(mcubes_table)]),
                 "mcubes_state_size": (ctypes.c_int, [ctx, P(ll)]),
                 "mcubes_state_export": (ctypes.c_int, [ctx, ctypes.c_void_p, ll]),
                 "mcubes_state_import": (ctypes.c_int, [ctx, ctypes.c_void_p, ll]),
@@ -279,6 +285,25 @@ class Context:
     def set_grid(self, B):
         B = _f64(B).reshape(-1)
         self._check(lib().mcubes_grid_set(self._h, _dp(B), B.size), "mcubes_grid_set")
+
+    def set_tables(self, tables):
+        """Interpolation tables of TABLE integrands: dicts with ndim (1 or 2),
+        values (array of n0 or n0 x n1 knot values), lo and hi (scalars, or
+        pairs for 2-D).  Ends the current problem (set up again after it)."""
+        arr = (mcubes_table * max(len(tables), 1))()
+        keep = []
+        for i, tb in enumerate(tables):
+            v = _f64(tb["values"])
+            keep.append(v)
+            lo, hi = np.atleast_1d(tb["lo"]).astype(float), np.atleast_1d(tb["hi"]).astype(float)
+            arr[i].ndim = int(tb["ndim"])
+            arr[i].n[0] = v.shape[0]
+            arr[i].n[1] = v.shape[1] if arr[i].ndim == 2 else 1
+            arr[i].lo[0], arr[i].hi[0] = lo[0], hi[0]
+            if arr[i].ndim == 2:
+                arr[i].lo[1], arr[i].hi[1] = lo[1], hi[1]
+            arr[i].values = _dp(np.ascontiguousarray(v).reshape(-1))
+        self._check(lib().mcubes_tables_set(self._h, len(tables), arr), "mcubes_tables_set")
 
     def problem(self):
         v = [ctypes.c_int() for _ in range(5)]

@@ -231,4 +231,4 @@ def suite(name: str, d: int | None = None, ncall: int = 10 ** 6, itmax: int = 10
                     itmax=itmax, seed=seed)
 
 
-CONFIGS = {"gauss3": gauss3, "cosmo6": cosmo6, "corner8": corner8, "osc10": osc10}
+CONFIGS = {"gauss3": gauss3, "cosmo6": cosmo6, "corner8": corner8, "osc10": osc10, "table6": table6}

@@ -1,0 +1,118 @@
+"""TABLE integrands (interpolation tables read at run time, the paper's
+stateful integrands of Sec. 6.1) on the GPU against the oracle, through the
+C ABI.  Double precision: per-iteration estimates within 1e-12 of their
+scale, variances within 1e-12 relative, grids within 1e-12 absolute, the
+histograms within 1e-12 relative.  Mixed precision (single-precision copies
+of the tables): the stated bound."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2202_01753_gb300 import closed_forms as CF
+from paper_2202_01753_gb300 import mcubes
+from paper_2202_01753_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12
+MIXED_BOUND = 2e-5
+
+
+def _gpu(make_ctx, w, precision="fp64"):
+    ctx = make_ctx(nbins=w.nb, seed=w.seed, precision=precision)
+    ctx.set_tables(w.meta["tables"])
+    res = ctx.integrate(w.fid, w.params, w.lo, w.hi, w.ncall, w.itmax, w.rel_tol, w.abs_tol)
+    I, V = ctx.trace()
+    out = dict(res=res, I=I, V=V, grid=ctx.grid(), hist=ctx.hist())
+    ctx.close()
+    return out
+
+
+def _oracle(w):
+    oracle.set_tables(w.meta["tables"])
+    return oracle.integrate(w.fid, w.params, w.lo, w.hi, w.ncall, w.itmax, nb=w.nb, seed=w.seed)
+
+
+@pytest.mark.parametrize("n2,n1,ncall", [(257, 4097, 100_000), (64, 1000, 50_000), (2, 2, 20_000)])
+def test_table_parity_fp64(gpu_ctx_factory, n2, n1, ncall):
+    w = W.table6(seed=3, n2=n2, n1=n1, ncall=ncall, itmax=5)
+    o = _oracle(w)
+    g = _gpu(gpu_ctx_factory, w)
+    assert g["res"]["iterations"] == o["iterations"]
+    s = np.max(np.abs(o["trace_I"]))
+    np.testing.assert_allclose(g["I"], o["trace_I"], rtol=0, atol=RTOL * s)
+    np.testing.assert_allclose(g["V"], o["trace_var"], rtol=RTOL, atol=0)
+    np.testing.assert_allclose(g["grid"], o["grid"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(g["hist"], o["hist"], rtol=1e-12, atol=1e-300)
+    assert abs(g["res"]["estimate"] - CF.exact(w)) <= 4 * g["res"]["sigma"]
+
+
+def test_table_mixed_bound(gpu_ctx_factory):
+    w = W.table6(seed=4, n2=257, n1=4097, ncall=200_000, itmax=5)
+    o = _oracle(w)
+    g = _gpu(gpu_ctx_factory, w, precision="mixed")
+    err = np.max(np.abs(g["I"] - o["trace_I"])) / np.max(np.abs(o["trace_I"]))
+    assert err < MIXED_BOUND, err
+    assert abs(g["res"]["estimate"] - CF.exact(w)) <= 5 * g["res"]["sigma"]
+
+
+def test_full_size_tables_sampled_range(gpu_ctx_factory):
+    """The benchmark's table sizes (two 4096 x 4096 and two 2^20-knot tables,
+    384 MB on the device) at 1e8 calls: one adjusting pass over a ragged
+    cube range on an adapted grid, against the oracle's pass over it."""
+    w = W.table6(seed=0)
+    ctx = gpu_ctx_factory(nbins=w.nb, seed=w.seed)
+    ctx.set_tables(w.meta["tables"])
+    ctx.setup(w.fid, w.params, w.lo, w.hi, w.ncall, w.itmax)
+    geo = ctx.geometry()
+    oracle.set_tables(w.meta["tables"])
+    pb = oracle.Problem(w.fid, w.params, w.lo, w.hi, w.ncall, nb=w.nb, seed=w.seed)
+    assert (pb.g, pb.m, pb.p) == (geo["g"], geo["m"], geo["p"])
+    B = oracle.init_grid(6, w.nb)
+    small = W.table6(seed=0, ncall=200_000, itmax=3)
+    B = _oracle(small)["grid"]                        # an adapted grid (same tables)
+    ctx.set_grid(B)
+    c0 = pb.m // 3 + 17
+    c1 = c0 + 20_011
+    sums, C = ctx.sample_range(7, True, c0, c1)
+    osums, oC, _, _ = pb.vsample(B, 7, True, c0, c1)
+    np.testing.assert_allclose(sums[:2], osums[:2], rtol=1e-12)
+    np.testing.assert_allclose(C, oC, rtol=1e-12, atol=1e-300)
+    ctx.close()
+
+
+def test_table_rejections(gpu_ctx_factory):
+    w = W.table6(seed=1, n2=17, n1=33, ncall=10_000, itmax=2)
+    ctx = gpu_ctx_factory()
+    with pytest.raises(mcubes.McubesError) as e:       # no tables yet
+        ctx.integrate(w.fid, w.params, w.lo, w.hi, w.ncall, 2)
+    assert e.value.status == mcubes.EINVAL
+    bad = [dict(ndim=3, values=np.ones(4), lo=0.0, hi=1.0)]
+    for tb in (bad, [dict(ndim=1, values=np.ones(1), lo=0.0, hi=1.0)],
+               [dict(ndim=1, values=np.array([1.0, np.nan]), lo=0.0, hi=1.0)],
+               [dict(ndim=1, values=np.ones(3), lo=1.0, hi=1.0)]):
+        with pytest.raises(mcubes.McubesError) as e:
+            ctx.set_tables(tb)
+        assert e.value.status == mcubes.EINVAL
+    ctx.set_tables(w.meta["tables"])
+    ctx.setup(w.fid, w.params, w.lo, w.hi, w.ncall, 2)
+    ctx.set_tables(w.meta["tables"])                   # ends the problem
+    with pytest.raises(mcubes.McubesError) as e:
+        ctx.iterate(1)
+    assert e.value.status == mcubes.ESTATE
+    p = w.params.copy()
+    p[2] = 7                                           # no table 7
+    with pytest.raises(mcubes.McubesError) as e:
+        ctx.integrate(w.fid, p, w.lo, w.hi, w.ncall, 2)
+    assert e.value.status == mcubes.EINVAL
+    p = w.params.copy()
+    p[4] = -1                                          # 2-D table given one axis
+    with pytest.raises(mcubes.McubesError) as e:
+        ctx.integrate(w.fid, p, w.lo, w.hi, w.ncall, 2)
+    assert e.value.status == mcubes.EINVAL
+    with pytest.raises(mcubes.McubesError) as e:       # the batched path has no table kernels
+        ctx.integrate_batch([dict(fid=w.fid, params=w.params, lo=w.lo, hi=w.hi, ncall=w.ncall, itmax=2)])
+    assert e.value.status == mcubes.EINVAL
+    r = ctx.integrate(w.fid, w.params, w.lo, w.hi, w.ncall, 2)
+    assert r["iterations"] == 2
+    ctx.close()

@@ -46,14 +46,29 @@ from paper_2202_01753_gb300 import closed_forms as CF  # noqa: E402
 # the FP64 pipe (2 per clk per SM on GB300, ncu peak_sustained); "issue": issued warp
 # instructions per 32 samples against 4 issue slots/clk/SM.
 ROOFLINE_UNITS = {
-    ("cosmo6", "fp64"): {"kind": "fp64", "per_sample": 56.40,
+    ("cosmo6", "fp64"): {"kind": "fp64", "per_sample": 58.41,
                          "source": "profiles/vsample_cosmo6_fp64.md"},
-    ("corner8", "mixed"): {"kind": "issue", "per_sample": 684.4,
+    ("table6", "fp64"): {"kind": "fp64", "per_sample": 66.56, "dram_bytes_per_sample": 409.4,
+                         "source": "profiles/vsample_table6_fp64.md"},
+    ("corner8", "mixed"): {"kind": "issue", "per_sample": 683.0,
                            "source": "profiles/vsample_corner8_mixed.md"},
     ("osc10", "mixed"): {"kind": "issue", "per_sample": 793.5,
                          "source": "profiles/vsample_osc10_mixed.md"},
 }
 DFMA_PER_CLK_PER_SM = 2.0
+
+
+
+def _measured_hbm_gbs() -> float:
+    """HBM copy bandwidth measured on this machine's GPUs (GB/s), else the fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
+HBM_PEAK_GBS = _measured_hbm_gbs()
 ISSUE_PER_CLK_PER_SM = 4.0
 
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2: written between timed steps
@@ -347,6 +362,11 @@ def ours(args):
                 "peak_how": "2 FP64 instructions/clk/SM (ncu peak_sustained) x SMs x median SM clock under load",
                 "measured_dfma_per_s": pk["dfma_per_s"],
                 "per_sample": f"{unit['per_sample']} FP64 instructions, DFMA+DADD+DMUL ({unit['source']})"}
+        if unit.get("dram_bytes_per_sample"):
+            hbm = unit["dram_bytes_per_sample"] * N / t_launch / 1e9
+            roof["hbm"] = {"achieved_gbs": hbm, "peak_gbs": HBM_PEAK_GBS, "frac": hbm / HBM_PEAK_GBS,
+                           "bytes_per_sample": unit["dram_bytes_per_sample"],
+                           "how": "ncu dram__bytes_read+write per launch / samples (full-size one-pass capture)"}
     elif unit and unit["kind"] == "issue" and sm_mhz:
         peak = ISSUE_PER_CLK_PER_SM * sms * sm_mhz * 1e6 / 1e9              # G warp-instructions/s
         achieved = unit["per_sample"] * (N / 32.0) / t_launch / 1e9

@@ -360,10 +360,11 @@ mcubes_status mcubes_sample_range(mcubes_ctx* ctx, unsigned it, int adjust, long
  * otherwise).  Work is enqueued on cuda_stream (NULL = legacy default
  * stream) and the call returns without waiting.
  *
- * It allocates nothing: per-block partial sums live in one static device
- * array of the library, MCUBES_NOALLOC_MAX_BLOCKS x MCUBES_NOALLOC_MAX_BINS
- * doubles plus small change (about 7.5 MiB), which every GPU that loads the
- * library keeps until the process exits.  Limits: d * nbins <=
+ * It allocates nothing: the per-block partial sums and the histogram
+ * accumulator live in one static device array of the library,
+ * 3 x MCUBES_NOALLOC_MAX_BLOCKS + 2 x MCUBES_NOALLOC_MAX_BINS doubles (about
+ * 56 KiB), which every GPU that loads the library keeps until the process
+ * exits.  Limits: d * nbins <=
  * MCUBES_NOALLOC_MAX_BINS, otherwise EINVAL (as for any invalid argument);
  * at most MCUBES_NOALLOC_MAX_BLOCKS sampling blocks are launched.  The first
  * call on a device looks up the array's device address (cudaGetSymbolAddress)
@@ -385,7 +386,9 @@ mcubes_status mcubes_sample_range_noalloc(int device, int integrand_id, const do
 /* Diagnostic: evaluates, element-wise over n doubles of the device array
  * d_in into d_out (device), the library's double-precision logarithm
  * (which = 0) or exponential (1) -- table-driven with fixed-point series,
- * used by the FP64 integrands -- or CUDA's log (2) or exp (3), on
+ * used by the FP64 integrands -- or CUDA's log (2) or exp (3), or the
+ * library's single-precision cosine of the mixed-precision kernels (4) or
+ * CUDA's cosf (5) (both on the value rounded to single precision), on
  * cuda_stream (NULL = legacy default stream); returns without waiting.
  * The paper has no counterpart; this exists to test accuracy.
  * Errors: EINVAL, ECUDA. */

@@ -79,7 +79,7 @@ cudaError_t launch_vsample_batch_family(bool mixed, int nb4, const BatchArgs& a,
                                         cudaStream_t s)
 {
     auto k = mixed ? vsample_batch_kernel_ptr<FAM, true>(nb4) : vsample_batch_kernel_ptr<FAM, false>(nb4);
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit((const void*)k, smem);
     if (e != cudaSuccess) return e;
     k<<<grid, kVsThreads, smem, s>>>(a);
     return cudaGetLastError();
@@ -89,7 +89,7 @@ template <int FAM>
 cudaError_t vsample_batch_occupancy_family(bool mixed, int nb4, size_t smem, int* blocks)
 {
     auto k = mixed ? vsample_batch_kernel_ptr<FAM, true>(nb4) : vsample_batch_kernel_ptr<FAM, false>(nb4);
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit((const void*)k, smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, kVsThreads, smem);
 }

@@ -3,6 +3,8 @@
 // enqueueing of the sampling and refinement launches of every iteration.
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -235,6 +237,27 @@ bool geometry(int d, long long ncall, long long g_override, int nb, long long* g
     return true;
 }
 
+cudaError_t ctx_refresh_cells(mcubes_ctx* c)
+{
+    const double* g = (const double*)c->grid.ptr;
+    return launch_cells(g, g + (size_t)c->d * c->nb, c->cellbox, c->d, c->nb, c->cells.ptr, c->stream);
+}
+
+cudaError_t raise_smem_limit(const void* kernel, size_t smem)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, size_t> set;  // (kernel, device) -> limit set
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = set[{kernel, dev}];
+    if (smem <= cur && cur > 0) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max(smem, cur));
+    if (e == cudaSuccess) cur = std::max(smem, cur);
+    return e;
+}
+
 // Multiplier of the cube order of a range of n cubes (see sample_cubes):
 // the integer nearest n times the golden-ratio fraction that is coprime to n.
 uint64_t cube_permutation(uint64_t n)
@@ -419,7 +442,8 @@ mcubes_status mcubes_destroy(mcubes_ctx* c)
     c->grid.release();
     c->hist.release();
     c->part.release();
-    c->part_hist.release();
+    c->hist_acc.release();
+    c->cells.release();
     c->state.release();
     c->range_out.release();
     delete c->engine;
@@ -496,14 +520,23 @@ mcubes_status mcubes_setup(mcubes_ctx* c, int id, const double* params, int npar
     c->grid_noadj = occ_noadj * c->num_sms;
     const long long resident = (long long)std::max(occ_adj, occ_noadj) * c->num_sms * kVsThreads;
     c->lanes = c->opts.lanes_per_cube > 0 ? c->opts.lanes_per_cube : choose_lanes(m, p, resident);
+    // Cube-split mode: when the cubes cannot keep a quarter of the resident
+    // threads busy (few cubes with many samples each), several blocks share
+    // one cube, so that about two waves of blocks sample every iteration.
+    c->split = 1;
+    if (c->opts.lanes_per_cube == 0 && m * c->lanes * 4 < resident && p >= 2 * kVsThreads) {
+        const long long want = (2LL * std::max(c->grid_adj, c->grid_noadj) + m - 1) / m;
+        c->split = (int)std::max(1LL, std::min(want, p / kVsThreads));
+        if (c->split > 1) c->grid_adj = c->grid_noadj = (int)(m * c->split);
+    }
     const int grid_max = std::max(c->grid_adj, c->grid_noadj);
 
     // device buffers
-    const size_t hist_elem = c->mixed ? sizeof(float) : sizeof(double);
     MC_CHECK(c, c->grid.reserve(2 * sizeof(double) * d * nb));  // high parts, then low parts
     MC_CHECK(c, c->hist.reserve(sizeof(double) * d * nb));
     MC_CHECK(c, c->part.reserve(sizeof(double) * 3 * grid_max));
-    MC_CHECK(c, c->part_hist.reserve(hist_elem * (size_t)grid_max * c->hist_d * nb));
+    MC_CHECK(c, c->hist_acc.reserve(sizeof(double) * (size_t)c->hist_d * nb));
+    MC_CHECK(c, c->cells.reserve((c->mixed ? sizeof(float2) : sizeof(double2)) * (size_t)d * nb));
 
     // kernel arguments
     VsArgs& a = c->vs;
@@ -511,7 +544,8 @@ mcubes_status mcubes_setup(mcubes_ctx* c, int id, const double* params, int npar
     a.grid = (const double*)c->grid.ptr;
     a.grid_lo = (const double*)c->grid.ptr + (size_t)d * nb;
     a.part = (double*)c->part.ptr;
-    a.part_hist = c->part_hist.ptr;
+    a.hist_acc = (double*)c->hist_acc.ptr;
+    a.cells_g = c->cells.ptr;
     a.st = (DevState*)c->state.ptr;
     a.d = (uint32_t)d;
     a.nb = (uint32_t)nb;
@@ -520,6 +554,7 @@ mcubes_status mcubes_setup(mcubes_ctx* c, int id, const double* params, int npar
     a.p = (uint32_t)p;
     a.lanes = (uint32_t)c->lanes;
     a.hist_d = (uint32_t)c->hist_d;
+    a.split = (uint32_t)c->split;
     a.cube_begin = 0;
     a.cube_end = (uint64_t)m;
     a.perm_k = cube_permutation((uint64_t)m);
@@ -539,12 +574,23 @@ mcubes_status mcubes_setup(mcubes_ctx* c, int id, const double* params, int npar
     r.grid_lo = (double*)c->grid.ptr + (size_t)d * nb;
     r.hist = (double*)c->hist.ptr;
     r.part = (const double*)c->part.ptr;
-    r.part_hist = c->part_hist.ptr;
+    r.hist_acc = (double*)c->hist_acc.ptr;
+    r.cells_g = c->cells.ptr;
+    r.g = (uint32_t)g;
+    r.mixed = c->mixed ? 1 : 0;
+    std::memset(&c->cellbox, 0, sizeof c->cellbox);
+    for (int j = 0; j < d; ++j) {
+        r.lo[j] = c->cellbox.lo[j] = lo[j];
+        r.scale[j] = c->cellbox.scale[j] = hi[j] - lo[j];
+    }
+    c->cellbox.g = (uint32_t)g;
+    c->cellbox.mixed = c->mixed ? 1 : 0;
     r.st = (DevState*)c->state.ptr;
     r.d = d;
     r.nb = nb;
-    r.hist_is_float = c->mixed ? 1 : 0;
     r.hist_d = c->hist_d;
+    r.split = c->split;
+    r.p = (double)p;
     r.alpha = c->opts.alpha;
     r.m = (double)m;
 
@@ -555,7 +601,9 @@ mcubes_status mcubes_setup(mcubes_ctx* c, int id, const double* params, int npar
     hst.abs_tol = abs_tol;
     MC_CHECK(c, cudaMemcpyAsync(c->state.ptr, &hst, offsetof(DevState, hist_I), cudaMemcpyHostToDevice, c->stream));
     MC_CHECK(c, launch_init_grid((double*)c->grid.ptr, (double*)c->grid.ptr + (size_t)d * nb, d, nb, c->stream));
+    MC_CHECK(c, ctx_refresh_cells(c));
     MC_CHECK(c, cudaMemsetAsync(c->hist.ptr, 0, sizeof(double) * d * nb, c->stream));
+    MC_CHECK(c, cudaMemsetAsync(c->hist_acc.ptr, 0, sizeof(double) * c->hist_d * nb, c->stream));
     MC_CHECK(c, cudaStreamSynchronize(c->stream));  // hst lives on this stack frame
     c->prob_params.assign(params, params + std::max(nparams, 0));
     c->prob_lo.assign(lo, lo + d);
@@ -691,6 +739,7 @@ mcubes_status mcubes_grid_set(mcubes_ctx* c, const double* B, long long count)
     MC_CHECK(c, cudaSetDevice(c->device));
     MC_CHECK(c, cudaMemcpyAsync(c->grid.ptr, B, sizeof(double) * count, cudaMemcpyHostToDevice, c->stream));
     MC_CHECK(c, cudaMemsetAsync((double*)c->grid.ptr + count, 0, sizeof(double) * count, c->stream));
+    MC_CHECK(c, ctx_refresh_cells(c));
     MC_CHECK(c, cudaStreamSynchronize(c->stream));
     return MCUBES_OK;
 }
@@ -705,6 +754,7 @@ mcubes_status mcubes_sample_range(mcubes_ctx* c, unsigned it, int adjust, long l
     VsArgs a = c->vs;
     a.st = nullptr;
     a.it_fixed = it;
+    a.split = 1;  // the range pass always uses the cube-stride layout (its partials are sums)
     a.cube_begin = (uint64_t)cube_begin;
     a.cube_end = (uint64_t)cube_end;
     a.perm_k = cube_permutation((uint64_t)(cube_end - cube_begin));
@@ -713,8 +763,8 @@ mcubes_status mcubes_sample_range(mcubes_ctx* c, unsigned it, int adjust, long l
     const size_t smem = adj ? c->smem_adj : c->smem_noadj;
     MC_CHECK(c, launch_vsample(c->fid, c->mixed, adj, a, grid, smem, c->stream));
     double* out = (double*)c->range_out.ptr;
-    MC_CHECK(c, launch_reduce_range((const double*)c->part.ptr, c->part_hist.ptr, c->mixed ? 1 : 0, grid,
-                                    c->hist_d, c->nb, adj ? 1 : 0, out, out + 3, c->stream));
+    MC_CHECK(c, launch_reduce_range((const double*)c->part.ptr, (double*)c->hist_acc.ptr, grid, c->hist_d, c->nb,
+                                    adj ? 1 : 0, out, out + 3, c->stream));
     MC_CHECK(c, cudaMemcpyAsync(sums, out, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream));
     if (adj && C) {
         const size_t kept = (size_t)c->hist_d * c->nb, all = (size_t)c->d * c->nb;

@@ -169,6 +169,7 @@ mcubes_status mcubes_state_import(mcubes_ctx* c, const void* buf, long long size
     c->ready = false;
     CK_CHECK(c, cudaMemcpyAsync(c->grid.ptr, grid.data(), grid_bytes(h.d, h.nb), cudaMemcpyHostToDevice, c->stream));
     CK_CHECK(c, cudaMemcpyAsync(c->state.ptr, &st, sizeof st, cudaMemcpyHostToDevice, c->stream));
+    CK_CHECK(c, ctx_refresh_cells(c));
     CK_CHECK(c, cudaStreamSynchronize(c->stream));  // grid and st live on this stack frame
     c->it_enqueued = h.it_enqueued;
     c->ready = true;

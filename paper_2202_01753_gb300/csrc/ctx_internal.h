@@ -12,6 +12,14 @@ struct EventPair {
 };
 }  // namespace mc
 
+struct mcubes_ctx;
+
+namespace mc {
+// Rebuilds the context's map cells from its grid (after set-up or after the
+// grid is replaced), on the context's stream.
+cudaError_t ctx_refresh_cells(mcubes_ctx* c);
+}  // namespace mc
+
 struct mcubes_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -28,6 +36,7 @@ struct mcubes_ctx {
     long long ncall = 0, g = 0, m = 0, p = 0;
     bool mixed = false;
     int hist_d = 0;   // axes with a histogram: d, or 1 in m-Cubes1D
+    int split = 1;    // blocks per cube (cube-split mode when > 1)
     int lanes = 1;
     int grid_adj = 0, grid_noadj = 0;
     size_t smem_adj = 0, smem_noadj = 0;
@@ -35,7 +44,9 @@ struct mcubes_ctx {
     mc::VsArgs vs{};
     mc::RefineArgs rf{};
 
-    mc::DevBuf grid, hist, part, part_hist, state, range_out;
+    mc::DevBuf grid, hist, part, hist_acc, state, range_out;
+    mc::DevBuf cells;     // [d][nb] map cells of the current grid (rebuilt by the refinement)
+    mc::CellBox cellbox{};
 
     // interpolation tables of TABLE integrands (mcubes_tables_set)
     mc::DevBuf tab_v, tab_vf, tab_desc;

@@ -112,5 +112,38 @@ __device__ __forceinline__ double fx_exp(double y)
     return __longlong_as_double((long long)bits);
 }
 
+// Single-precision cosine for the mixed-precision kernels: x = k pi/2 + r
+// with k = rint(x 2/pi) and r = x - k pi/2 by a three-term Cody-Waite
+// reduction with fused multiply-adds (pi/2 = F1 + F2 + F3; the products are
+// exact inside the FMAs), |r| <= pi/4 (plus rounding); then cos x = cos r,
+// -sin r, -cos r or sin r by k mod 4, with the Taylor series
+// cos r = 1 - r^2/2! + ... + r^8/8! (next term < 2.5e-8) and
+// sin r = r - r^3/3! + ... + r^9/9! (next term < 2.2e-9).  Error: a few
+// units of 2^-24 for |x| < 2^22 (tested against CUDA's cosf).  Beyond 2^22,
+// where a float argument is itself known only to about 0.5, the hardware
+// approximation __cosf is used; no local-memory slow path is compiled in.
+__device__ __forceinline__ float fx_cosf(float x)
+{
+    if (!(fabsf(x) < 4194304.0f)) return __cosf(x);
+    const float k = rintf(x * kTwoOverPiF);
+    float r = fmaf(-k, kHalfPiF1, x);
+    r = fmaf(-k, kHalfPiF2, r);
+    r = fmaf(-k, kHalfPiF3, r);
+    const float r2 = r * r;
+    float c = 1.0f / 40320.0f;
+    c = fmaf(c, r2, -1.0f / 720.0f);
+    c = fmaf(c, r2, 1.0f / 24.0f);
+    c = fmaf(c, r2, -0.5f);
+    c = fmaf(c, r2, 1.0f);
+    float s = 1.0f / 362880.0f;
+    s = fmaf(s, r2, -1.0f / 5040.0f);
+    s = fmaf(s, r2, 1.0f / 120.0f);
+    s = fmaf(s, r2, -1.0f / 6.0f);
+    s = fmaf(s * r2, r, r);
+    const int q = (int)k & 3;
+    const float v = (q & 1) ? s : c;
+    return (q == 1 || q == 2) ? -v : v;
+}
+
 }  // namespace fx
 }  // namespace mc

@@ -1,5 +1,6 @@
-// fxtest.cu -- element-wise evaluation of the library's fixed-point log/exp
-// (and CUDA's, for comparison) over a device array, for accuracy tests.
+// fxtest.cu -- element-wise evaluation of the library's log/exp (fixed-point
+// series) and single-precision cosine, and of CUDA's, over a device array,
+// for accuracy tests.
 #include <algorithm>
 
 #include "mc_device.cuh"
@@ -15,7 +16,9 @@ __global__ void fxmath_kernel(int which, long long n, const double* in, double* 
         case 0: y = mc::fx::fx_log(x); break;
         case 1: y = mc::fx::fx_exp(x); break;
         case 2: y = log(x); break;
-        default: y = exp(x); break;
+        case 3: y = exp(x); break;
+        case 4: y = (double)mc::fx::fx_cosf((float)x); break;
+        default: y = (double)cosf((float)x); break;
         }
         out[i] = y;
     }
@@ -26,7 +29,7 @@ __global__ void fxmath_kernel(int which, long long n, const double* in, double* 
 extern "C" mcubes_status mcubes_selftest_fxmath(int which, long long n, const double* d_in, double* d_out,
                                                void* cuda_stream)
 {
-    if (which < 0 || which > 3 || n < 0 || (n > 0 && (!d_in || !d_out))) return MCUBES_EINVAL;
+    if (which < 0 || which > 5 || n < 0 || (n > 0 && (!d_in || !d_out))) return MCUBES_EINVAL;
     if (n == 0) return MCUBES_OK;
     fxmath_kernel<<<(int)std::min<long long>((n + 255) / 256, 65535), 256, 0, (cudaStream_t)cuda_stream>>>(
         which, n, d_in, d_out);

@@ -106,6 +106,38 @@ __device__ __forceinline__ uint4 sample_words(const BatchView& v, uint4 ctr)
 }
 
 // ---------------------------------------------------------------------------
+// Map cell k of one axis in the box's coordinates, from the double-double
+// right edges (unit cube) of that axis's row: (x left edge, x width / g) for
+// the FP64 kernels, (x left edge, nb * x width) in single precision for the
+// mixed ones.  inv_g = 1 / g.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void map_cell(const double* row, const double* row_lo, uint32_t k, double lo,
+                                         double scale, double* xl, double* xw)
+{
+    const DD right{row[k], row_lo[k]};
+    const DD left = k ? DD{row[k - 1], row_lo[k - 1]} : DD{0.0, 0.0};
+    const DD wd = dd_add(right, DD{-left.hi, -left.lo});
+    *xl = lo + scale * left.hi;
+    *xw = scale * (wd.hi + wd.lo);
+}
+
+__device__ __forceinline__ double2 map_cell_f64(const double* row, const double* row_lo, uint32_t k, double lo,
+                                                double scale, double inv_g)
+{
+    double xl, xw;
+    map_cell(row, row_lo, k, lo, scale, &xl, &xw);
+    return make_double2(xl, xw * inv_g);
+}
+
+__device__ __forceinline__ float2 map_cell_f32(const double* row, const double* row_lo, uint32_t k, double lo,
+                                               double scale, uint32_t nb)
+{
+    double xl, xw;
+    map_cell(row, row_lo, k, lo, scale, &xl, &xw);
+    return make_float2((float)xl, (float)(xw * (double)nb));
+}
+
+// ---------------------------------------------------------------------------
 // Exact position of one coordinate (Alg. 1 map step, Alg. 3 Get-Bin-ID).  The
 // sample sits at y = (c + u)/g on this axis, c the sub-cube digit and
 // u = (w + 1/2) / 2^32 the offset drawn from the random word w.  With
@@ -192,7 +224,7 @@ template <> struct RealOps<double> {
 template <> struct RealOps<float> {
     __device__ static float exp_(float v) { return expf(v); }
     __device__ static float log_(float v) { return logf(v); }
-    __device__ static float cos_(float v) { return cosf(v); }
+    __device__ static float cos_(float v) { return fx::fx_cosf(v); }
     __device__ static float rcp(float v) { return 1.0f / v; }
     __device__ static float par(const FamParams& f, int i) { return f.cf[i]; }
 };
@@ -313,30 +345,51 @@ template <typename R> struct Family<MCUBES_F_COSMO6, R> {
 // knots, so a point on a knot gives the same value from either cell.
 template <typename R> struct TabOps;
 template <> struct TabOps<double> {
-    __device__ static void cell(double x, double lo, double hi, double s, int n, int* i, double* t)
+    // Cell and fraction with two FP64 operations for u and one for t: the
+    // floor of u (0 <= u < 2^31) is taken by clearing the fraction bits of
+    // its encoding, the clamps are integer tests on those bits, so no FP64
+    // conversion or compare is issued (GB300 runs 2 FP64 instructions per
+    // clock per SM).
+    __device__ static void cell(double x, double lo, double s, int n, int* i, double* t)
     {
-        const double u = (fmin(fmax(x, lo), hi) - lo) * s;
-        const int k = min((int)u, n - 2);  // u >= 0: truncation is the floor
+        const double u = (x - lo) * s;
+        int64_t b = __double_as_longlong(u);
+        if (b < 0) b = 0;                         // below the range (or -0): u = 0
+        const int e = (int)((uint64_t)b >> 52) - 1023;
+        int k = 0;
+        int64_t kb = 0;                           // encoding of (double)k
+        if (e >= 0) {
+            const int sh = 52 - e;                // u < 2^31: sh > 21
+            k = (int)((((uint64_t)b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> sh);
+            kb = b & (int64_t)(~0ull << sh);
+        }
+        if (k > n - 2) {                          // floor(u) >= n - 1: at or above the last knot
+            *i = n - 2;
+            *t = 1.0;
+            return;
+        }
         *i = k;
-        *t = u - (double)k;
+        *t = __longlong_as_double(b) - __longlong_as_double(kb);  // exact
     }
     __device__ static double interp1(const TableDesc& T, double x)
     {
         int i;
         double t;
-        cell(x, T.lo0, T.hi0, T.s0, T.n0, &i, &t);
-        return (1.0 - t) * __ldg(T.v + i) + t * __ldg(T.v + i + 1);
+        cell(x, T.lo0, T.s0, T.n0, &i, &t);
+        const double v0 = __ldg(T.v + i), v1 = __ldg(T.v + i + 1);
+        return fma(t, v1 - v0, v0);
     }
     __device__ static double interp2(const TableDesc& T, double x, double y)
     {
         int i, k;
         double t, s;
-        cell(x, T.lo0, T.hi0, T.s0, T.n0, &i, &t);
-        cell(y, T.lo1, T.hi1, T.s1, T.n1, &k, &s);
+        cell(x, T.lo0, T.s0, T.n0, &i, &t);
+        cell(y, T.lo1, T.s1, T.n1, &k, &s);
         const double* r0 = T.v + (size_t)i * T.n1 + k;
         const double* r1 = r0 + T.n1;
-        return (1.0 - t) * (1.0 - s) * __ldg(r0) + t * (1.0 - s) * __ldg(r1) + (1.0 - t) * s * __ldg(r0 + 1) +
-               t * s * __ldg(r1 + 1);
+        const double v00 = __ldg(r0), v01 = __ldg(r0 + 1), v10 = __ldg(r1), v11 = __ldg(r1 + 1);
+        const double a = fma(t, v10 - v00, v00), b = fma(t, v11 - v01, v01);
+        return fma(s, b - a, a);
     }
 };
 template <> struct TabOps<float> {

@@ -69,12 +69,17 @@ struct VsArgs {
     const double* grid;       // [d][nb] right edges, unit coordinates (double-double: high parts)
     const double* grid_lo;    // [d][nb] low parts
     double* part;             // [gridDim][3]: sum of cube means, of their variances, of |means|
-    void* part_hist;          // [gridDim][d][nb] per-block sums of F^2 (double or float)
+    const void* cells_g;      // [d][nb] map cells of the current grid (double2 or float2), or null: build
+                              // them from grid/grid_lo in every block
+    double* hist_acc;         // [hist_d][nb] sums of F^2 of this pass: zero before an adjusting launch;
+                              // every block adds its shared-memory histogram once (global reductions)
     DevState* st;             // iteration state; nullptr -> use it_fixed and always run
     uint32_t it_fixed;
     uint32_t d, nb, g, gmagic;  // gmagic = floor((2^32-1)/g)
     uint32_t p, lanes;          // samples per cube, threads per cube (power of two <= 32)
     uint32_t hist_d;            // axes with a histogram: d, or 1 for m-Cubes1D (part_hist is [gridDim][hist_d][nb])
+    uint32_t split;             // > 1: blocks per cube (cube-split mode: gridDim = cubes * split, part holds
+                                // each block's shifted sums (K, S1, S2) of its slice of one cube)
     uint64_t cube_begin, cube_end;
     uint64_t perm_k;          // cube order: logical i -> cube_begin + (i perm_k mod n), gcd(perm_k, n) = 1
     uint32_t rk[10][2];       // Philox round keys (key + r * Weyl constants)
@@ -162,13 +167,28 @@ struct RefineArgs {
     double* grid_lo;          // [d][nb] edge low parts
     double* hist;             // [d][nb] reduced histogram (written for read-back)
     const double* part;       // [nblocks][3]
-    const void* part_hist;    // [nblocks][hist_d][nb]
+    double* hist_acc;         // [hist_d][nb] histogram of the sampling pass; read, then cleared
+    void* cells_g;            // [d][nb] map cells, rebuilt for every rebinned axis (null: none kept)
+    double lo[kDMax], scale[kDMax];
+    uint32_t g;
+    int mixed;
     DevState* st;
-    int nblocks, d, nb, adjust, hist_is_float;
+    int nblocks, d, nb, adjust;
     int hist_d;               // axes with a histogram: d, or 1 (m-Cubes1D: axis 0's new edges go to every axis)
+    int split;                // > 1: part holds (K, S1, S2) per block, split blocks per cube
+    double p;                 // samples per cube
     double alpha;
     double m;                 // number of cubes
 };
+
+// The box and format of the map cells (cells_kernel).
+struct CellBox {
+    double lo[kDMax], scale[kDMax];
+    uint32_t g;
+    int mixed;
+};
+cudaError_t launch_cells(const double* grid, const double* grid_lo, const CellBox& box, int d, int nb, void* out,
+                         cudaStream_t s);
 
 // Launchers (one per integrand family translation unit).
 cudaError_t launch_vsample(int family, bool mixed, bool adjust, const VsArgs& a, int grid,
@@ -176,12 +196,16 @@ cudaError_t launch_vsample(int family, bool mixed, bool adjust, const VsArgs& a,
 size_t vsample_smem_bytes(bool mixed, bool adjust, int d, int nb, int hist_d);
 cudaError_t vsample_occupancy(int family, bool mixed, bool adjust, int d, size_t smem, int* blocks_per_sm);
 uint64_t cube_permutation(uint64_t n);
+// Raises a kernel's dynamic shared-memory limit on the current device to at
+// least smem bytes (never lowers it, so that contexts of different sizes can
+// share a kernel); a host-side record skips the driver call when the limit
+// is already high enough.
+cudaError_t raise_smem_limit(const void* kernel, size_t smem);
 double jacobian_scale(long long g, long long nb, int d);  // (g nb)^d
 
 cudaError_t launch_refine(const RefineArgs& a, cudaStream_t s);
-cudaError_t launch_reduce_range(const double* part, const void* part_hist, int hist_is_float,
-                                int nblocks, int d, int nb, int adjust, double* out_sums,
-                                double* out_hist, cudaStream_t s);
+cudaError_t launch_reduce_range(const double* part, double* hist_acc, int nblocks, int d, int nb, int adjust,
+                                double* out_sums, double* out_hist, cudaStream_t s);
 cudaError_t launch_init_grid(double* grid, double* grid_lo, int d, int nb, cudaStream_t s);
 
 }  // namespace mc

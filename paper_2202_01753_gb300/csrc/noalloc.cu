@@ -25,12 +25,12 @@ using namespace mc;
 namespace {
 
 // Layout of the static scratch: [block partials: kMaxBlocks x 3 doubles]
-// [per-block histograms: kMaxBlocks x kMaxBins doubles] [zero low parts of
+// [the pass's histogram accumulator: kMaxBins doubles] [zero low parts of
 // the grid edges: kMaxBins doubles].
 constexpr int kMaxBlocks = MCUBES_NOALLOC_MAX_BLOCKS;
 constexpr int kMaxBins = MCUBES_NOALLOC_MAX_BINS;
 constexpr size_t kPartBytes = sizeof(double) * 3 * kMaxBlocks;
-constexpr size_t kHistBytes = sizeof(double) * (size_t)kMaxBlocks * kMaxBins;
+constexpr size_t kHistBytes = sizeof(double) * (size_t)kMaxBins;
 constexpr size_t kLoBytes = sizeof(double) * kMaxBins;
 constexpr size_t kScratchBytes = kPartBytes + kHistBytes + kLoBytes;
 
@@ -88,7 +88,7 @@ extern "C" mcubes_status mcubes_sample_range_noalloc(
         unsigned char* scratch = nullptr;
         if (scratch_address(device, &scratch) != cudaSuccess) { st = MCUBES_ECUDA; break; }
         double* part = reinterpret_cast<double*>(scratch);
-        double* part_hist = reinterpret_cast<double*>(scratch + kPartBytes);
+        double* hist_acc = reinterpret_cast<double*>(scratch + kPartBytes);
         double* grid_lo = reinterpret_cast<double*>(scratch + kPartBytes + kHistBytes);
 
         const size_t smem = vsample_smem_bytes(mixed, adj, d, nbins, d);
@@ -111,7 +111,7 @@ extern "C" mcubes_status mcubes_sample_range_noalloc(
         a.grid = d_grid;
         a.grid_lo = grid_lo;
         a.part = part;
-        a.part_hist = part_hist;  // float entries in the mixed path (half the room is used)
+        a.hist_acc = hist_acc;
         a.st = nullptr;
         a.it_fixed = it;
         a.d = (uint32_t)d;
@@ -124,6 +124,7 @@ extern "C" mcubes_status mcubes_sample_range_noalloc(
         while (lanes < 32 && 2 * lanes <= p && (m * lanes < 4 * resident || p / lanes > 64)) lanes *= 2;
         a.lanes = (uint32_t)lanes;
         a.hist_d = (uint32_t)d;
+        a.split = 1;
         a.cube_begin = (uint64_t)cube_begin;
         a.cube_end = (uint64_t)cube_end;
         a.perm_k = cube_permutation((uint64_t)(cube_end - cube_begin));
@@ -137,11 +138,12 @@ extern "C" mcubes_status mcubes_sample_range_noalloc(
         a.nb_f = (float)nbins;
         a.fam = fp;
 
-        // the grid's low parts must read as zero; the partials are overwritten
+        // the grid's low parts must read as zero and the histogram accumulator
+        // start empty; the partials are overwritten
         if (cudaMemsetAsync(grid_lo, 0, sizeof(double) * d * nbins, s) != cudaSuccess ||
+            (adj && cudaMemsetAsync(hist_acc, 0, sizeof(double) * d * nbins, s) != cudaSuccess) ||
             launch_vsample(integrand_id, mixed, adj, a, grid, smem, s) != cudaSuccess ||
-            launch_reduce_range(part, part_hist, mixed ? 1 : 0, grid, d, nbins, adj ? 1 : 0, d_sums, d_hist, s) !=
-                cudaSuccess) {
+            launch_reduce_range(part, hist_acc, grid, d, nbins, adj ? 1 : 0, d_sums, d_hist, s) != cudaSuccess) {
             st = MCUBES_ECUDA;
             break;
         }

@@ -20,23 +20,41 @@ __global__ void __launch_bounds__(kRefineThreads) refine_kernel(const __grid_con
     if ((int)blockIdx.x == nrebin) {
         const IterRecord r{&st->it, &st->done, &st->error, &st->n, &st->converged, &st->estimate, &st->sigma,
                            &st->chi2_dof, st->hist_I, st->hist_V, kItMax, st->rel_tol, st->abs_tol};
-        finalize_iteration(a.part, a.nblocks, a.m, r, scratch);
+        finalize_iteration(a.part, a.nblocks, a.m, r, scratch, a.split, a.p);
     } else {
         const int ax = blockIdx.x;
         const size_t off = (size_t)ax * a.nb;
-        const size_t elem = a.hist_is_float ? sizeof(float) : sizeof(double);
-        rebin_axis(static_cast<const char*>(a.part_hist) + off * elem, (size_t)a.hist_d * a.nb, a.nblocks,
-                   a.hist_is_float != 0, a.nb, a.alpha, a.grid + off, a.grid_lo + off, a.hist + off, &st->error,
-                   &st->done, scratch, a.hist_d == a.d ? 1 : a.d);
+        const int rows = a.hist_d == a.d ? 1 : a.d;  // m-Cubes1D: axis 0's edges go to every axis
+        rebin_axis(a.hist_acc + off, 0, 1, false, a.nb, a.alpha, a.grid + off, a.grid_lo + off, a.hist + off,
+                   &st->error, &st->done, scratch, rows);
+        // rebin_axis read the row before its first barrier: clear it for the next pass
+        for (int k = threadIdx.x; k < a.nb; k += blockDim.x) a.hist_acc[off + k] = 0.0;
+        if (a.cells_g) {
+            __syncthreads();  // the block's new edges are in global memory
+            const double inv_g = 1.0 / (double)a.g;
+            for (int r = 0; r < rows; ++r) {
+                const int j = ax + r;
+                const double* row = a.grid + (size_t)j * a.nb;
+                const double* row_lo = a.grid_lo + (size_t)j * a.nb;
+                for (int k = threadIdx.x; k < a.nb; k += blockDim.x) {
+                    const size_t i = (size_t)j * a.nb + k;
+                    if (a.mixed)
+                        static_cast<float2*>(a.cells_g)[i] = map_cell_f32(row, row_lo, k, a.lo[j], a.scale[j], a.nb);
+                    else
+                        static_cast<double2*>(a.cells_g)[i] = map_cell_f64(row, row_lo, k, a.lo[j], a.scale[j], inv_g);
+                }
+            }
+        }
     }
 }
 
 // Sums of one sampling pass over a cube range (no state change): block
-// d (or 0) adds the partial sums, blocks 0..d-1 the histogram columns (d is
-// the number of axes with a histogram).
+// d (or 0) adds the partial sums, blocks 0..d-1 copy the histogram rows out
+// of the accumulator and clear them (d is the number of axes with a
+// histogram).
 __global__ void __launch_bounds__(kRefineThreads)
-reduce_range_kernel(const double* part, const void* part_hist, int hist_is_float, int nblocks, int d,
-                    int nb, int adjust, double* out_sums, double* out_hist)
+reduce_range_kernel(const double* part, double* hist_acc, int nblocks, int d, int nb, int adjust,
+                    double* out_sums, double* out_hist)
 {
     __shared__ double scratch[33];
     const int nrebin = adjust ? d : 0;
@@ -51,18 +69,23 @@ reduce_range_kernel(const double* part, const void* part_hist, int hist_is_float
         return;
     }
     const int ax = blockIdx.x;
-    const size_t stride = (size_t)d * nb;
     for (int k = threadIdx.x; k < nb; k += blockDim.x) {
-        double acc = 0.0;
-        if (hist_is_float) {
-            const float* ph = static_cast<const float*>(part_hist) + (size_t)ax * nb + k;
-            for (int b = 0; b < nblocks; ++b) acc += (double)ph[b * stride];
-        } else {
-            const double* ph = static_cast<const double*>(part_hist) + (size_t)ax * nb + k;
-            for (int b = 0; b < nblocks; ++b) acc += ph[b * stride];
-        }
-        out_hist[(size_t)ax * nb + k] = acc;
+        const size_t i = (size_t)ax * nb + k;
+        out_hist[i] = hist_acc[i];
+        hist_acc[i] = 0.0;
     }
+}
+
+// Map cells of the whole grid (set-up, and after the grid is replaced).
+__global__ void cells_kernel(const double* grid, const double* grid_lo, CellBox box, int d, int nb, void* out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d * nb) return;
+    const int j = i / nb, k = i - j * nb;
+    const double* row = grid + (size_t)j * nb;
+    const double* row_lo = grid_lo + (size_t)j * nb;
+    if (box.mixed) static_cast<float2*>(out)[i] = map_cell_f32(row, row_lo, k, box.lo[j], box.scale[j], nb);
+    else static_cast<double2*>(out)[i] = map_cell_f64(row, row_lo, k, box.lo[j], box.scale[j], 1.0 / (double)box.g);
 }
 
 // Init-Bins (Alg. 2): nb equal bins per axis, right edges (k+1)/nb held as
@@ -92,13 +115,20 @@ cudaError_t launch_refine(const RefineArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_range(const double* part, const void* part_hist, int hist_is_float,
-                                int nblocks, int d, int nb, int adjust, double* out_sums,
-                                double* out_hist, cudaStream_t s)
+cudaError_t launch_reduce_range(const double* part, double* hist_acc, int nblocks, int d, int nb, int adjust,
+                                double* out_sums, double* out_hist, cudaStream_t s)
 {
     const int blocks = (adjust ? d : 0) + 1;
-    reduce_range_kernel<<<blocks, kRefineThreads, 0, s>>>(part, part_hist, hist_is_float, nblocks, d,
-                                                          nb, adjust, out_sums, out_hist);
+    reduce_range_kernel<<<blocks, kRefineThreads, 0, s>>>(part, hist_acc, nblocks, d, nb, adjust, out_sums,
+                                                          out_hist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cells(const double* grid, const double* grid_lo, const CellBox& box, int d, int nb, void* out,
+                         cudaStream_t s)
+{
+    const int n = d * nb;
+    cells_kernel<<<(n + 255) / 256, 256, 0, s>>>(grid, grid_lo, box, d, nb, out);
     return cudaGetLastError();
 }
 

@@ -146,12 +146,36 @@ struct IterRecord {
 // Reduces nparts block partials (3 doubles each, fixed order) into the
 // iteration estimate I = sum means / m and variance sum vars / m^2, records
 // them, weighs all iterations, tests convergence and advances the iteration.
-static __device__ void finalize_iteration(const double* part, int nparts, double m, const IterRecord& r, double* scratch)
+// With split > 1 the partials are (K, S1, S2) of cube slices, split
+// consecutive ones per cube (sums of F - K over a slice of q = ceil(p/split)
+// samples, the last slice shorter): each cube's slices are re-based on the
+// first slice's shift and summed in order, then the cube's mean and the
+// variance of that mean follow (UpdateVariance of Alg. 3).
+static __device__ void finalize_iteration(const double* part, int nparts, double m, const IterRecord& r,
+                                          double* scratch, int split = 1, double p = 0.0)
 {
     double s0 = 0.0, s1 = 0.0;
-    for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
-        s0 += part[3 * (size_t)b + 0];
-        s1 += part[3 * (size_t)b + 1];
+    if (split > 1) {
+        const int ncubes = nparts / split;
+        const double q = ceil(p / split);
+        for (int cb = threadIdx.x; cb < ncubes; cb += blockDim.x) {
+            const double* v = part + 3 * (size_t)cb * split;
+            const double K0 = v[0];
+            double S1 = 0.0, S2 = 0.0;
+            for (int k = 0; k < split; ++k) {
+                const double n = fmin(q, fmax(p - q * k, 0.0));
+                const double dK = v[3 * k] - K0;
+                S2 += fma(dK, fma(n, dK, 2.0 * v[3 * k + 1]), v[3 * k + 2]);
+                S1 += fma(n, dK, v[3 * k + 1]);
+            }
+            s0 += K0 + S1 / p;
+            s1 += (S2 - S1 * S1 / p) / (p * (p - 1.0));
+        }
+    } else {
+        for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
+            s0 += part[3 * (size_t)b + 0];
+            s1 += part[3 * (size_t)b + 1];
+        }
     }
     s0 = block_sum(s0, scratch);
     s1 = block_sum(s1, scratch);
@@ -236,12 +260,19 @@ static __device__ void rebin_axis(const void* parts, size_t stride, int nparts, 
         return;
     }
     if (total <= 0.0) return;  // no information on this axis: grid unchanged
+    // compression ((r - 1)/ln r)^alpha with the library's log/exp (their FP64
+    // work is a few instructions; CUDA's log and pow cost ~100 on a pipe
+    // that issues 2 per clock per SM, and one block runs an axis)
+    const double inv_total = 1.0 / total;
     for (int k = threadIdx.x; k < nb; k += blockDim.x) {
-        const double r = sW[k] / total;
+        const double r = sW[k] * inv_total;
         double w;
         if (r <= 0.0) w = 0.0;
         else if (r == 1.0) w = 1.0;
-        else w = pow((r - 1.0) / log(r), alpha);
+        else {
+            const double q = (r - 1.0) / fx::fx_log(r);
+            w = alpha == 1.5 ? q * sqrt(q) : fx::fx_exp(alpha * fx::fx_log(q));
+        }
         sW[k] = w;
     }
     __syncthreads();

@@ -11,15 +11,28 @@
 // walk the cube range with a grid stride.  The bin grid of all axes is staged
 // in shared memory once per block as (left edge, nb * width) cells in the
 // integration box's coordinates.  In adjusting iterations every sample adds
-// F^2 to a per-block shared-memory histogram [d][nb], flushed to global
-// memory once at the end of the block: no per-sample global atomics.  Each
-// block writes three double partials (sum of cube means, of their variances,
-// of |means|) which the refinement launch reduces in fixed order.
+// F^2 to a per-block shared-memory histogram [d][nb], which the block adds
+// to the pass's global histogram once at its end (one global reduction per
+// non-empty bin; no per-sample global atomics).  Each block writes three
+// double partials (sum of cube means, of their variances, of |means|) which
+// the refinement launch reduces in fixed order.
 #pragma once
 
 #include "mc_device.cuh"
 
 namespace mc {
+
+// Adds v to the shared-memory histogram word at byte offset `off` of the
+// histogram whose shared-window address is `base` (a reduction: no value
+// comes back, so nothing waits on it).
+__device__ __forceinline__ void hist_add(uint32_t base, uint32_t idx, float v)
+{
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(base + 4u * idx), "f"(v));
+}
+__device__ __forceinline__ void hist_add(uint32_t base, uint32_t idx, double v)
+{
+    asm volatile("red.shared.add.f64 [%0], %1;" ::"r"(base + 8u * idx), "d"(v));
+}
 
 template <bool MIXED> struct Prec;
 template <> struct Prec<false> {
@@ -44,16 +57,28 @@ __device__ __forceinline__ void stage_grid(typename Prec<MIXED>::Cell* cells, ty
 {
     if constexpr (ADJ)
         for (uint32_t i = threadIdx.x; i < hist_d * nb; i += blockDim.x) hist[i] = typename Prec<MIXED>::H(0);
+    const double inv_g = 1.0 / (double)g;  // one division per thread, a multiply per cell
     for (uint32_t i = threadIdx.x; i < d * nb; i += blockDim.x) {
         const uint32_t j = i / nb, k = i - j * nb;
-        const DD right{grid[i], grid_lo[i]};
-        const DD left = k ? DD{grid[i - 1], grid_lo[i - 1]} : DD{0.0, 0.0};
-        const DD wd = dd_add(right, DD{-left.hi, -left.lo});
-        const double xl = lo[j] + scale[j] * left.hi;
-        const double xw = scale[j] * (wd.hi + wd.lo);
-        if constexpr (MIXED) cells[i] = make_float2((float)xl, (float)(xw * (double)nb));
-        else cells[i] = make_double2(xl, xw / (double)g);
+        if constexpr (MIXED) cells[i] = map_cell_f32(grid + j * nb, grid_lo + j * nb, k, lo[j], scale[j], nb);
+        else cells[i] = map_cell_f64(grid + j * nb, grid_lo + j * nb, k, lo[j], scale[j], inv_g);
     }
+}
+
+// The same staging from cells already built in global memory (by the
+// refinement after each rebin, and at set-up): a copy, 16-byte words.
+template <bool MIXED, bool ADJ>
+__device__ __forceinline__ void stage_cells(typename Prec<MIXED>::Cell* cells, typename Prec<MIXED>::H* hist,
+                                            const void* cells_g, uint32_t d, uint32_t nb, uint32_t hist_d)
+{
+    if constexpr (ADJ)
+        for (uint32_t i = threadIdx.x; i < hist_d * nb; i += blockDim.x) hist[i] = typename Prec<MIXED>::H(0);
+    const uint32_t bytes = d * nb * (uint32_t)sizeof(typename Prec<MIXED>::Cell);
+    const uint4* src = static_cast<const uint4*>(cells_g);
+    uint4* dst = reinterpret_cast<uint4*>(cells);
+    for (uint32_t i = threadIdx.x; i < bytes / 16; i += blockDim.x) dst[i] = src[i];
+    if (threadIdx.x == 0 && (bytes & 15u))  // an odd number of 8-byte cells
+        reinterpret_cast<uint2*>(cells)[bytes / 8 - 1] = static_cast<const uint2*>(cells_g)[bytes / 8 - 1];
 }
 
 // One sample: random words -> exact bin position -> map -> integrand.
@@ -136,6 +161,7 @@ __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIX
     constexpr int DN = 4 * NB4;
     const uint32_t d = a.d, nb = a.nb;
     const uint32_t hist_d = a.hist_d;  // axes with a histogram: d, or 1 (m-Cubes1D, Sec. 3)
+    const uint32_t hist_s = (uint32_t)__cvta_generic_to_shared(hist);
     const uint32_t L = lanes;
     const uint32_t seg_lane = threadIdx.x & (L - 1u);
     const uint32_t cubes_per_group = blockDim.x / L;
@@ -182,7 +208,7 @@ __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIX
                     const HT F2 = (HT)(F * F);
 #pragma unroll
                     for (int j = 0; j < DN; ++j)
-                        if (j < (int)hist_d) atomicAdd(&hist[(idx[j >> 1] >> (16 * (j & 1))) & 0xFFFFu], F2);
+                        if (j < (int)hist_d) hist_add(hist_s, (idx[j >> 1] >> (16 * (j & 1))) & 0xFFFFu, F2);
                 }
             }
         }
@@ -227,6 +253,95 @@ __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIX
     }
 }
 
+// Cube-split sampling, for geometries with few cubes and many samples each
+// (e.g. 64 cubes of 16384 samples): `split` blocks share one cube, block k
+// drawing samples [k q, min(p, (k+1) q)), q = ceil(p / split), spread over
+// its threads.  Every thread keeps sums of its samples shifted by its first
+// value K_t; they are re-based on thread 0's shift K (S1 += n dK,
+// S2 += dK (2 S1 + n dK), dK = K_t - K: no division) and summed in a fixed
+// order; the block writes (K, S1, S2) to out[0..2] and the refinement
+// combines a cube's blocks the same way.
+template <int FAM, bool MIXED, bool ADJ, int NB4, class A>
+__device__ __forceinline__ void sample_cube_slice(const A& a, const typename Prec<MIXED>::Cell* cells,
+                                                  typename Prec<MIXED>::H* hist, uint64_t cube, uint32_t k,
+                                                  uint32_t split, uint32_t it, uint32_t p,
+                                                  double (*red)[kVsThreads / 32], double* out)
+{
+    using R = typename Prec<MIXED>::R;
+    using HT = typename Prec<MIXED>::H;
+    constexpr int DN = 4 * NB4;
+    const uint32_t d = a.d, nb = a.nb;
+    const uint32_t hist_d = a.hist_d;
+    const uint32_t q = (p + split - 1) / split;
+    const uint32_t s_lo = k * q, s_hi = min(p, s_lo + q);
+    const uint32_t hist_s = (uint32_t)__cvta_generic_to_shared(hist);
+    const uint32_t c = (uint32_t)cube;
+    uint32_t nbc[DN];
+    {
+        uint32_t rest = c;
+#pragma unroll
+        for (int j = 0; j < DN; ++j) {
+            if (j < (int)d) {
+                uint32_t qq = __umulhi(rest, a.gmagic);
+                uint32_t r = rest - qq * a.g;
+                if (r >= a.g) { ++qq; r -= a.g; }
+                if (r >= a.g) { ++qq; r -= a.g; }
+                nbc[j] = r * nb;
+                rest = qq;
+            }
+        }
+    }
+    R K = R(0), S1 = R(0), S2 = R(0);
+    uint32_t n = 0;
+    for (uint32_t s = s_lo + threadIdx.x; s < s_hi; s += blockDim.x) {
+        uint32_t idx[2 * NB4];
+        const R F = sample_point<FAM, MIXED, NB4>(a, cells, c, s, it, nbc, idx);
+        if (n == 0) K = F;
+        const R z = F - K;
+        S1 += z;
+        S2 += z * z;
+        ++n;
+        if constexpr (ADJ) {
+            const HT F2 = (HT)(F * F);
+#pragma unroll
+            for (int j = 0; j < DN; ++j)
+                if (j < (int)hist_d) hist_add(hist_s, (idx[j >> 1] >> (16 * (j & 1))) & 0xFFFFu, F2);
+        }
+    }
+    // re-base on thread 0's shift (every thread has a sample: q >= blockDim;
+    // a thread without one adds nothing)
+    __syncthreads();
+    if (threadIdx.x == 0) red[0][0] = (double)K;
+    __syncthreads();
+    const double K0 = red[0][0];
+    __syncthreads();
+    const double dK = (double)K - K0, cnt = (double)n;
+    double s1 = (double)S1, s2 = (double)S2;
+    s2 = fma(dK, fma(cnt, dK, 2.0 * s1), s2);
+    s1 = fma(cnt, dK, s1);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        s1 += __shfl_down_sync(0xffffffffu, s1, off);
+        s2 += __shfl_down_sync(0xffffffffu, s2, off);
+    }
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red[1][warp] = s1;
+        red[2][warp] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b1 = 0.0, b2 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            b1 += red[1][w];
+            b2 += red[2][w];
+        }
+        out[0] = K0;
+        out[1] = b1;
+        out[2] = b2;
+    }
+}
+
 // Fixed-order block sum of the three per-thread sums; thread 0 writes them.
 __device__ __forceinline__ void block_write_sums(const CubeSums& acc, double (*red)[kVsThreads / 32], double* out)
 {
@@ -258,9 +373,11 @@ __device__ __forceinline__ void block_write_sums(const CubeSums& acc, double (*r
 }
 
 // Resident blocks per SM the register allocation is bounded for: three
-// (80 registers) where that costs no significant spilling, else two.
+// (80 registers) in mixed precision, where the latency hiding of 24 warps
+// is worth some spilling (measured: osc10, 12 axes' worth of state, +10%
+// with 132 bytes of spills), two in FP64.
 template <bool MIXED, int NB4>
-constexpr int vsample_min_blocks() { return (MIXED && NB4 <= 2) ? 3 : 2; }
+constexpr int vsample_min_blocks() { return MIXED ? 3 : 2; }
 
 template <int FAM, bool MIXED, bool ADJ, int NB4>
 __global__ void __launch_bounds__(kVsThreads, vsample_min_blocks<MIXED, NB4>())
@@ -285,17 +402,28 @@ vsample_kernel(const __grid_constant__ VsArgs a)
 
     Cell* cells = reinterpret_cast<Cell*>(smem);
     HT* hist = reinterpret_cast<HT*>(smem + cell_bytes(MIXED) * d * nb);
-    stage_grid<MIXED, ADJ>(cells, hist, a.grid, a.grid_lo, a.lo, a.scale, d, nb, a.g, a.hist_d);
+    if (a.cells_g) stage_cells<MIXED, ADJ>(cells, hist, a.cells_g, d, nb, a.hist_d);
+    else stage_grid<MIXED, ADJ>(cells, hist, a.grid, a.grid_lo, a.lo, a.scale, d, nb, a.g, a.hist_d);
     __syncthreads();
 
-    CubeSums acc;
-    sample_cubes<FAM, MIXED, ADJ, NB4>(a, cells, hist, a.cube_begin, a.cube_end - a.cube_begin, a.perm_k, blockIdx.x,
-                                       gridDim.x, it, a.lanes, a.p, acc);
-    block_write_sums(acc, red, a.part + 3 * (size_t)blockIdx.x);
+    if (a.split > 1) {
+        sample_cube_slice<FAM, MIXED, ADJ, NB4>(a, cells, hist, a.cube_begin + blockIdx.x / a.split,
+                                                blockIdx.x % a.split, a.split, it, a.p, red,
+                                                a.part + 3 * (size_t)blockIdx.x);
+    } else {
+        CubeSums acc;
+        sample_cubes<FAM, MIXED, ADJ, NB4>(a, cells, hist, a.cube_begin, a.cube_end - a.cube_begin, a.perm_k,
+                                           blockIdx.x, gridDim.x, it, a.lanes, a.p, acc);
+        block_write_sums(acc, red, a.part + 3 * (size_t)blockIdx.x);
+    }
     if constexpr (ADJ) {
         __syncthreads();
-        HT* out = reinterpret_cast<HT*>(a.part_hist) + (size_t)blockIdx.x * a.hist_d * nb;
-        for (uint32_t i = threadIdx.x; i < a.hist_d * nb; i += blockDim.x) out[i] = hist[i];
+        // the block's histogram goes into the pass's accumulator once: one
+        // global reduction per non-empty bin (no per-sample global atomics)
+        for (uint32_t i = threadIdx.x; i < a.hist_d * nb; i += blockDim.x) {
+            const double v = (double)hist[i];
+            if (v != 0.0) atomicAdd(a.hist_acc + i, v);
+        }
     }
     }
 }
@@ -321,7 +449,7 @@ cudaError_t launch_vsample_family(bool mixed, bool adjust, const VsArgs& a, int 
                                   cudaStream_t s)
 {
     auto k = vsample_kernel_ptr<FAM>(mixed, adjust, (int)a.d);
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit((const void*)k, smem);
     if (e != cudaSuccess) return e;
     k<<<grid, kVsThreads, smem, s>>>(a);
     return cudaGetLastError();
@@ -331,7 +459,7 @@ template <int FAM>
 cudaError_t occupancy_family(bool mixed, bool adjust, int d, size_t smem, int* blocks)
 {
     auto k = vsample_kernel_ptr<FAM>(mixed, adjust, d);
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit((const void*)k, smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, kVsThreads, smem);
 }

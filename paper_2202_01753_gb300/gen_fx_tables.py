@@ -9,6 +9,9 @@ floating-point arithmetic", ACM TOMS 15(2), 1989:
 * log: c_j = 1 + (j + 1/2)/256 for j = 0..255; 1/c_j as an unsigned Q63
   integer and ln(c_j) as an unsigned Q64 fraction; ln 2 to 128 bits.
 * exp: 2^(j/256) for j = 0..255 as unsigned Q62 integers.
+* single-precision cosine: pi/2 as the sum of three floats (each the float
+  nearest to what remains of pi/2) for a Cody-Waite reduction (Cody and
+  Waite, "Software Manual for the Elementary Functions", 1980), and 2/pi.
 
 Values are computed with 60-digit mpmath arithmetic and rounded once.
 Run from the repository root: python -m paper_2202_01753_gb300.gen_fx_tables
@@ -20,6 +23,12 @@ import os
 import mpmath
 
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc", "fx_tables.h")
+
+
+def _f32(x):
+    """x rounded to the nearest single-precision value (returned as a Python float)."""
+    import struct
+    return struct.unpack("<f", struct.pack("<f", float(mpmath.mpf(x))))[0]
 
 
 def _dd(x):
@@ -51,6 +60,7 @@ def render():
     c = ln2 / 256
     c_hi = float(mpmath.floor(c * 2 ** 42) / 2 ** 42)
     c_lo = float(c - mpmath.mpf(c_hi))
+    hp = mpmath.pi / 2
     lines = [
         "// fx_tables.h -- generated by paper_2202_01753_gb300/gen_fx_tables.py (do not edit).",
         "// Tables of the fixed-point logarithm and exponential (fx_math.cuh).",
@@ -66,6 +76,10 @@ def render():
         f"constexpr double kLn2Over256Hi = {c_hi!r};",
         f"constexpr double kLn2Over256Lo = {c_lo!r};",
         f"constexpr double k256OverLn2 = {float(256 / ln2)!r};",
+        f"constexpr float kHalfPiF1 = {_f32(hp)!r}f;  // pi/2 = F1 + F2 + F3 (+ ~1e-23)",
+        f"constexpr float kHalfPiF2 = {_f32(hp - _f32(hp))!r}f;",
+        f"constexpr float kHalfPiF3 = {_f32(hp - _f32(hp) - _f32(hp - _f32(hp)))!r}f;",
+        f"constexpr float kTwoOverPiF = {_f32(2 / mpmath.pi)!r}f;",
         "",
         "// 1 / c_j, c_j = 1 + (j + 1/2)/256, as Q63",
         "__device__ const uint64_t kLogInvC[256] = {",

@@ -190,6 +190,28 @@ def test_edge_shapes(gpu_ctx_factory, d, ncall, nb, lanes):
     assert_parity(w, o, g)
 
 
+@pytest.mark.parametrize("d,ncall,g,ita", [
+    (2, 100_000, 3, None),   # 9 cubes of 11111 samples: 43 blocks per cube, a ragged last slice
+    (3, 1_000_000, 2, 2),    # 8 cubes of 125000 samples, then no-adjust iterations
+    (1, 300_000, 1, None),   # one cube
+])
+def test_cube_split_mode(gpu_ctx_factory, d, ncall, g, ita):
+    """Few cubes with many samples: several blocks share each cube and the
+    refinement merges their (count, mean, M2) in order."""
+    rng = np.random.Generator(np.random.PCG64(77 + d))
+    w = W.random_integral(rng, d, W.F_GAUSS, ncall, itmax=4, seed=13)
+    w.precision = "fp64"
+    w.g_override = g
+    w.ita = ita
+    o = oracle_run(w)
+    g_ = gpu_run(gpu_ctx_factory, w)
+    assert g_["geom"]["blocks"] > g_["geom"]["m"]      # the split layout ran
+    assert_parity(w, o, g_)
+    gm = gpu_run(gpu_ctx_factory, w, precision="mixed")
+    err = np.max(np.abs(gm["I"] - o["trace_I"])) / cond_scale(w, o)
+    assert err < MIXED_BOUND, err
+
+
 def test_no_adjust_iterations_keep_grid(gpu_ctx_factory):
     w = W.suite("f4", 3, ncall=50_000, itmax=5)
     w.ita = 2

@@ -44,15 +44,19 @@ from paper_2202_01753_gb300 import closed_forms as CF  # noqa: E402
 # profiles/ (the per-unit figures of the roofline), keyed by (config,
 # precision).  "fp64": FP64 instructions per sample (DFMA + DADD + DMUL) against
 # the FP64 pipe (2 per clk per SM on GB300, ncu peak_sustained); "issue": issued warp
-# instructions per 32 samples against 4 issue slots/clk/SM.
+# instructions per 32 samples against 4 issue slots/clk/SM.  "traffic": DRAM
+# bytes read + written by one full-size launch (one-pass ncu capture of
+# dram__bytes_read.sum and dram__bytes_write.sum on the same kernel build).
 ROOFLINE_UNITS = {
-    ("cosmo6", "fp64"): {"kind": "fp64", "per_sample": 58.41,
+    ("cosmo6", "fp64"): {"kind": "fp64", "per_sample": 54.78, "traffic": 211.97e3,
                          "source": "profiles/vsample_cosmo6_fp64.md"},
-    ("table6", "fp64"): {"kind": "fp64", "per_sample": 66.56, "dram_bytes_per_sample": 409.4,
+    ("gauss3", "fp64"): {"kind": "fp64", "per_sample": 31.39, "traffic": 104.19e3,
+                         "source": "profiles/vsample_gauss3_fp64.md"},
+    ("table6", "fp64"): {"kind": "fp64", "per_sample": 64.49, "dram_bytes_per_sample": 409.3, "traffic": 38.5135e9,
                          "source": "profiles/vsample_table6_fp64.md"},
-    ("corner8", "mixed"): {"kind": "issue", "per_sample": 683.0,
+    ("corner8", "mixed"): {"kind": "issue", "per_sample": 677.3, "traffic": 502.53e3,
                            "source": "profiles/vsample_corner8_mixed.md"},
-    ("osc10", "mixed"): {"kind": "issue", "per_sample": 793.5,
+    ("osc10", "mixed"): {"kind": "issue", "per_sample": 805.8, "traffic": 515.84e3,
                          "source": "profiles/vsample_osc10_mixed.md"},
 }
 DFMA_PER_CLK_PER_SM = 2.0
@@ -358,7 +362,7 @@ def ours(args):
         peak = DFMA_PER_CLK_PER_SM * sms * sm_mhz * 1e6 / 1e12              # T FP64 instructions/s
         achieved = unit["per_sample"] * N / t_launch / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T FP64-inst/s",
-                "frac": achieved / peak, "traffic": None, "pipe": "fp64",
+                "frac": achieved / peak, "traffic": unit.get("traffic"), "pipe": "fp64",
                 "peak_how": "2 FP64 instructions/clk/SM (ncu peak_sustained) x SMs x median SM clock under load",
                 "measured_dfma_per_s": pk["dfma_per_s"],
                 "per_sample": f"{unit['per_sample']} FP64 instructions, DFMA+DADD+DMUL ({unit['source']})"}
@@ -371,7 +375,7 @@ def ours(args):
         peak = ISSUE_PER_CLK_PER_SM * sms * sm_mhz * 1e6 / 1e9              # G warp-instructions/s
         achieved = unit["per_sample"] * (N / 32.0) / t_launch / 1e9
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gwarp-inst/s", "frac": achieved / peak,
-                "traffic": None, "pipe": "issue",
+                "traffic": unit.get("traffic"), "pipe": "issue",
                 "peak_how": "4 warp-instructions/clk/SM x SMs x median SM clock under load",
                 "per_sample": f"{unit['per_sample']} thread-instructions ({unit['source']})"}
     else:

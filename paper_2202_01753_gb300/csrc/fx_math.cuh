@@ -10,7 +10,8 @@
 // (fx_tables.h, generated by gen_fx_tables.py), but evaluate the reduced
 // argument's series in Q62 integers: the logarithm uses no FP64 operation
 // (its parts are summed as a 128-bit fixed-point number and rounded to a
-// double with integer operations), the exponential six.
+// double with integer operations), the exponential one (the FMA that picks
+// n = round(y 256/ln 2); r = y - n ln2/256 is formed in 128-bit integers).
 //
 // Accuracy (tested against 60-digit references): fx_exp within 1 ulp;
 // fx_log within 1 ulp plus 2^-58 absolute (the series is absolute-accurate,
@@ -83,15 +84,22 @@ __device__ __forceinline__ double fx_log(double x)
 
 __device__ __forceinline__ double fx_exp(double y)
 {
-    const uint64_t ay = (uint64_t)__double_as_longlong(y) & 0x7FFFFFFFFFFFFFFFull;
+    const uint64_t u = (uint64_t)__double_as_longlong(y);
+    const uint64_t ay = u & 0x7FFFFFFFFFFFFFFFull;
     if (ay >= 0x4086200000000000ull) return exp(y);  // |y| >= 708 (or NaN): CUDA's exp
-    // y = n ln2/256 + r, n = round(y 256/ln2) by the 1.5 * 2^52 shift
+    if (ay < 0x3C30000000000000ull) return 1.0 + y;  // |y| < 2^-60: exp(y) rounds from 1 + y
+    // y = n ln2/256 + r, n = round(y 256/ln2) by the 1.5 * 2^52 shift (one FMA)
     const double t = fma(y, k256OverLn2, 0x1.8p52);
     const int64_t n = __double_as_longlong(t) - __double_as_longlong(0x1.8p52);
-    const double nd = t - 0x1.8p52;
-    double r = fma(-nd, kLn2Over256Hi, y);  // exact: n * hi is exact and cancels
-    r = fma(-nd, kLn2Over256Lo, r);        // |r| <= ln2/512 + tiny
-    const int64_t rq = __double2ll_rz(r * 0x1p62);
+    // r = y - n ln2/256 in Q62 with integers: y exactly (bits below 2^-62
+    // dropped; |y| < 2^10 fits 72 bits) minus n ln2/256 from a Q115 constant
+    const int sh = (int)((u >> 52) & 0x7FF) - 1013;  // y = M 2^(E-1075): Q62 needs a shift by E - 1013
+    const uint64_t M = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    __int128 Y = sh >= 0 ? ((__int128)M << sh) : (__int128)(M >> -sh);
+    if (u >> 63) Y = -Y;
+    const __int128 C = ((__int128)kLn2Over256Q115Hi << 64) | (__int128)kLn2Over256Q115Lo;
+    const __int128 L = ((__int128)n * C + ((__int128)1 << 52)) >> 53;
+    const int64_t rq = (int64_t)(Y - L);  // |r| <= ln2/512 + tiny: |rq| < 2^54
     // e^r = 1 + r + r^2/2 + r^3/6 + r^4/24 + r^5/120 (+ |r|^6/720 < 2^-66)
     int64_t s = kQ62One / 120;
     s = kQ62One / 24 + mul_q62(rq, s);

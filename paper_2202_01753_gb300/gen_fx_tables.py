@@ -8,7 +8,8 @@ floating-point arithmetic", ACM TOMS 15(2), 1989:
 
 * log: c_j = 1 + (j + 1/2)/256 for j = 0..255; 1/c_j as an unsigned Q63
   integer and ln(c_j) as an unsigned Q64 fraction; ln 2 to 128 bits.
-* exp: 2^(j/256) for j = 0..255 as unsigned Q62 integers.
+* exp: 2^(j/256) for j = 0..255 as unsigned Q62 integers; ln 2 / 256 as a
+  128-bit Q115 integer for the fixed-point argument reduction.
 * single-precision cosine: pi/2 as the sum of three floats (each the float
   nearest to what remains of pi/2) for a Cody-Waite reduction (Cody and
   Waite, "Software Manual for the Elementary Functions", 1980), and 2/pi.
@@ -55,12 +56,9 @@ def render():
     # ln 2 as a 128-bit binary fraction (two 64-bit words)
     ln2_q128 = int(mpmath.floor(ln2 * 2 ** 128))
     ln2_w1, ln2_w2 = ln2_q128 >> 64, ln2_q128 & (2 ** 64 - 1)
-    # ln 2 / 256 split for the exponential's Cody-Waite reduction: n * hi must
-    # be exact for |n| < 2^19, so hi keeps 34 significant bits
     c = ln2 / 256
-    c_hi = float(mpmath.floor(c * 2 ** 42) / 2 ** 42)
-    c_lo = float(c - mpmath.mpf(c_hi))
     hp = mpmath.pi / 2
+    c_q115 = int(mpmath.nint(c * mpmath.mpf(2) ** 115))
     lines = [
         "// fx_tables.h -- generated by paper_2202_01753_gb300/gen_fx_tables.py (do not edit).",
         "// Tables of the fixed-point logarithm and exponential (fx_math.cuh).",
@@ -73,9 +71,9 @@ def render():
         "",
         f"constexpr uint64_t kLn2W1 = 0x{ln2_w1:016x}ull;  // ln 2 = (W1 + W2 2^-64) 2^-64",
         f"constexpr uint64_t kLn2W2 = 0x{ln2_w2:016x}ull;",
-        f"constexpr double kLn2Over256Hi = {c_hi!r};",
-        f"constexpr double kLn2Over256Lo = {c_lo!r};",
         f"constexpr double k256OverLn2 = {float(256 / ln2)!r};",
+        f"constexpr uint64_t kLn2Over256Q115Hi = 0x{c_q115 >> 64:016x}ull;  // ln2/256 = (Hi 2^64 + Lo) 2^-115",
+        f"constexpr uint64_t kLn2Over256Q115Lo = 0x{c_q115 & (2 ** 64 - 1):016x}ull;",
         f"constexpr float kHalfPiF1 = {_f32(hp)!r}f;  // pi/2 = F1 + F2 + F3 (+ ~1e-23)",
         f"constexpr float kHalfPiF2 = {_f32(hp - _f32(hp))!r}f;",
         f"constexpr float kHalfPiF3 = {_f32(hp - _f32(hp) - _f32(hp - _f32(hp)))!r}f;",

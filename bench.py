@@ -47,6 +47,8 @@ from paper_2202_01753_gb300 import closed_forms as CF  # noqa: E402
 # instructions per 32 samples against 4 issue slots/clk/SM.  "traffic": DRAM
 # bytes read + written by one full-size launch (one-pass ncu capture of
 # dram__bytes_read.sum and dram__bytes_write.sum on the same kernel build).
+# "fp32_flops": 2 FFMA + FADD + FMUL per sample (the FP32-pipe fraction shown
+# beside the issue fraction).
 ROOFLINE_UNITS = {
     ("cosmo6", "fp64"): {"kind": "fp64", "per_sample": 54.78, "traffic": 211.97e3,
                          "source": "profiles/vsample_cosmo6_fp64.md"},
@@ -54,9 +56,9 @@ ROOFLINE_UNITS = {
                          "source": "profiles/vsample_gauss3_fp64.md"},
     ("table6", "fp64"): {"kind": "fp64", "per_sample": 64.49, "dram_bytes_per_sample": 409.3, "traffic": 38.5135e9,
                          "source": "profiles/vsample_table6_fp64.md"},
-    ("corner8", "mixed"): {"kind": "issue", "per_sample": 677.3, "traffic": 502.53e3,
+    ("corner8", "mixed"): {"kind": "issue", "per_sample": 677.3, "traffic": 502.53e3, "fp32_flops": 109.94,
                            "source": "profiles/vsample_corner8_mixed.md"},
-    ("osc10", "mixed"): {"kind": "issue", "per_sample": 805.8, "traffic": 515.84e3,
+    ("osc10", "mixed"): {"kind": "issue", "per_sample": 805.8, "traffic": 515.84e3, "fp32_flops": 139.5,
                          "source": "profiles/vsample_osc10_mixed.md"},
 }
 DFMA_PER_CLK_PER_SM = 2.0
@@ -378,6 +380,13 @@ def ours(args):
                 "traffic": unit.get("traffic"), "pipe": "issue",
                 "peak_how": "4 warp-instructions/clk/SM x SMs x median SM clock under load",
                 "per_sample": f"{unit['per_sample']} thread-instructions ({unit['source']})"}
+        if unit.get("fp32_flops"):
+            fp32_peak = 2 * 128 * sms * sm_mhz * 1e6 / 1e12          # TFLOP/s: 128 FFMA lanes/SM
+            fp32 = unit["fp32_flops"] * N / t_launch / 1e12
+            roof["fp32"] = {"achieved_tflops": fp32, "peak_tflops": fp32_peak, "frac": fp32 / fp32_peak,
+                            "flops_per_sample": unit["fp32_flops"],
+                            "how": "(2 FFMA + FADD + FMUL) per sample from ncu x samples / kernel time against "
+                                   "128 FMA lanes x 2 x SMs x clock"}
     else:
         roof = {"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
                 "note": "no ncu per-sample count recorded for this configuration"}

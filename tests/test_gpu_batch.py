@@ -53,7 +53,9 @@ def test_batch_matches_solo(gpu_ctx_factory, precision, rtol):
         assert b["status"] == s["status"] == mcubes.ENOCONV
         assert b["iterations"] == s["iterations"] == w.itmax
         assert (b["g"], b["m"], b["p"]) == (s["g"], s["m"], s["p"])
-        scale = max(abs(s["estimate"]), s["sigma"])
+        # |I|, sigma, and a floor for oscillatory integrals that cancel to
+        # near zero (far below the integrands' O(1) values)
+        scale = max(abs(s["estimate"]), s["sigma"], 1e-9)
         assert abs(b["estimate"] - s["estimate"]) <= rtol * scale, (w.name, b["estimate"], s["estimate"])
         assert b["sigma"] == pytest.approx(s["sigma"], rel=rtol * 10)
 

@@ -71,14 +71,38 @@ namespace {
 
 using namespace refine_detail;
 
-// Refinement of one iteration of every live integral: block (axis, j) of the
-// live integral j rebins that axis (adjusting iterations); block (d or 0, j)
-// reduces the integral's segment partials in order and weighs the iteration.
+// Map cells of one axis of a slot from its grid (block-wide).
+__device__ void slot_cells_row(const BatchDesc& D, int j)
+{
+    const int nb = (int)D.nb;
+    const double* row = D.grid + (size_t)j * nb;
+    const double* row_lo = D.grid + (size_t)D.d * nb + (size_t)j * nb;
+    const double inv_g = 1.0 / (double)D.g;
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+        const size_t i = (size_t)j * nb + k;
+        if (D.mixed) static_cast<float2*>(D.cells)[i] = map_cell_f32(row, row_lo, k, D.lo[j], D.scale[j], nb);
+        else static_cast<double2*>(D.cells)[i] = map_cell_f64(row, row_lo, k, D.lo[j], D.scale[j], inv_g);
+    }
+}
+
+__device__ void refine_one(const BatchRefineArgs& a, uint32_t j, double* scratch);
+
+// Refinement of one iteration of every live integral: block row y handles
+// live integrals y, y + gridDim.y, ...; for integral j, block (axis, row)
+// rebins that axis (adjusting iterations) and block (d or 0, row) reduces
+// the integral's segment partials in order and weighs the iteration.
 __global__ void __launch_bounds__(kRefineThreads) refine_batch_kernel(const __grid_constant__ BatchRefineArgs a)
 {
     __shared__ double scratch[33];
-    const uint32_t j = blockIdx.y;
-    if (j >= *a.nlive) return;
+    const uint32_t nlive = *a.nlive;
+    for (uint32_t j = blockIdx.y; j < nlive; j += gridDim.y) {
+        refine_one(a, j, scratch);
+        __syncthreads();  // scratch is reused by the next integral
+    }
+}
+
+__device__ void refine_one(const BatchRefineArgs& a, uint32_t j, double* scratch)
+{
     const uint32_t slot = a.live[j];
     const BatchDesc& D = a.desc[slot];
     const uint32_t s0 = a.live_seg[j], s1 = a.live_seg[j + 1];
@@ -98,6 +122,8 @@ __global__ void __launch_bounds__(kRefineThreads) refine_batch_kernel(const __gr
         const char* parts = static_cast<const char*>(a.seg_hist) + (a.segs[s0].hist_off + off) * elem;
         rebin_axis(parts, (size_t)d * nb, (int)(s1 - s0), a.hist_is_float != 0, nb, a.alpha, D.grid + off,
                    D.grid + (size_t)d * nb + off, D.hist + off, &st->error, &st->done, scratch);
+        __syncthreads();  // the axis's new edges are in global memory: rebuild its map cells
+        slot_cells_row(D, ax);
     }
 }
 
@@ -119,6 +145,8 @@ __global__ void init_slots_kernel(const BatchDesc* desc, BatchState* st, const u
         D.grid[(size_t)d * nb + i] = lo;
         D.hist[i] = 0.0;
     }
+    __syncthreads();  // the grid is in global memory: build the map cells
+    for (int j = 0; j < d; ++j) slot_cells_row(D, j);
     if (threadIdx.x == 0) {
         BatchState z;
         memset(&z, 0, sizeof z);
@@ -128,9 +156,9 @@ __global__ void init_slots_kernel(const BatchDesc* desc, BatchState* st, const u
 
 }  // namespace
 
-cudaError_t launch_refine_batch(const BatchRefineArgs& a, int capacity, cudaStream_t s)
+cudaError_t launch_refine_batch(const BatchRefineArgs& a, int capacity, int rows, cudaStream_t s)
 {
-    refine_batch_kernel<<<dim3(kDMax + 1, capacity), kRefineThreads, 0, s>>>(a);
+    refine_batch_kernel<<<dim3(kDMax + 1, std::max(1, std::min(capacity, rows))), kRefineThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -158,7 +186,7 @@ void BatchEngine::release()
     if (graph_) cudaGraphDestroy(graph_);
     exec_ = nullptr;
     graph_ = nullptr;
-    for (DevBuf* b : {&desc_, &st_, &grids_, &hists_, &histories_, &segs_, &blk_seg_, &live_, &live_seg_, &nlive_,
+    for (DevBuf* b : {&desc_, &st_, &grids_, &cells_, &hists_, &histories_, &segs_, &blk_seg_, &live_, &live_seg_, &nlive_,
                       &seg_part_, &seg_hist_, &admit_slots_})
         b->release();
     if (h_segs_) cudaFreeHost(h_segs_);
@@ -198,6 +226,7 @@ cudaError_t BatchEngine::reserve(int capacity, int itcap)
     const size_t table = (size_t)kNumClasses * (bmax_ + 1);
     if ((e = desc_.reserve(sizeof(BatchDesc) * capacity)) || (e = st_.reserve(sizeof(BatchState) * capacity)) ||
         (e = grids_.reserve(sizeof(double) * grid_stride * capacity)) ||
+        (e = cells_.reserve(cell_bytes(mixed_) * hist_stride * capacity)) ||
         (e = hists_.reserve(sizeof(double) * hist_stride * capacity)) ||
         (e = histories_.reserve(sizeof(double) * 2 * (size_t)itcap * capacity)) ||
         (e = segs_.reserve(sizeof(BatchSeg) * segmax)) || (e = blk_seg_.reserve(sizeof(uint32_t) * table)) ||
@@ -235,7 +264,8 @@ size_t BatchEngine::slot_bytes(const mcubes_opts& o, int itcap)
     const size_t bins = (size_t)kDMax * o.nbins;
     const size_t elem = o.precision == MCUBES_MIXED ? sizeof(float) : sizeof(double);
     return sizeof(double) * (3 * bins + 2 * (size_t)itcap) + sizeof(BatchDesc) + sizeof(BatchState) +
-           bins * elem + sizeof(BatchSeg) + 3 * sizeof(double) + 3 * sizeof(uint32_t);
+           bins * elem + bins * cell_bytes(o.precision == MCUBES_MIXED) + sizeof(BatchSeg) + 3 * sizeof(double) +
+           3 * sizeof(uint32_t);
 }
 
 mcubes_status BatchEngine::validate(const mcubes_request& r) const
@@ -289,6 +319,8 @@ mcubes_status BatchEngine::admit(const mcubes_request& r, long long tag, int* sl
     D.fam = fp;
     const size_t grid_stride = 2 * (size_t)kDMax * nb, hist_stride = (size_t)kDMax * nb;
     D.grid = (double*)grids_.ptr + grid_stride * slot;
+    D.cells = static_cast<unsigned char*>(cells_.ptr) + cell_bytes(mixed_) * hist_stride * slot;
+    D.mixed = mixed_ ? 1 : 0;
     D.hist = (double*)hists_.ptr + hist_stride * slot;
     D.hist_I = (double*)histories_.ptr + 2 * (size_t)itcap_ * slot;
     D.hist_V = D.hist_I + itcap_;
@@ -463,7 +495,7 @@ cudaError_t BatchEngine::enqueue_iteration(unsigned mask)
         cudaError_t e = launch_vsample_batch(c, mixed_, sample_args(c), class_blocks(c), smem_bytes(c), stream_);
         if (e) return e;
     }
-    return launch_refine_batch(refine_args(), capacity_, stream_);
+    return launch_refine_batch(refine_args(), capacity_, 2 * num_sms_, stream_);
 }
 
 // One iteration as a CUDA graph: the sampling kernels of the classes in the

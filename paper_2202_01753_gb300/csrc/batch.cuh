@@ -42,8 +42,8 @@ vsample_batch_kernel(const __grid_constant__ BatchArgs a)
         const uint32_t d = sd.d, nb = sd.nb;
         Cell* cells = reinterpret_cast<Cell*>(smem);
         HT* hist = reinterpret_cast<HT*>(smem + cell_bytes(MIXED) * d * nb);
-        if (seg.adjust) stage_grid<MIXED, true>(cells, hist, sd.grid, sd.grid + d * nb, sd.lo, sd.scale, d, nb, sd.g, d);
-        else stage_grid<MIXED, false>(cells, hist, sd.grid, sd.grid + d * nb, sd.lo, sd.scale, d, nb, sd.g, d);
+        if (seg.adjust) stage_cells<MIXED, true>(cells, hist, sd.cells, d, nb, d);
+        else stage_cells<MIXED, false>(cells, hist, sd.cells, d, nb, d);
         __syncthreads();
 
         const BatchView v{d, nb, sd.g, sd.gmagic, sd.key0, sd.key1, d, sd.jac0, sd.phi_scale_f, sd.fam};

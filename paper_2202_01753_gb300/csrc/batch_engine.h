@@ -112,7 +112,7 @@ private:
     std::vector<BatchDesc> hdesc_;
     std::vector<int> free_, pending_;
 
-    DevBuf desc_, st_, grids_, hists_, histories_, segs_, blk_seg_, live_, live_seg_, nlive_, seg_part_, seg_hist_,
+    DevBuf desc_, st_, grids_, cells_, hists_, histories_, segs_, blk_seg_, live_, live_seg_, nlive_, seg_part_, seg_hist_,
         admit_slots_;
     BatchSeg* h_segs_ = nullptr;     // pinned staging
     uint32_t* h_small_ = nullptr;    // pinned staging: block offsets, live lists, counts

@@ -100,7 +100,7 @@ struct BatchDesc {
     uint32_t d, nb, g, gmagic;
     uint32_t p, lanes;
     uint32_t key0, key1;        // Philox key = the integral's own seed
-    int family, ita, itmax, pad;
+    int family, ita, itmax, mixed;
     uint64_t m;
     double jac0;                // (g nb)^d
     float phi_scale_f;          // 1 / (g nb)
@@ -109,6 +109,8 @@ struct BatchDesc {
     double scale[kDMax];
     FamParams fam;
     double* grid;               // [d][nb] edge high parts, then [d][nb] low parts
+    void* cells;                // [d][nb] map cells of the grid (double2 in FP64, float2 in mixed), rebuilt
+                                // by the refinement after each rebin
     double* hist;               // [d][nb] histogram of the last adjusting iteration
     double* hist_I;             // [itmax] iteration estimates
     double* hist_V;             // [itmax] iteration variances
@@ -158,7 +160,7 @@ constexpr int kNumClasses = MCUBES_F_TABLE * 3;  // families with batched kernel
 __host__ __device__ constexpr int batch_class(int family, int d) { return family * 3 + (d + 3) / 4 - 1; }
 cudaError_t launch_vsample_batch(int cls, bool mixed, const BatchArgs& a, int grid, size_t smem, cudaStream_t s);
 cudaError_t vsample_batch_occupancy(int cls, bool mixed, size_t smem, int* blocks_per_sm);
-cudaError_t launch_refine_batch(const BatchRefineArgs& a, int capacity, cudaStream_t s);
+cudaError_t launch_refine_batch(const BatchRefineArgs& a, int capacity, int rows, cudaStream_t s);
 cudaError_t launch_init_slots(const BatchDesc* desc, BatchState* st, const uint32_t* slots, int count,
                               cudaStream_t s);
 

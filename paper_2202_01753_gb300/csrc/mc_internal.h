@@ -77,7 +77,7 @@ struct VsArgs {
     uint32_t it_fixed;
     uint32_t d, nb, g, gmagic;  // gmagic = floor((2^32-1)/g)
     uint32_t p, lanes;          // samples per cube, threads per cube (power of two <= 32)
-    uint32_t hist_d;            // axes with a histogram: d, or 1 for m-Cubes1D (part_hist is [gridDim][hist_d][nb])
+    uint32_t hist_d;            // axes with a histogram: d, or 1 for m-Cubes1D (hist_acc is [hist_d][nb])
     uint32_t split;             // > 1: blocks per cube (cube-split mode: gridDim = cubes * split, part holds
                                 // each block's shifted sums (K, S1, S2) of its slice of one cube)
     uint64_t cube_begin, cube_end;

@@ -1,8 +1,9 @@
 // refine.cu -- per-iteration finalisation of a single integral on the
 // device: the fixed-order reduction of the sampling launch's block partials,
-// Adjust-Bin-Bounds (Alg. 2) as one block per axis, and Weighted-Estimates
-// plus Check-Convergence (Alg. 2) as one more block.  Keeping these on the GPU
-// lets a whole iteration run without the host.
+// Adjust-Bin-Bounds (Alg. 2) as one block per axis (reading and clearing the
+// pass's histogram, then rebuilding that axis's map cells), and
+// Weighted-Estimates plus Check-Convergence (Alg. 2) as one more block.
+// Keeping these on the GPU lets a whole iteration run without the host.
 #include "refine_dev.cuh"
 
 namespace mc {

@@ -372,15 +372,16 @@ __device__ __forceinline__ void block_write_sums(const CubeSums& acc, double (*r
     }
 }
 
-// Resident blocks per SM the register allocation is bounded for: three
-// (80 registers) in mixed precision, where the latency hiding of 24 warps
-// is worth some spilling (measured: osc10, 12 axes' worth of state, +10%
-// with 132 bytes of spills), two in FP64.
-template <bool MIXED, int NB4>
-constexpr int vsample_min_blocks() { return MIXED ? 3 : 2; }
+// Resident blocks per SM the register allocation is bounded for: three (80
+// registers, 24 warps) — measured against two: osc10 mixed +10% despite 132
+// bytes of spills, cosmo6 FP64 +4% and gauss3 FP64 +9% with none — except
+// for the table integrands in FP64, whose spills and larger table footprint
+// in L1/L2 cost a third (two blocks).
+template <int FAM, bool MIXED, int NB4>
+constexpr int vsample_min_blocks() { return (FAM == MCUBES_F_TABLE && !MIXED) ? 2 : 3; }
 
 template <int FAM, bool MIXED, bool ADJ, int NB4>
-__global__ void __launch_bounds__(kVsThreads, vsample_min_blocks<MIXED, NB4>())
+__global__ void __launch_bounds__(kVsThreads, vsample_min_blocks<FAM, MIXED, NB4>())
 vsample_kernel(const __grid_constant__ VsArgs a)
 {
     if constexpr (FAM == MCUBES_F_COSMO6 && NB4 != 2) {

@@ -50,9 +50,9 @@ from paper_2202_01753_gb300 import closed_forms as CF  # noqa: E402
 # "fp32_flops": 2 FFMA + FADD + FMUL per sample (the FP32-pipe fraction shown
 # beside the issue fraction).
 ROOFLINE_UNITS = {
-    ("cosmo6", "fp64"): {"kind": "fp64", "per_sample": 54.78, "traffic": 211.97e3,
+    ("cosmo6", "fp64"): {"kind": "fp64", "per_sample": 54.89, "traffic": 371.97e3,
                          "source": "profiles/vsample_cosmo6_fp64.md"},
-    ("gauss3", "fp64"): {"kind": "fp64", "per_sample": 31.39, "traffic": 104.19e3,
+    ("gauss3", "fp64"): {"kind": "fp64", "per_sample": 31.34, "traffic": 104.45e3,
                          "source": "profiles/vsample_gauss3_fp64.md"},
     ("table6", "fp64"): {"kind": "fp64", "per_sample": 64.49, "dram_bytes_per_sample": 409.3, "traffic": 38.5135e9,
                          "source": "profiles/vsample_table6_fp64.md"},

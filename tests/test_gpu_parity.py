@@ -179,6 +179,9 @@ def test_mixed_configs_in_fp64_scaled(gpu_ctx_factory, make):
     (8, 20_000, 1024, 0),    # the largest bin count
     (2, 9_999, 500, 4),      # forced lanes with a ragged p (p = 4999/... )
     (5, 77_777, 333, 8),
+    (1, 2, 2, 0),            # the smallest problem: one cube of two samples
+    (12, 2, 50, 0),          # twelve axes, one cube of two samples
+    (3, 3, 64, 0),           # ncall odd and below two cubes' worth: g = 1, p = 3
 ])
 def test_edge_shapes(gpu_ctx_factory, d, ncall, nb, lanes):
     rng = np.random.Generator(np.random.PCG64(d * 1000 + nb))

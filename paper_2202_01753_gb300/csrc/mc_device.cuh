@@ -106,6 +106,47 @@ __device__ __forceinline__ uint4 sample_words(const BatchView& v, uint4 ctr)
 }
 
 // ---------------------------------------------------------------------------
+// Product of positive doubles in integer arithmetic (the FP64 kernels'
+// Jacobian): the running value is m 2^(e - 63) with m in [2^63, 2^64); each
+// factor's 53-bit significand is multiplied in as a 64 x 64 -> high-64
+// product (truncated: < 2^-63 relative per factor) and renormalised by one
+// bit; the result is rounded to a double once.  No FP64 instruction (GB300
+// issues 2 per clock per SM, the integer multiplies run elsewhere).
+// ---------------------------------------------------------------------------
+struct IntProd {
+    uint64_t m;
+    int e;
+};
+
+__device__ __forceinline__ IntProd int_prod_of(double v)  // v > 0, finite
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(v);
+    const int E = (int)(b >> 52);
+    const uint64_t mant = b & 0xFFFFFFFFFFFFFull;
+    if (E) return IntProd{(mant | (1ull << 52)) << 11, E - 1023};
+    const int s = __clzll((long long)mant);  // subnormal
+    return IntProd{mant << s, -1074 + 63 - s};
+}
+
+__device__ __forceinline__ void int_prod_mul(IntProd& p, double v)
+{
+    const IntProd f = int_prod_of(v);
+    const uint64_t H = __umul64hi(p.m, f.m);
+    const uint64_t top = H >> 63;
+    p.m = top ? H : H << 1;
+    p.e += f.e + (int)top;
+}
+
+__device__ __forceinline__ double int_prod_value(const IntProd& p)
+{
+    // rounded to 53 bits (2^53 after a carry); m + 2^10 could wrap around
+    const uint64_t r = (p.m >> 11) + ((p.m >> 10) & 1ull);
+    const int E = p.e + 1023;
+    if (E < 1 || E > 2046) return ldexp((double)r, p.e - 52);  // beyond the normal range: rare
+    return __longlong_as_double((long long)(((uint64_t)E << 52) + r - (1ull << 52)));
+}
+
+// ---------------------------------------------------------------------------
 // Map cell k of one axis in the box's coordinates, from the double-double
 // right edges (unit cube) of that axis's row: (x left edge, x width / g) for
 // the FP64 kernels, (x left edge, nb * x width) in single precision for the

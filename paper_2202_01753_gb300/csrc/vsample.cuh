@@ -107,9 +107,9 @@ sample_point(const A& a, const typename Prec<MIXED>::Cell* cells, uint32_t c, ui
     }
     typename Fam::S fs;
     Fam::begin(fs);
-    R jac;
-    if constexpr (MIXED) jac = 1.0f;
-    else jac = a.jac0;
+    R jac = R(1);                          // mixed: single-precision product of the widths
+    IntProd jp{0, 0};                      // FP64: the product in integer arithmetic, from jac0
+    if constexpr (!MIXED) jp = int_prod_of(a.jac0);
 #pragma unroll
     for (int j = 0; j < DN; ++j) {
         if (j < (int)d) {
@@ -123,13 +123,15 @@ sample_point(const A& a, const typename Prec<MIXED>::Cell* cells, uint32_t c, ui
             } else {
                 x = fma(cell.y, bin_gphi_f64(bp), cell.x);            // (width/g)(g phi)
             }
-            jac *= cell.y;
+            if constexpr (MIXED) jac *= cell.y;
+            else int_prod_mul(jp, cell.y);
             Fam::add(fs, j, x, a.fam);
             // flat histogram indices (< 2^16) packed two per register
             if (j & 1) idx[j >> 1] |= flat << 16;
             else idx[j >> 1] = flat;
         }
     }
+    if constexpr (!MIXED) jac = int_prod_value(jp);
     return Fam::end(fs, d, a.fam) * jac;
 }
 
@@ -199,10 +201,13 @@ __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIX
             for (uint32_t s = seg_lane; s < p; s += L) {
                 uint32_t idx[2 * NB4];
                 const R F = sample_point<FAM, MIXED, NB4>(a, cells, c, s, it, nbc, idx);
-                if (n == 0) K = F;
-                const R z = F - K;
-                S1 += z;
-                S2 += z * z;
+                if (n == 0) {
+                    K = F;  // the shift: its own term is zero
+                } else {
+                    const R z = F - K;
+                    S1 += z;
+                    S2 += z * z;
+                }
                 ++n;
                 if constexpr (ADJ) {
                     const HT F2 = (HT)(F * F);
@@ -296,10 +301,13 @@ __device__ __forceinline__ void sample_cube_slice(const A& a, const typename Pre
     for (uint32_t s = s_lo + threadIdx.x; s < s_hi; s += blockDim.x) {
         uint32_t idx[2 * NB4];
         const R F = sample_point<FAM, MIXED, NB4>(a, cells, c, s, it, nbc, idx);
-        if (n == 0) K = F;
-        const R z = F - K;
-        S1 += z;
-        S2 += z * z;
+        if (n == 0) {
+            K = F;  // the shift: its own term is zero
+        } else {
+            const R z = F - K;
+            S1 += z;
+            S2 += z * z;
+        }
         ++n;
         if constexpr (ADJ) {
             const HT F2 = (HT)(F * F);

@@ -242,25 +242,49 @@ def cpu_oracle_rate(w, seconds):
                             "sample": f"cubes [0, {n}) ({n * pb.p} samples, {dt1:.1f} s)"}}
 
 
+def _oracle_pass_it(job):
+    """_oracle_pass for a given iteration index (reference arm steps)."""
+    import oracle
+    spec, c0, c1, it = job
+    if spec.get("tables_from"):
+        name, kw = spec["tables_from"]
+        oracle.set_tables(W.CONFIGS[name](**kw).meta["tables"])
+    pb = oracle.Problem(spec["fid"], spec["params"], spec["lo"], spec["hi"], spec["ncall"], nb=spec["nb"],
+                        g_override=spec["g_override"], seed=spec["seed"])
+    B = oracle.init_grid(pb.d, pb.nb)
+    t = time.perf_counter()
+    pb.vsample(B, it, True, c0, c1)
+    return time.perf_counter() - t, (c1 - c0) * pb.p
+
+
 def reference_arm(args):
+    """The oracle (the method as plainly written) on the host: every step is
+    one adjusting pass over a bounded cube range of the workload, split into
+    one equal range per host core (spawned processes, started before
+    timing)."""
+    import multiprocessing as mp
+
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     w = workload(args, 0)
     import oracle
-    if w.fid == W.F_TABLE:
-        oracle.set_tables(w.meta["tables"])
-    pb = oracle.Problem(w.fid, w.params, w.lo, w.hi, w.ncall, nb=w.nb, g_override=w.g_override, seed=w.seed)
-    B = oracle.init_grid(pb.d, pb.nb)
-    # one step: one adjusting sampling pass of the oracle over a fixed cube range
-    cubes = max(1, min(pb.m, (400_000 // pb.p) if pb.p < 1000 else 1))
-    for i in range(args.warmup):
-        pb.vsample(B, i, True, 0, cubes)
-    t = time.perf_counter()
-    for i in range(args.steps):
-        pb.vsample(B, args.warmup + i, True, 0, cubes)
-    dt = time.perf_counter() - t
-    samples = cubes * pb.p * args.steps
+    g, m, p = oracle.geometry(w.d, w.ncall, w.g_override, w.nb)
+    cores = os.cpu_count() or 1
+    per = max(1, min(m // cores, (400_000 // p) if p < 1000 else 1))
+    spec = dict(fid=w.fid, params=[float(v) for v in w.params], lo=[float(v) for v in w.lo],
+                hi=[float(v) for v in w.hi], ncall=w.ncall, nb=w.nb, g_override=w.g_override, seed=w.seed,
+                tables_from=w.meta.get("tables_from"))
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_pass_it, [(spec, 0, 1, 0)] * cores)      # start-up and library load, untimed
+        for i in range(args.warmup):
+            pool.map(_oracle_pass_it, [(spec, c * per, (c + 1) * per, i) for c in range(cores)], chunksize=1)
+        t = time.perf_counter()
+        for i in range(args.steps):
+            pool.map(_oracle_pass_it, [(spec, c * per, (c + 1) * per, args.warmup + i) for c in range(cores)],
+                     chunksize=1)
+        dt = time.perf_counter() - t
+    samples = per * cores * p * args.steps
     value = samples / dt
     line = {
         "impl": "reference", "metric": "integrand evaluations per second", "value": value,
@@ -268,9 +292,10 @@ def reference_arm(args):
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "d": w.d, "ncall": w.ncall, "nbins": w.nb,
-                   "sample_per_step": f"cubes [0, {cubes}) of one iteration ({cubes * pb.p} samples)"},
-        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{cubes * pb.p} samples per step, {args.steps} steps"},
+                   "sample_per_step": f"cubes [0, {per * cores}) of one iteration ({per * cores * p} samples) "
+                                      f"in {cores} equal ranges, one process per core"},
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per * cores * p} samples per step, {args.steps} steps"},
         "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))

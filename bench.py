@@ -50,11 +50,12 @@ from paper_2202_01753_gb300 import closed_forms as CF  # noqa: E402
 # "fp32_flops": 2 FFMA + FADD + FMUL per sample (the FP32-pipe fraction shown
 # beside the issue fraction).
 ROOFLINE_UNITS = {
-    ("cosmo6", "fp64"): {"kind": "fp64", "per_sample": 54.89, "traffic": 371.97e3,
+    ("cosmo6", "fp64"): {"kind": "fp64", "per_sample": 48.89, "traffic": 585.47e3, "pipe_busy": 0.690,
                          "source": "profiles/vsample_cosmo6_fp64.md"},
-    ("gauss3", "fp64"): {"kind": "fp64", "per_sample": 31.34, "traffic": 104.45e3,
+    ("gauss3", "fp64"): {"kind": "fp64", "per_sample": 28.36, "traffic": 104.19e3, "pipe_busy": 0.779,
                          "source": "profiles/vsample_gauss3_fp64.md"},
-    ("table6", "fp64"): {"kind": "fp64", "per_sample": 64.49, "dram_bytes_per_sample": 409.3, "traffic": 38.5135e9,
+    ("table6", "fp64"): {"kind": "fp64", "per_sample": 58.49, "dram_bytes_per_sample": 409.3, "traffic": 38.5134e9,
+                         "pipe_busy": 0.831,
                          "source": "profiles/vsample_table6_fp64.md"},
     ("corner8", "mixed"): {"kind": "issue", "per_sample": 677.3, "traffic": 502.53e3, "fp32_flops": 109.94,
                            "source": "profiles/vsample_corner8_mixed.md"},
@@ -393,6 +394,8 @@ def ours(args):
                 "peak_how": "2 FP64 instructions/clk/SM (ncu peak_sustained) x SMs x median SM clock under load",
                 "measured_dfma_per_s": pk["dfma_per_s"],
                 "per_sample": f"{unit['per_sample']} FP64 instructions, DFMA+DADD+DMUL ({unit['source']})"}
+        if unit.get("pipe_busy"):
+            roof["ncu_fp64_pipe_busy"] = unit["pipe_busy"]   # sm__pipe_fp64_cycles_active, same kernel
         if unit.get("dram_bytes_per_sample"):
             hbm = unit["dram_bytes_per_sample"] * N / t_launch / 1e9
             roof["hbm"] = {"achieved_gbs": hbm, "peak_gbs": HBM_PEAK_GBS, "frac": hbm / HBM_PEAK_GBS,

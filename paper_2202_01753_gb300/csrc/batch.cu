@@ -312,6 +312,7 @@ mcubes_status BatchEngine::admit(const mcubes_request& r, long long tag, int* sl
     D.m = (uint64_t)m;
     D.jac0 = jacobian_scale(g, nb, d);
     D.phi_scale_f = (float)(1.0 / ((double)g * nb));
+    set_moment_scales(D, p);
     for (int j = 0; j < d; ++j) {
         D.lo[j] = r.lo[j];
         D.scale[j] = r.hi[j] - r.lo[j];

@@ -46,7 +46,8 @@ vsample_batch_kernel(const __grid_constant__ BatchArgs a)
         else stage_cells<MIXED, false>(cells, hist, sd.cells, d, nb, d);
         __syncthreads();
 
-        const BatchView v{d, nb, sd.g, sd.gmagic, sd.key0, sd.key1, d, sd.jac0, sd.phi_scale_f, sd.fam};
+        const BatchView v{d,        nb,           sd.g,     sd.gmagic,         sd.key0,          sd.key1, d,
+                          sd.jac0,  sd.phi_scale_f, sd.inv_p, sd.inv_var_den, sd.inv_p_f, sd.inv_var_den_f, sd.fam};
         const uint32_t it = a.st[seg.slot].it;
         CubeSums acc;
         if (seg.adjust)

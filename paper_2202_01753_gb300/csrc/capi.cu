@@ -174,6 +174,8 @@ bool integrand_prepare(int id, const double* p, int np, int d, FamParams* out, c
     case MCUBES_F_COSMO6:
         if (!(p[7] > 0.0) || !(p[9] > 0.0)) return false;
         for (int j = 0; j < 6; ++j) c[j] = p[j];
+        c[2] = p[2] + 1.0;  // the lognormals' 1/x_3, 1/x_4 join the a_3, a_4 powers
+        c[3] = p[3] + 1.0;
         c[6] = p[6];
         c[7] = 1.0 / (2.0 * p[7] * p[7]);
         c[8] = p[8];
@@ -276,6 +278,18 @@ double jacobian_scale(long long g, long long nb, int d)
     double j = 1.0;
     for (int i = 0; i < d; ++i) j *= (double)g * (double)nb;
     return j;
+}
+
+// 1/p and 1/(p (p-1)) of the cube moments (p >= 2), in both precisions,
+// each a correctly rounded IEEE division.
+MomentScales moment_scales(long long p)
+{
+    MomentScales m;
+    m.inv_p = 1.0 / (double)p;
+    m.inv_var_den = m.inv_p / (double)(p - 1);
+    m.inv_p_f = 1.0f / (float)p;
+    m.inv_var_den_f = m.inv_p_f / (float)(p - 1);
+    return m;
 }
 
 void philox_round_keys(uint64_t seed, uint32_t rk[10][2])
@@ -566,6 +580,7 @@ mcubes_status mcubes_setup(mcubes_ctx* c, int id, const double* params, int npar
     a.jac0 = jacobian_scale(g, nb, d);
     a.phi_scale_f = (float)(1.0 / ((double)g * nb));
     a.nb_f = (float)nb;
+    set_moment_scales(a, p);
     a.fam = fp;
 
     RefineArgs& r = c->rf;

@@ -8,10 +8,13 @@
 // function in IEEE floating-point arithmetic", ACM TOMS 16(4), 1990; "...of
 // the exponential function...", ACM TOMS 15(2), 1989) with 256-entry tables
 // (fx_tables.h, generated by gen_fx_tables.py), but evaluate the reduced
-// argument's series in Q62 integers: the logarithm uses no FP64 operation
-// (its parts are summed as a 128-bit fixed-point number and rounded to a
-// double with integer operations), the exponential one (the FMA that picks
-// n = round(y 256/ln 2); r = y - n ln2/256 is formed in 128-bit integers).
+// argument's series in fixed-point integers: the logarithm uses no FP64
+// operation (its table point is the one at or below the mantissa, so its
+// series runs on unsigned high multiplies; its parts are summed as a 128-bit
+// fixed-point number and rounded to a double with integer operations), the
+// exponential one (the FMA that picks n = round(y 256/ln 2); r = y - n ln2/256
+// is formed from the low 64 bits of its two terms and made non-negative, so
+// its series also runs on unsigned high multiplies).
 //
 // Accuracy (tested against 60-digit references): fx_exp within 1 ulp;
 // fx_log within 1 ulp plus 2^-58 absolute (the series is absolute-accurate,
@@ -28,89 +31,138 @@
 namespace mc {
 namespace fx {
 
-// floor(a * b / 2^62) for signed Q62 operands, |a| < 2^61: one high multiply.
-__device__ __forceinline__ int64_t mul_q62(int64_t a, int64_t b) { return __mul64hi(a * 4, b); }
-
-constexpr int64_t kQ62One = (int64_t)1 << 62;
-
-// Rounds the signed Q64 number v (value v / 2^64, |v| >= 1) to the nearest
-// double (ties away from zero) using integer operations only.
-__device__ __forceinline__ double q64_to_double(__int128 v)
+// Rounds (-1)^neg (hi 2^64 + lo) / 2^64, a nonzero magnitude below 2^74, to
+// the nearest double (ties away from zero) with 64-bit integer operations.
+__device__ __forceinline__ double q64_to_double(uint64_t hi, uint64_t lo, bool neg)
 {
-    const bool neg = v < 0;
-    unsigned __int128 a = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
-    const uint64_t hw = (uint64_t)(a >> 64);
-    const int p = hw ? 127 - __clzll((long long)hw) : 63 - __clzll((long long)(uint64_t)a);  // leading bit
+    const int p = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);  // leading bit
     uint64_t m;
     int e = p - 64 + 1023;
     if (p > 52) {
-        const int sh = p - 52;
-        m = (uint64_t)((a + ((unsigned __int128)1 << (sh - 1))) >> sh);
+        const int sh = p - 52;  // 1..21
+        m = (hi << (64 - sh)) | (lo >> sh);
+        m += (lo >> (sh - 1)) & 1ull;
         if (m >> 53) {  // rounding carried into a new leading bit
             m >>= 1;
             ++e;
         }
     } else {
-        m = (uint64_t)a << (52 - p);
+        m = lo << (52 - p);
     }
-    const uint64_t bits = ((uint64_t)neg << 63) | ((uint64_t)e << 52) | (m & 0xFFFFFFFFFFFFFull);
+    const uint64_t bits = ((uint64_t)neg << 63) | (((uint64_t)e << 52) + m - (1ull << 52));
     return __longlong_as_double((long long)bits);
 }
 
+// The rare cases go to CUDA's functions through calls, so that their code is
+// not inlined into every use (the sampling loop inlines the fast paths once
+// per axis; inlined slow paths multiply its size and its instruction-fetch
+// stalls).
+static __device__ __noinline__ double log_slow(double x) { return log(x); }
+static __device__ __noinline__ double exp_slow(double y) { return exp(y); }
+
+// Constants of the series: round(2^32 / k), round(2^62 / k) and round(2^63 / k).
+__host__ __device__ constexpr uint32_t q32_inv(uint32_t k) { return (uint32_t)((((uint64_t)1 << 32) + k / 2) / k); }
+__host__ __device__ constexpr uint64_t q62_inv(uint64_t k) { return (((uint64_t)1 << 62) + k / 2) / k; }
+__host__ __device__ constexpr uint64_t q63_inv(uint64_t k) { return (((uint64_t)1 << 63) + k / 2) / k; }
+
+// ln x = e ln 2 + ln c_j + ln(1 + r) for x = 2^e m, c_j = 1 + j/256 the table
+// point at or below m and r = (m - c_j)/c_j in [0, 2^-8): every quantity is
+// non-negative, so the series runs on unsigned high multiplies.
 __device__ __forceinline__ double fx_log(double x)
 {
     const uint64_t u = (uint64_t)__double_as_longlong(x);
-    if (u - 0x0010000000000000ull >= 0x7FE0000000000000ull) return log(x);  // not a positive normal number
+    if (u - 0x0010000000000000ull >= 0x7FE0000000000000ull) return log_slow(x);  // not a positive normal number
     const int e = (int)(u >> 52) - 1023;
     const uint64_t f = u & 0xFFFFFFFFFFFFFull;
-    const int j = (int)(f >> 44);  // nearest table point c_j = 1 + (j + 1/2)/256
-    // m - c_j in Q52 (|.| <= 2^43), then r = (m - c_j) / c_j in Q62 (|r| <= 2^-9)
-    const int64_t D = (int64_t)f - ((int64_t)(2 * j + 1) << 43);
-    const int64_t r = __mul64hi((int64_t)((uint64_t)D << 11), (int64_t)__ldg(&kLogInvC[j]));
-    // ln(1 + r) = r - r^2/2 + r^3/3 - r^4/4 + r^5/5 - r^6/6 (+ |r|^7/7 < 2^-65)
-    int64_t s = -kQ62One / 6;
-    s = kQ62One / 5 + mul_q62(r, s);
-    s = -kQ62One / 4 + mul_q62(r, s);
-    s = kQ62One / 3 + mul_q62(r, s);
-    s = -kQ62One / 2 + mul_q62(r, s);
-    s = kQ62One + mul_q62(r, s);
-    const int64_t l1 = mul_q62(r, s);
-    // ln x = e ln2 + ln c_j + ln(1 + r), summed as a Q64 fixed-point number
-    const __int128 v = (__int128)e * (__int128)kLn2W1 + (((__int128)e * (__int128)kLn2W2) >> 64) +
-                       (__int128)__ldg(&kLogCQ64[j]) + ((__int128)l1 << 2);
-    if (v == 0) return 0.0;
-    return q64_to_double(v);
+    const int j = (int)(f >> 44);
+    // m - c_j is the mantissa's low 44 bits (Q52); r = (m - c_j)/c_j in Q64 (< 2^56)
+    const uint64_t r = __umul64hi((f & 0xFFFFFFFFFFFull) << 13, __ldg(&kLogInvC[j]));
+    // ln(1 + r) = r (1 - r (1/2 - r (1/3 - r (1/4 - r (1/5 - r (1/6 - r/7)))))) (+ r^8/8 < 2^-67),
+    // every bracket positive.  The three innermost reach the result multiplied by
+    // r^4 < 2^-32, so they run in Q32 with 32-bit high multiplies; the rest in Q63.
+    const uint32_t r32 = (uint32_t)(r >> 32);
+    uint32_t t = q32_inv(7);
+    t = q32_inv(6) - __umulhi(r32, t);
+    t = q32_inv(5) - __umulhi(r32, t);
+    t = q32_inv(4) - __umulhi(r32, t);
+    uint64_t s = q63_inv(3) - __umul64hi(r, (uint64_t)t << 31);
+    s = q63_inv(2) - __umul64hi(r, s);
+    s = q63_inv(1) - __umul64hi(r, s);
+    const uint64_t l1 = __umul64hi(r, s);                  // ln(1 + r), Q63
+    const uint64_t U = __ldg(&kLogCQ64[j]) + (l1 << 1);    // ln m, Q64 (< ln 2)
+    // e ln 2 + ln m as sign and 128-bit magnitude in Q64
+    const uint64_t ae = (uint64_t)(e < 0 ? -e : e);
+    const uint64_t plo = ae * kLn2Q64, phi = __umul64hi(ae, kLn2Q64);
+    uint64_t lo, hi;
+    bool neg = false;
+    if (e >= 0) {
+        lo = plo + U;
+        hi = phi + (lo < U ? 1ull : 0ull);
+    } else {
+        lo = plo - U;
+        hi = phi - (plo < U ? 1ull : 0ull);
+        neg = true;
+        if ((int64_t)hi < 0) {  // ln m > |e| ln 2 by rounding (x just below 1): a tiny positive value
+            lo = 0ull - lo;
+            hi = ~hi + (lo == 0 ? 1ull : 0ull);
+            neg = false;
+        }
+    }
+    if ((hi | lo) == 0) return 0.0;
+    return q64_to_double(hi, lo, neg);
 }
 
-__device__ __forceinline__ double fx_exp(double y)
+// exp of the double with bits u
+__device__ __forceinline__ double fx_exp_bits(uint64_t u)
 {
-    const uint64_t u = (uint64_t)__double_as_longlong(y);
+    const double y = __longlong_as_double((long long)u);
     const uint64_t ay = u & 0x7FFFFFFFFFFFFFFFull;
-    if (ay >= 0x4086200000000000ull) return exp(y);  // |y| >= 708 (or NaN): CUDA's exp
-    if (ay < 0x3C30000000000000ull) return 1.0 + y;  // |y| < 2^-60: exp(y) rounds from 1 + y
+    if (ay >= 0x4086200000000000ull) {  // |y| >= 708, infinite or NaN
+        // y < -745.2 (down to -inf): exp(y) < 2^-1075 rounds to +0.  Integrands
+        // with narrow peaks land here often, so it takes no FP64 work; the
+        // rest (overflow, subnormal results, NaN) is CUDA's exp.
+        if ((u >> 63) && ay > 0x408749999999999Aull && ay <= 0x7FF0000000000000ull) return 0.0;
+        return exp_slow(y);
+    }
+    if (ay < 0x3C30000000000000ull) return 1.0;  // |y| < 2^-60: exp(y) rounds to 1
     // y = n ln2/256 + r, n = round(y 256/ln2) by the 1.5 * 2^52 shift (one FMA)
     const double t = fma(y, k256OverLn2, 0x1.8p52);
-    const int64_t n = __double_as_longlong(t) - __double_as_longlong(0x1.8p52);
-    // r = y - n ln2/256 in Q62 with integers: y exactly (bits below 2^-62
-    // dropped; |y| < 2^10 fits 72 bits) minus n ln2/256 from a Q115 constant
+    int64_t n = __double_as_longlong(t) - __double_as_longlong(0x1.8p52);
+    // r = y - n ln2/256 in Q62 (|r| <= ln2/512 + tiny: |rq| < 2^54), so only the
+    // low 64 bits of y in Q62 and of n ln2/256 matter: y's bits below 2^-62 are
+    // dropped; n ln2/256 = (n C + 2^52) >> 53 with C = ln2/256 in Q115 =
+    // Hi 2^64 + Lo, of which bits 53..116 are kept
     const int sh = (int)((u >> 52) & 0x7FF) - 1013;  // y = M 2^(E-1075): Q62 needs a shift by E - 1013
     const uint64_t M = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    __int128 Y = sh >= 0 ? ((__int128)M << sh) : (__int128)(M >> -sh);
-    if (u >> 63) Y = -Y;
-    const __int128 C = ((__int128)kLn2Over256Q115Hi << 64) | (__int128)kLn2Over256Q115Lo;
-    const __int128 L = ((__int128)n * C + ((__int128)1 << 52)) >> 53;
-    const int64_t rq = (int64_t)(Y - L);  // |r| <= ln2/512 + tiny: |rq| < 2^54
-    // e^r = 1 + r + r^2/2 + r^3/6 + r^4/24 + r^5/120 (+ |r|^6/720 < 2^-66)
-    int64_t s = kQ62One / 120;
-    s = kQ62One / 24 + mul_q62(rq, s);
-    s = kQ62One / 6 + mul_q62(rq, s);
-    s = kQ62One / 2 + mul_q62(rq, s);
-    s = kQ62One + mul_q62(rq, s);
-    s = kQ62One + mul_q62(rq, s);
-    // 2^(j/256) e^r in Q62, within [0.9986, 2)
+    uint64_t Y = sh >= 0 ? M << sh : (sh > -64 ? M >> -sh : 0ull);
+    if (u >> 63) Y = 0ull - Y;
+    const uint64_t nu = (uint64_t)n;
+    const uint64_t plo = nu * kLn2Over256Q115Lo;
+    uint64_t phi = __umul64hi(nu, kLn2Over256Q115Lo) - (n < 0 ? kLn2Over256Q115Lo : 0ull);  // n Lo, signed
+    const uint64_t plo2 = plo + (1ull << 52);
+    phi += plo2 < plo ? 1ull : 0ull;
+    const uint64_t L = ((phi + nu * kLn2Over256Q115Hi) << 11) | (plo2 >> 53);
+    int64_t rq = (int64_t)(Y - L);
+    if (rq < 0) {  // r in [0, ln2/256): n one lower
+        --n;
+        rq += (int64_t)kLn2Over256Q62;
+    }
+    // e^r = 1 + r (1 + r (1/2 + r (1/6 + r (1/24 + r (1/120 + r/720))))) (+ r^7/5040 < 2^-72),
+    // every bracket positive.  The two innermost reach the result multiplied by
+    // r^4 < 2^-34, so they run in Q32 with 32-bit high multiplies; the rest in Q62.
+    const uint32_t r32 = (uint32_t)((uint64_t)rq >> 30);
+    uint32_t a = q32_inv(720);
+    a = q32_inv(120) + __umulhi(r32, a);
+    a = q32_inv(24) + __umulhi(r32, a);
+    const uint64_t rr = (uint64_t)rq << 2;  // r in Q64
+    uint64_t s = q62_inv(6) + __umul64hi(rr, (uint64_t)a << 30);
+    s = q62_inv(2) + __umul64hi(rr, s);
+    s = q62_inv(1) + __umul64hi(rr, s);
+    s = q62_inv(1) + __umul64hi(rr, s);
+    // 2^(j/256) e^r in Q62, within [1, 2)
     const int j = (int)(n & 255);
     const int k = (int)(n >> 8);
-    const uint64_t P = __umul64hi(__ldg(&kExp2[j]) << 1, (uint64_t)s << 1);
+    const uint64_t P = __umul64hi(__ldg(&kExp2[j]) << 1, s << 1);
     // assemble 2^k P / 2^62 (rounded to nearest, ties away), a normal double for |y| < 708
     uint64_t bits;
     if (P >= ((uint64_t)1 << 62))
@@ -118,6 +170,14 @@ __device__ __forceinline__ double fx_exp(double y)
     else
         bits = ((uint64_t)(k + 1022) << 52) + (((P + (1ull << 8)) >> 9) - (1ull << 52));
     return __longlong_as_double((long long)bits);
+}
+
+__device__ __forceinline__ double fx_exp(double y) { return fx_exp_bits((uint64_t)__double_as_longlong(y)); }
+
+// exp(-v), the sign flipped on the bits (no FP64 negation)
+__device__ __forceinline__ double fx_exp_neg(double v)
+{
+    return fx_exp_bits((uint64_t)__double_as_longlong(v) ^ 0x8000000000000000ull);
 }
 
 // Single-precision cosine for the mixed-precision kernels: x = k pi/2 + r

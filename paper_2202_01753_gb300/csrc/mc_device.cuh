@@ -97,6 +97,8 @@ struct BatchView {
     uint32_t hist_d;  // axes with a histogram (d)
     double jac0;
     float phi_scale_f;
+    double inv_p, inv_var_den;     // 1/p, 1/(p (p-1))
+    float inv_p_f, inv_var_den_f;
     const FamParams& fam;
 };
 
@@ -250,13 +252,14 @@ __device__ __forceinline__ float bin_phi_f32(const BinPos& b, float scale)
 //   PRODPEAK c[j] = c_j^-2, c[12+j] = w_j
 //   C0       c[j] = c_j, c[12+j] = w_j
 //   DISCONT  c[j] = c_j, c[12+j] = w_j
-//   COSMO6   c[0..5] = a, c[6] = mu, c[7] = 1/(2 s^2), c[8] = r, c[9] = 1/(2 t^2),
+//   COSMO6   c[0..5] = a (c[2], c[3] = a_3 + 1, a_4 + 1), c[6] = mu, c[7] = 1/(2 s^2), c[8] = r, c[9] = 1/(2 t^2),
 //            c[10] = 1/(2 pi s^2)
 // ---------------------------------------------------------------------------
 template <typename R> struct RealOps;
 template <> struct RealOps<double> {
     // fixed-point table-driven versions: a few FP64 operations instead of tens
     __device__ static double exp_(double v) { return fx::fx_exp(v); }
+    __device__ static double expm_(double v) { return fx::fx_exp_neg(v); }   // exp(-v)
     __device__ static double log_(double v) { return fx::fx_log(v); }
     __device__ static double cos_(double v) { return cos(v); }
     __device__ static double rcp(double v) { return 1.0 / v; }
@@ -264,6 +267,7 @@ template <> struct RealOps<double> {
 };
 template <> struct RealOps<float> {
     __device__ static float exp_(float v) { return expf(v); }
+    __device__ static float expm_(float v) { return expf(-v); }
     __device__ static float log_(float v) { return logf(v); }
     __device__ static float cos_(float v) { return fx::fx_cosf(v); }
     __device__ static float rcp(float v) { return 1.0f / v; }
@@ -289,7 +293,7 @@ template <typename R> struct Family<MCUBES_F_GAUSS, R> {
     }
     __device__ static R end(const S& s, uint32_t, const FamParams& f)
     {
-        return RealOps<R>::par(f, 0) * RealOps<R>::exp_(-s.q);
+        return RealOps<R>::par(f, 0) * RealOps<R>::expm_(s.q);
     }
 };
 
@@ -340,7 +344,7 @@ template <typename R> struct Family<MCUBES_F_C0, R> {
         const R z = x - RealOps<R>::par(f, 12 + j);
         s.t += RealOps<R>::par(f, j) * (z < R(0) ? -z : z);
     }
-    __device__ static R end(const S& s, uint32_t, const FamParams&) { return RealOps<R>::exp_(-s.t); }
+    __device__ static R end(const S& s, uint32_t, const FamParams&) { return RealOps<R>::expm_(s.t); }
 };
 
 template <typename R> struct Family<MCUBES_F_DISCONT, R> {
@@ -359,23 +363,26 @@ template <typename R> struct Family<MCUBES_F_DISCONT, R> {
 
 template <typename R> struct Family<MCUBES_F_COSMO6, R> {
     // f = c10 exp(-sum a_i L_i - L_3 - L_4 - (L_3-mu)^2 h - (L_4-mu)^2 h - (x_1+x_2-r)^2 ht)
-    // with L_i = ln x_i (the 1/(x_3 x_4) of the lognormals folded into the exponent)
+    // with L_i = ln x_i (the 1/(x_3 x_4) of the lognormals folded into the
+    // exponent, c2 = a_3 + 1 and c3 = a_4 + 1).  The add of axis j is unrolled
+    // with j known, so each axis takes only its own terms.
     struct S { R e; R x12; };
     __device__ static void begin(S& s) { s.e = R(0); s.x12 = R(0); }
     __device__ static void add(S& s, int j, R x, const FamParams& f)
     {
         const R L = RealOps<R>::log_(x);
-        s.e += RealOps<R>::par(f, j) * L;
+        s.e = j == 0 ? RealOps<R>::par(f, 0) * L : s.e + RealOps<R>::par(f, j) * L;
         if (j == 2 || j == 3) {
             const R z = L - RealOps<R>::par(f, 6);
-            s.e += L + z * z * RealOps<R>::par(f, 7);
+            s.e += z * z * RealOps<R>::par(f, 7);
         }
-        if (j < 2) s.x12 += x;
+        if (j == 0) s.x12 = x;
+        if (j == 1) s.x12 += x;
     }
     __device__ static R end(const S& s, uint32_t, const FamParams& f)
     {
         const R z = s.x12 - RealOps<R>::par(f, 8);
-        return RealOps<R>::par(f, 10) * RealOps<R>::exp_(-(s.e + z * z * RealOps<R>::par(f, 9)));
+        return RealOps<R>::par(f, 10) * RealOps<R>::expm_(s.e + z * z * RealOps<R>::par(f, 9));
     }
 };
 
@@ -386,37 +393,43 @@ template <typename R> struct Family<MCUBES_F_COSMO6, R> {
 // knots, so a point on a knot gives the same value from either cell.
 template <typename R> struct TabOps;
 template <> struct TabOps<double> {
-    // Cell and fraction with two FP64 operations for u and one for t: the
-    // floor of u (0 <= u < 2^31) is taken by clearing the fraction bits of
-    // its encoding, the clamps are integer tests on those bits, so no FP64
-    // conversion or compare is issued (GB300 runs 2 FP64 instructions per
-    // clock per SM).
-    __device__ static void cell(double x, double lo, double s, int n, int* i, double* t)
+    // Cell and fraction with one FP64 operation: u = x s - lo s by one FMA;
+    // the floor of u (0 <= u < 2^31) and the fraction t = u - floor(u) are
+    // taken from the bits of u's encoding (t normalised into a double with
+    // integer operations), and the clamps are integer tests on those bits, so
+    // no FP64 subtraction, conversion or compare is issued (GB300 runs 2 FP64
+    // instructions per clock per SM against 64 integer ones).
+    __device__ static void cell(double x, double s, double los, int n, int* i, double* t)
     {
-        const double u = (x - lo) * s;
+        const double u = fma(x, s, -los);
         int64_t b = __double_as_longlong(u);
         if (b < 0) b = 0;                         // below the range (or -0): u = 0
         const int e = (int)((uint64_t)b >> 52) - 1023;
-        int k = 0;
-        int64_t kb = 0;                           // encoding of (double)k
-        if (e >= 0) {
-            const int sh = 52 - e;                // u < 2^31: sh > 21
-            k = (int)((((uint64_t)b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> sh);
-            kb = b & (int64_t)(~0ull << sh);
+        if (e < 0) {                              // u < 1: cell 0, t = u
+            *i = 0;
+            *t = __longlong_as_double(b);
+            return;
         }
+        const int sh = 52 - e;
+        const uint64_t M = ((uint64_t)b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+        const int k = e < 31 ? (int)(M >> sh) : n;  // u >= 2^31 > n - 1 (also inf, NaN)
         if (k > n - 2) {                          // floor(u) >= n - 1: at or above the last knot
             *i = n - 2;
             *t = 1.0;
             return;
         }
         *i = k;
-        *t = __longlong_as_double(b) - __longlong_as_double(kb);  // exact
+        // t = F 2^-sh for the fraction bits F < 2^sh: exact, normalised here
+        const uint64_t F = M & ((1ull << sh) - 1ull);
+        const int q = 63 - __clzll((long long)F);  // leading bit of F (q < sh <= 52)
+        const uint64_t tb = ((uint64_t)(q - sh + 1022) << 52) + (F << (52 - q));
+        *t = F ? __longlong_as_double((long long)tb) : 0.0;
     }
     __device__ static double interp1(const TableDesc& T, double x)
     {
         int i;
         double t;
-        cell(x, T.lo0, T.s0, T.n0, &i, &t);
+        cell(x, T.s0, T.los0, T.n0, &i, &t);
         const double v0 = __ldg(T.v + i), v1 = __ldg(T.v + i + 1);
         return fma(t, v1 - v0, v0);
     }
@@ -424,8 +437,8 @@ template <> struct TabOps<double> {
     {
         int i, k;
         double t, s;
-        cell(x, T.lo0, T.s0, T.n0, &i, &t);
-        cell(y, T.lo1, T.s1, T.n1, &k, &s);
+        cell(x, T.s0, T.los0, T.n0, &i, &t);
+        cell(y, T.s1, T.los1, T.n1, &k, &s);
         const double* r0 = T.v + (size_t)i * T.n1 + k;
         const double* r1 = r0 + T.n1;
         const double v00 = __ldg(r0), v01 = __ldg(r0 + 1), v10 = __ldg(r1), v11 = __ldg(r1 + 1);

@@ -46,6 +46,7 @@ struct TableDesc {
     const float* vf;
     int ndim, n0, n1, pad;
     double lo0, hi0, s0, lo1, hi1, s1;   // s = (n - 1) / (hi - lo)
+    double los0, los1;                    // lo * s (rounded): u = (x - lo) s as fma(x, s, -lo s)
     float lo0f, hi0f, s0f, lo1f, hi1f, s1f;
 };
 
@@ -88,6 +89,8 @@ struct VsArgs {
     double jac0;              // (g nb)^d: FP64 cells hold width / g, so J = jac0 prod(cell widths)
     float phi_scale_f;        // 1 / (g nb): mixed cells hold nb width, so x = left + (nb width)(g phi)/(g nb)
     float nb_f;
+    double inv_p, inv_var_den;     // 1/p and 1/(p (p-1)) of the cube moments (Alg. 3 UpdateVariance)
+    float inv_p_f, inv_var_den_f;  // the same in single precision (mixed)
     FamParams fam;
 };
 
@@ -103,7 +106,9 @@ struct BatchDesc {
     int family, ita, itmax, mixed;
     uint64_t m;
     double jac0;                // (g nb)^d
+    double inv_p, inv_var_den;  // 1/p and 1/(p (p-1)) of the cube moments
     float phi_scale_f;          // 1 / (g nb)
+    float inv_p_f, inv_var_den_f;
     float pad2;
     double lo[kDMax];
     double scale[kDMax];
@@ -204,6 +209,19 @@ uint64_t cube_permutation(uint64_t n);
 // is already high enough.
 cudaError_t raise_smem_limit(const void* kernel, size_t smem);
 double jacobian_scale(long long g, long long nb, int d);  // (g nb)^d
+struct MomentScales {
+    double inv_p, inv_var_den;
+    float inv_p_f, inv_var_den_f;
+};
+MomentScales moment_scales(long long p);  // 1/p, 1/(p (p-1)), p >= 2
+template <class T> void set_moment_scales(T& a, long long p)
+{
+    const MomentScales m = moment_scales(p);
+    a.inv_p = m.inv_p;
+    a.inv_var_den = m.inv_var_den;
+    a.inv_p_f = m.inv_p_f;
+    a.inv_var_den_f = m.inv_var_den_f;
+}
 
 cudaError_t launch_refine(const RefineArgs& a, cudaStream_t s);
 cudaError_t launch_reduce_range(const double* part, double* hist_acc, int nblocks, int d, int nb, int adjust,

@@ -136,6 +136,7 @@ extern "C" mcubes_status mcubes_sample_range_noalloc(
         a.jac0 = jacobian_scale(g, nbins, d);
         a.phi_scale_f = (float)(1.0 / ((double)g * nbins));
         a.nb_f = (float)nbins;
+        set_moment_scales(a, p);
         a.fam = fp;
 
         // the grid's low parts must read as zero and the histogram accumulator

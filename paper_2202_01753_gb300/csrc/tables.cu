@@ -87,10 +87,12 @@ extern "C" mcubes_status mcubes_tables_set(mcubes_ctx* c, int n, const mcubes_ta
         d.lo0 = t.lo[0];
         d.hi0 = t.hi[0];
         d.s0 = (double)(t.n[0] - 1) / (t.hi[0] - t.lo[0]);
+        d.los0 = d.lo0 * d.s0;
         if (t.ndim == 2) {
             d.lo1 = t.lo[1];
             d.hi1 = t.hi[1];
             d.s1 = (double)(t.n[1] - 1) / (t.hi[1] - t.lo[1]);
+            d.los1 = d.lo1 * d.s1;
         }
         d.lo0f = (float)d.lo0;
         d.hi0f = (float)d.hi0;

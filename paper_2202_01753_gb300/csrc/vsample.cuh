@@ -34,6 +34,29 @@ __device__ __forceinline__ void hist_add(uint32_t base, uint32_t idx, double v)
     asm volatile("red.shared.add.f64 [%0], %1;" ::"r"(base + 8u * idx), "d"(v));
 }
 
+// Adds F2 to the sample's bin on each of the first hist_d axes; idx holds the
+// flat bin indices two per word (axis 2k in the low half of idx[k]).  In
+// double precision, where a shared-memory add is a compare-and-swap loop that
+// repeats while lanes of the warp collide on one bin, odd lanes take the two
+// axes of each word in the opposite order: at every step the warp adds to two
+// different axes' histograms and half as many lanes compete for the same
+// bins.  The single-precision add is a native reduction; there the swap
+// measured slower and is not made.
+template <int NB4, class HT>
+__device__ __forceinline__ void hist_add_sample(uint32_t hist_s, const uint32_t (&idx)[2 * NB4], uint32_t hist_d,
+                                                HT F2)
+{
+    const uint32_t odd = sizeof(HT) == 8 ? (threadIdx.x & 1u) : 0u;
+#pragma unroll
+    for (int k = 0; k < 2 * NB4; ++k) {
+        if (2 * k < (int)hist_d) {
+            const uint32_t w = __funnelshift_l(idx[k], idx[k], odd << 4);  // halves swapped on odd lanes
+            if (((2u * k) ^ odd) < hist_d) hist_add(hist_s, w & 0xFFFFu, F2);
+            if (((2u * k + 1u) ^ odd) < hist_d) hist_add(hist_s, w >> 16, F2);
+        }
+    }
+}
+
 template <bool MIXED> struct Prec;
 template <> struct Prec<false> {
     using R = double;
@@ -151,7 +174,9 @@ struct CubeSums {
 // of the range (gcd(perm_k, ncubes) = 1) that gives the lanes of a warp
 // cubes with unrelated digits on every axis, so that their samples spread
 // over all bins instead of crowding the same few (fewer shared-memory atomic
-// conflicts and bank conflicts).
+// conflicts and bank conflicts).  Besides what sample_point reads, A provides
+// inv_p = 1/p and inv_var_den = 1/(p (p-1)) (inv_p_f, inv_var_den_f in single
+// precision).
 template <int FAM, bool MIXED, bool ADJ, int NB4, class A>
 __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIXED>::Cell* cells,
                                              typename Prec<MIXED>::H* hist, uint64_t cube_lo, uint64_t ncubes,
@@ -167,8 +192,16 @@ __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIX
     const uint32_t L = lanes;
     const uint32_t seg_lane = threadIdx.x & (L - 1u);
     const uint32_t cubes_per_group = blockDim.x / L;
-    const R inv_p = R(1) / R(p);
-    const R inv_var_den = inv_p / R(p - 1);   // 1 / (p (p-1))
+    // 1/p and 1/(p (p-1)), rounded once on the host: a division here would be
+    // recomputed inside the cube loop when registers run short
+    R inv_p, inv_var_den;
+    if constexpr (MIXED) {
+        inv_p = a.inv_p_f;
+        inv_var_den = a.inv_var_den_f;
+    } else {
+        inv_p = a.inv_p;
+        inv_var_den = a.inv_var_den;
+    }
     const uint64_t first = group0 * cubes_per_group + threadIdx.x / L;
     uint64_t off = ncubes ? (first % ncubes) * perm_k % ncubes : 0;               // physical offset of `first`
     const uint64_t step = ncubes ? (gstride * cubes_per_group % ncubes) * perm_k % ncubes : 0;
@@ -210,10 +243,7 @@ __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIX
                 }
                 ++n;
                 if constexpr (ADJ) {
-                    const HT F2 = (HT)(F * F);
-#pragma unroll
-                    for (int j = 0; j < DN; ++j)
-                        if (j < (int)hist_d) hist_add(hist_s, (idx[j >> 1] >> (16 * (j & 1))) & 0xFFFFu, F2);
+                    hist_add_sample<NB4>(hist_s, idx, hist_d, (HT)(F * F));
                 }
             }
         }
@@ -233,25 +263,22 @@ __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIX
                 }
             }
         } else {
-            // merge (count, mean, M2) across the cube's lanes (Chan et al.)
-            double cnt = (double)n;
-            double mean = n ? (double)K + (double)S1 / cnt : 0.0;
-            double M2 = n ? (double)S2 - (double)S1 * (double)S1 / cnt : 0.0;
+            // the cube's lanes re-base their sums on the shift of its first lane
+            // (S1 += n dK, S2 += dK (2 S1 + n dK), dK = K_l - K_0; a lane without
+            // samples adds nothing) and add them with XOR shuffles: no division
+            const double K0 = __shfl_sync(0xffffffffu, (double)K, (int)((threadIdx.x & 31u) & ~(L - 1u)));
+            const double dK = (double)K - K0, cnt = (double)n;
+            double s1 = (double)S1, s2 = (double)S2;
+            s2 = fma(dK, fma(cnt, dK, 2.0 * s1), s2);
+            s1 = fma(cnt, dK, s1);
             for (uint32_t off = 1; off < L; off <<= 1) {
-                const double cnt_o = __shfl_xor_sync(0xffffffffu, cnt, off);
-                const double mean_o = __shfl_xor_sync(0xffffffffu, mean, off);
-                const double M2_o = __shfl_xor_sync(0xffffffffu, M2, off);
-                const double tot = cnt + cnt_o;
-                if (tot > 0.0) {
-                    const double delta = mean_o - mean;
-                    mean += delta * (cnt_o / tot);
-                    M2 += M2_o + delta * delta * (cnt * cnt_o / tot);
-                }
-                cnt = tot;
+                s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+                s2 += __shfl_xor_sync(0xffffffffu, s2, off);
             }
             if (valid && seg_lane == 0) {
+                const double mean = K0 + s1 * a.inv_p;
                 acc.I += mean;
-                acc.V += M2 / (cnt * (cnt - 1.0));
+                acc.V += (s2 - s1 * s1 * a.inv_p) * a.inv_var_den;
                 acc.A += fabs(mean);
             }
         }
@@ -310,10 +337,7 @@ __device__ __forceinline__ void sample_cube_slice(const A& a, const typename Pre
         }
         ++n;
         if constexpr (ADJ) {
-            const HT F2 = (HT)(F * F);
-#pragma unroll
-            for (int j = 0; j < DN; ++j)
-                if (j < (int)hist_d) hist_add(hist_s, (idx[j >> 1] >> (16 * (j & 1))) & 0xFFFFu, F2);
+            hist_add_sample<NB4>(hist_s, idx, hist_d, (HT)(F * F));
         }
     }
     // re-base on thread 0's shift (every thread has a sample: q >= blockDim;
@@ -384,7 +408,8 @@ __device__ __forceinline__ void block_write_sums(const CubeSums& acc, double (*r
 // registers, 24 warps) — measured against two: osc10 mixed +10% despite 132
 // bytes of spills, cosmo6 FP64 +4% and gauss3 FP64 +9% with none — except
 // for the table integrands in FP64, whose spills and larger table footprint
-// in L1/L2 cost a third (two blocks).
+// in L1/L2 cost a third (two blocks; table6 at three: 16.6 ms per 1e8 calls
+// against 10.0 ms).
 template <int FAM, bool MIXED, int NB4>
 constexpr int vsample_min_blocks() { return (FAM == MCUBES_F_TABLE && !MIXED) ? 2 : 3; }
 

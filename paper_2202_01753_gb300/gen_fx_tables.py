@@ -6,10 +6,13 @@ the logarithm function in IEEE floating-point arithmetic", ACM TOMS 16(4),
 1990, and "Table-driven implementation of the exponential function in IEEE
 floating-point arithmetic", ACM TOMS 15(2), 1989:
 
-* log: c_j = 1 + (j + 1/2)/256 for j = 0..255; 1/c_j as an unsigned Q63
-  integer and ln(c_j) as an unsigned Q64 fraction; ln 2 to 128 bits.
+* log: c_j = 1 + j/256 for j = 0..255 (the left end of each mantissa
+  interval, so that the reduced argument is never negative); 1/c_j as an
+  unsigned Q63 integer and ln(c_j) as an unsigned Q64 fraction; ln 2 as a
+  Q64 integer.
 * exp: 2^(j/256) for j = 0..255 as unsigned Q62 integers; ln 2 / 256 as a
-  128-bit Q115 integer for the fixed-point argument reduction.
+  128-bit Q115 integer for the fixed-point argument reduction and as a Q62
+  integer for the step that makes the reduced argument non-negative.
 * single-precision cosine: pi/2 as the sum of three floats (each the float
   nearest to what remains of pi/2) for a Cody-Waite reduction (Cody and
   Waite, "Software Manual for the Elementary Functions", 1980), and 2/pi.
@@ -42,7 +45,7 @@ def tables():
     mpmath.mp.dps = 60
     inv_c, log_q64, exp2 = [], [], []
     for j in range(256):
-        c = 1 + (mpmath.mpf(j) + mpmath.mpf("0.5")) / 256
+        c = 1 + mpmath.mpf(j) / 256
         inv_c.append(int(mpmath.nint(2 ** 63 / c)))
         log_q64.append(int(mpmath.nint(2 ** 64 * mpmath.log(c))))
         exp2.append(int(mpmath.nint(2 ** 62 * mpmath.power(2, mpmath.mpf(j) / 256))))
@@ -53,9 +56,7 @@ def tables():
 def render():
     inv_c, log_q64, exp2, ln2 = tables()
     mpmath.mp.dps = 60
-    # ln 2 as a 128-bit binary fraction (two 64-bit words)
-    ln2_q128 = int(mpmath.floor(ln2 * 2 ** 128))
-    ln2_w1, ln2_w2 = ln2_q128 >> 64, ln2_q128 & (2 ** 64 - 1)
+    ln2_q64 = int(mpmath.nint(ln2 * 2 ** 64))
     c = ln2 / 256
     hp = mpmath.pi / 2
     c_q115 = int(mpmath.nint(c * mpmath.mpf(2) ** 115))
@@ -69,22 +70,22 @@ def render():
         "namespace mc {",
         "namespace fx {",
         "",
-        f"constexpr uint64_t kLn2W1 = 0x{ln2_w1:016x}ull;  // ln 2 = (W1 + W2 2^-64) 2^-64",
-        f"constexpr uint64_t kLn2W2 = 0x{ln2_w2:016x}ull;",
+        f"constexpr uint64_t kLn2Q64 = 0x{ln2_q64:016x}ull;  // ln 2 as Q64",
         f"constexpr double k256OverLn2 = {float(256 / ln2)!r};",
         f"constexpr uint64_t kLn2Over256Q115Hi = 0x{c_q115 >> 64:016x}ull;  // ln2/256 = (Hi 2^64 + Lo) 2^-115",
         f"constexpr uint64_t kLn2Over256Q115Lo = 0x{c_q115 & (2 ** 64 - 1):016x}ull;",
+        f"constexpr uint64_t kLn2Over256Q62 = 0x{int(mpmath.nint(c * mpmath.mpf(2) ** 62)):016x}ull;  // ln2/256 as Q62",
         f"constexpr float kHalfPiF1 = {_f32(hp)!r}f;  // pi/2 = F1 + F2 + F3 (+ ~1e-23)",
         f"constexpr float kHalfPiF2 = {_f32(hp - _f32(hp))!r}f;",
         f"constexpr float kHalfPiF3 = {_f32(hp - _f32(hp) - _f32(hp - _f32(hp)))!r}f;",
         f"constexpr float kTwoOverPiF = {_f32(2 / mpmath.pi)!r}f;",
         "",
-        "// 1 / c_j, c_j = 1 + (j + 1/2)/256, as Q63",
+        "// 1 / c_j, c_j = 1 + j/256, as Q63 (j = 0: exactly 2^63)",
         "__device__ const uint64_t kLogInvC[256] = {",
     ]
     for i in range(0, 256, 4):
         lines.append("    " + ", ".join(f"0x{v:016x}ull" for v in inv_c[i:i + 4]) + ",")
-    lines += ["};", "", "// ln c_j as Q64 (a binary fraction; 0 < ln c_j < ln 2)",
+    lines += ["};", "", "// ln c_j as Q64 (a binary fraction; 0 <= ln c_j < ln 2)",
               "__device__ const uint64_t kLogCQ64[256] = {"]
     for i in range(0, 256, 4):
         lines.append("    " + ", ".join(f"0x{v:016x}ull" for v in log_q64[i:i + 4]) + ",")

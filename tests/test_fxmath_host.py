@@ -1,0 +1,76 @@
+"""The kernels' fixed-point log and exp (csrc/fx_math.cuh), compiled for the
+host with stand-ins for the device intrinsics (tests/fxmath_host.cpp), against
+40-digit references: log within 1 ulp plus 2^-58 absolute, exp within 2^-52
+relative, and the special values.  The GPU tests check the same functions on
+the device against these bounds and against CUDA's log and exp."""
+import math
+import os
+import shutil
+import subprocess
+
+import mpmath
+import numpy as np
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_2202_01753_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def fxhost(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if not cxx:
+        pytest.skip("no C++ compiler")
+    exe = str(tmp_path_factory.mktemp("fx") / "fxmath_host")
+    subprocess.run([cxx, "-O2", "-std=c++17", "-I", CSRC, "-o", exe, os.path.join(HERE, "fxmath_host.cpp")],
+                   check=True)
+
+    def run(xs):
+        out = subprocess.run([exe], input="\n".join(float(x).hex() for x in xs), capture_output=True,
+                             text=True, check=True).stdout.split()
+        return (np.array([float.fromhex(v) for v in out[0::2]]),
+                np.array([float.fromhex(v) for v in out[1::2]]))
+    return run
+
+
+def _bits(x):
+    return int(np.float64(x).view(np.uint64))
+
+
+def _dbl(b):
+    return float(np.uint64(b).view(np.float64))
+
+
+def test_log_accuracy_host(fxhost):
+    rng = np.random.default_rng(21)
+    xs = np.concatenate([np.exp(rng.uniform(-700, 700, 4000)), rng.uniform(0.01, 5.0, 4000),
+                         1.0 + rng.uniform(-1e-3, 1e-3, 1000)])
+    # the ends of every table interval, values next to 1, the extremes of the range
+    edges = [_dbl((1023 << 52) | (j << 44) | d) for j in range(256) for d in (0, 1, (1 << 44) - 1)]
+    near1 = [_dbl(_bits(1.0) - k) for k in range(1, 40)] + [_dbl(_bits(1.0) + k) for k in range(0, 40)]
+    ends = [_dbl(((1023 + e) << 52) | (255 << 44) | ((1 << 44) - 1)) for e in range(-1022, 1024, 7)]
+    xs = np.concatenate([xs, edges, near1, ends, [2.2250738585072014e-308, 1.7976931348623157e308]])
+    got, _ = fxhost(xs)
+    mpmath.mp.dps = 40
+    for x, g in zip(xs, got):
+        ref = mpmath.log(mpmath.mpf(float(x)))
+        tol = math.ulp(float(ref)) * 1.01 + 2.0 ** -58
+        assert abs(mpmath.mpf(float(g)) - ref) <= tol, (x, g, float(ref))
+    assert got[list(xs).index(1.0)] == 0.0
+
+
+def test_exp_accuracy_host(fxhost):
+    rng = np.random.default_rng(22)
+    ys = np.concatenate([rng.uniform(-708.9, 707.9, 4000), rng.uniform(-3, 3, 4000),
+                         rng.uniform(-1e-6, 1e-6, 500), [0.0, 1.0, -1.0, -700.0, 700.0]])
+    # arguments at and next to multiples of ln2/256, where the reduction picks n
+    steps = np.array([n * math.log(2) / 256 for n in range(-2000, 2000, 7)])
+    ys = np.concatenate([ys, steps, np.nextafter(steps, np.inf), np.nextafter(steps, -np.inf)])
+    _, got = fxhost(ys)      # fx_exp(-y)
+    mpmath.mp.dps = 40
+    for y, g in zip(ys, got):
+        ref = mpmath.exp(-mpmath.mpf(float(y)))
+        assert abs(mpmath.mpf(float(g)) - ref) / ref <= 2.0 ** -52, (y, g, float(ref))
+    # exp(y) for y < -745.2 (to -inf) is +0 exactly
+    _, z = fxhost([745.3, 800.0, 1e5, 1e300, math.inf])
+    assert np.all(z == 0.0) and not np.any(np.signbit(z))

@@ -59,9 +59,12 @@ def test_exp_accuracy(torch_cuda):
         ref = mpmath.exp(mpmath.mpf(float(y)))
         assert abs(mpmath.mpf(float(g)) - ref) / ref <= 2.0 ** -52, (y, g, float(ref))
     assert np.all(np.abs(got - cuda) <= 2 * np.spacing(np.abs(cuda)))
-    special = np.array([-800.0, 800.0, -np.inf, np.inf, np.nan, -708.5, 709.5])
+    special = np.array([-800.0, 800.0, -np.inf, np.inf, np.nan, -708.5, 709.5, -745.1, -745.14, -745.2,
+                        np.nextafter(-745.2, -np.inf), -746.0, -1e5, -1e300, -np.finfo(np.float64).max])
     g, c = _eval(torch_cuda, 1, special), _eval(torch_cuda, 3, special)
     assert np.array_equal(np.isnan(g), np.isnan(c)) and np.all((g == c) | np.isnan(g))
+    # below -745.2 the result is +0 exactly (exp(y) < 2^-1075), as libm gives
+    assert np.all(g[special < -745.2] == 0.0) and not np.any(np.signbit(g[special < -745.2]))
 
 
 def test_cosf_accuracy(torch_cuda):

@@ -36,54 +36,82 @@ static __device__ __forceinline__ double block_sum(double v, double* scratch)
     return out;
 }
 
-static __device__ __forceinline__ DD dd_shfl_up(DD v, int off)
+// ---------------------------------------------------------------------------
+// Exact cumulative weights of the rebinning: each bin weight w in [0, 1] as an
+// unsigned Q100 integer (128 bits; bits below 2^-100 dropped), their prefix
+// sums exact (at most nb 2^100 < 2^110), so the order of the additions does
+// not matter and the quantile tests are exact integer comparisons.
+// ---------------------------------------------------------------------------
+using u128 = unsigned __int128;
+
+static __device__ __forceinline__ u128 q100_of(double w)  // 0 <= w < 2^27
 {
-    return DD{__shfl_up_sync(0xffffffffu, v.hi, off), __shfl_up_sync(0xffffffffu, v.lo, off)};
+    const uint64_t b = (uint64_t)__double_as_longlong(w);
+    const int E = (int)(b >> 52);
+    if (E == 0) return 0;                             // zero (or below 2^-1022)
+    const uint64_t M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = E - 975;                           // w = (M << (E - 975)) 2^-100
+    if (sh >= 0) return (u128)M << sh;                // sh < 75: below 2^128
+    return sh > -53 ? (u128)(M >> -sh) : (u128)0;
 }
 
-// Inclusive double-double prefix sum of w[0..n) into (chi, clo), fixed
-// order: each thread adds kPerThread consecutive values, the thread totals
-// are scanned by warp shuffles and then across warps.
-static __device__ void dd_inclusive_scan(const double* w, double* chi, double* clo, int n, DD* wtot)
+// v rounded to the nearest double: one correctly rounded 64-bit conversion of
+// the top word (a sticky bit stands for the rest) and an exact power-of-two
+// scale.
+static __device__ __forceinline__ double u128_to_double(u128 v)
+{
+    const uint64_t hi = (uint64_t)(v >> 64), lo = (uint64_t)v;
+    if (hi == 0) return (double)lo;
+    const int lz = __clzll((long long)hi);
+    const u128 n = v << lz;
+    const uint64_t top = (uint64_t)(n >> 64) | ((uint64_t)n != 0 ? 1ull : 0ull);
+    const double scale = __longlong_as_double((long long)((uint64_t)(1023 + 64 - lz) << 52));  // 2^(64 - lz)
+    return (double)top * scale;
+}
+
+static __device__ __forceinline__ u128 shfl_up_u128(u128 v, int off)
+{
+    const unsigned long long lo = __shfl_up_sync(0xffffffffu, (unsigned long long)v, off);
+    const unsigned long long hi = __shfl_up_sync(0xffffffffu, (unsigned long long)(v >> 64), off);
+    return ((u128)hi << 64) | (u128)lo;
+}
+
+// Inclusive prefix sum of the values w[0..n) (Q100) into c[0..n); thread t
+// holds w[t kPerThread + i] in v[i] (zero beyond n).  The thread totals are
+// scanned by warp shuffles and then across warps.  Exact, so any order gives
+// the same sums.
+static __device__ void u128_inclusive_scan(const u128 (&v)[kPerThread], u128* c, int n, u128* wtot)
 {
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int begin = t * kPerThread;
-    DD local{0.0, 0.0};
-    DD mine[kPerThread];
-    for (int i = 0; i < kPerThread; ++i) {
-        const int k = begin + i;
-        if (k < n) local = dd_add(local, DD{w[k], 0.0});
-        mine[i] = local;
-    }
-    DD incl = local;
+    u128 local = 0;
+#pragma unroll
+    for (int i = 0; i < kPerThread; ++i) local += v[i];
+    u128 incl = local;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-        const DD o = dd_shfl_up(incl, off);
-        if (lane >= off) incl = dd_add(o, incl);
+        const u128 o = shfl_up_u128(incl, off);
+        if (lane >= off) incl += o;
     }
     __syncthreads();
     if (lane == 31) wtot[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        DD v = lane < kWarps ? wtot[lane] : DD{0.0, 0.0};
+        u128 x = lane < kWarps ? wtot[lane] : (u128)0;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
-            const DD o = dd_shfl_up(v, off);
-            if (lane >= off) v = dd_add(o, v);
+            const u128 o = shfl_up_u128(x, off);
+            if (lane >= off) x += o;
         }
-        if (lane < kWarps) wtot[lane] = v;  // inclusive warp totals
+        if (lane < kWarps) wtot[lane] = x;  // inclusive warp totals
     }
     __syncthreads();
-    // exclusive prefix of this thread = (incl - local) within the warp + earlier warps
-    DD before = dd_add(incl, DD{-local.hi, -local.lo});
-    if (warp > 0) before = dd_add(wtot[warp - 1], before);
+    u128 run = incl - local + (warp > 0 ? wtot[warp - 1] : (u128)0);
+#pragma unroll
     for (int i = 0; i < kPerThread; ++i) {
         const int k = begin + i;
-        if (k < n) {
-            const DD c = dd_add(before, mine[i]);
-            chi[k] = c.hi;
-            clo[k] = c.lo;
-        }
+        run += v[i];
+        if (k < n) c[k] = run;
     }
     __syncthreads();
 }
@@ -204,9 +232,15 @@ static __device__ void finalize_iteration(const double* part, int nparts, double
 // smooth the bin sums with their neighbours, normalise, compress with
 // ((r - 1) / ln r)^alpha, then place the new right edges where the
 // cumulative compressed weight reaches i / nb of its total, the weight of an
-// old bin being spread evenly over it.  The cumulative weight and the
-// targets are double-double, so an edge is exact to about 2^-104 of the total
-// weight and the new bin widths keep full double precision.
+// old bin being spread evenly over it.  The smoothing keeps three times the
+// neighbour mean (the normalisation removes the factor, and no division is
+// issued per bin); the cumulative weight is exact in Q100 integers, so the
+// bin of target i is the first k with nb C_k >= i W (W the total) and the
+// fraction within it is (i W - nb C_{k-1}) / (nb w_k), both exact integers
+// rounded once to doubles; the edge left + width * fraction is formed in
+// double-double, so the new bin widths keep full double precision.  GB300
+// issues 2 FP64 instructions per clock per SM and one block runs an axis:
+// the integer form keeps the scan and the search off the FP64 pipe.
 // The axis's histogram is the sum of nparts partials, element k of partial t
 // at parts[t * stride + k] (float or double).  grid/grid_lo are this axis's
 // edges (updated in place), hist_out receives the summed histogram.  The new
@@ -217,11 +251,10 @@ static __device__ void rebin_axis(const void* parts, size_t stride, int nparts, 
                            int ncopy = 1)
 {
     __shared__ double sC[kNbMax];
-    __shared__ double sW[kNbMax];
     __shared__ double sB[kNbMax];
-    __shared__ double sLo[kNbMax];
     __shared__ double sBlo[kNbMax];
-    __shared__ DD wtot[kWarps];
+    __shared__ u128 sCum[kNbMax];   // inclusive cumulative compressed weights, Q100
+    __shared__ u128 wtot[kWarps];
     for (int k = threadIdx.x; k < nb; k += blockDim.x) {
         double acc = 0.0;
         if (is_float) {
@@ -237,19 +270,19 @@ static __device__ void rebin_axis(const void* parts, size_t stride, int nparts, 
         sBlo[k] = grid_lo[k];
     }
     __syncthreads();
+    // three times the smoothed value: C_{k-1} + C_k + C_{k+1}; the ends 1.5 (C_0 + C_1)
+    double sm3[kPerThread];
     double part = 0.0;
-    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
-        double sm;
-        if (k == 0) sm = (sC[0] + sC[1]) / 2.0;
-        else if (k == nb - 1) sm = (sC[nb - 2] + sC[nb - 1]) / 2.0;
-        else sm = (sC[k - 1] + sC[k] + sC[k + 1]) / 3.0;
-        sW[k] = sm;
-    }
-    __syncthreads();
-    // fixed-order total: contiguous chunks per thread, then the tree
     for (int i = 0; i < kPerThread; ++i) {
         const int k = threadIdx.x * kPerThread + i;
-        if (k < nb) part += sW[k];
+        double v = 0.0;
+        if (k < nb) {
+            if (k == 0) v = 1.5 * (sC[0] + sC[1]);
+            else if (k == nb - 1) v = 1.5 * (sC[nb - 2] + sC[nb - 1]);
+            else v = sC[k - 1] + sC[k] + sC[k + 1];
+        }
+        sm3[i] = v;
+        part += v;  // fixed order: contiguous chunks per thread, then the tree
     }
     const double total = block_sum(part, scratch);
     if (!isfinite(total)) {
@@ -264,22 +297,23 @@ static __device__ void rebin_axis(const void* parts, size_t stride, int nparts, 
     // work is a few instructions; CUDA's log and pow cost ~100 on a pipe
     // that issues 2 per clock per SM, and one block runs an axis)
     const double inv_total = 1.0 / total;
-    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
-        const double r = sW[k] * inv_total;
+    u128 wq[kPerThread];
+#pragma unroll
+    for (int i = 0; i < kPerThread; ++i) {
+        const int k = threadIdx.x * kPerThread + i;
+        const double r = sm3[i] * inv_total;
         double w;
-        if (r <= 0.0) w = 0.0;
-        else if (r == 1.0) w = 1.0;
+        if (k >= nb || r <= 0.0) w = 0.0;
+        else if (r >= 1.0) w = 1.0;
         else {
             const double q = (r - 1.0) / fx::fx_log(r);
             w = alpha == 1.5 ? q * sqrt(q) : fx::fx_exp(alpha * fx::fx_log(q));
         }
-        sW[k] = w;
+        wq[i] = q100_of(w);
     }
-    __syncthreads();
-    // sC, sLo = cumulative weight through bin k (double-double)
-    dd_inclusive_scan(sW, sC, sLo, nb, wtot);
-    const DD wsum{sC[nb - 1], sLo[nb - 1]};
-    if (!(wsum.hi > 0.0) || !isfinite(wsum.hi)) {
+    u128_inclusive_scan(wq, sCum, nb, wtot);
+    const u128 W = sCum[nb - 1];
+    if (W == 0) {
         if (threadIdx.x == 0) {
             *error = MCUBES_ENONFINITE;
             *done = 1;
@@ -289,20 +323,19 @@ static __device__ void rebin_axis(const void* parts, size_t stride, int nparts, 
     double* out = grid;
     double* out_lo = grid_lo;
     for (int i = 1 + threadIdx.x; i < nb; i += blockDim.x) {
-        const DD target = dd_div(dd_scale(wsum, (double)i), (double)nb);
+        const u128 T = (u128)(uint64_t)i * W;  // i W: the target times nb
         // first bin k whose cumulative weight through k reaches the target
         int lo = 0, hi = nb - 1;
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
-            if (dd_ge(DD{sC[mid], sLo[mid]}, target)) hi = mid; else lo = mid + 1;
+            if ((u128)(uint64_t)nb * sCum[mid] >= T) hi = mid; else lo = mid + 1;
         }
         const int k = lo;
-        const DD before = k > 0 ? DD{sC[k - 1], sLo[k - 1]} : DD{0.0, 0.0};
-        const DD rem = dd_add(target, DD{-before.hi, -before.lo});
+        const u128 before = k > 0 ? (u128)(uint64_t)nb * sCum[k - 1] : (u128)0;  // < T
+        const u128 wk = sCum[k] - (k > 0 ? sCum[k - 1] : (u128)0);
+        const double frac = u128_to_double(T - before) / u128_to_double((u128)(uint64_t)nb * wk);
         const DD left = k > 0 ? DD{sB[k - 1], sBlo[k - 1]} : DD{0.0, 0.0};
         const DD width = dd_add(DD{sB[k], sBlo[k]}, DD{-left.hi, -left.lo});
-        double frac = (rem.hi + rem.lo) / sW[k];
-        frac = fmin(fmax(frac, 0.0), 1.0);
         const DD e = dd_add(left, dd_scale(width, frac));
         for (int r = 0; r < ncopy; ++r) {
             out[(size_t)r * nb + i - 1] = e.hi;

@@ -117,34 +117,43 @@ static __device__ void u128_inclusive_scan(const u128 (&v)[kPerThread], u128* c,
 }
 
 // Weighted-Estimates (inverse-variance weights, chi^2 per degree of freedom)
-// and Check-Convergence over n recorded iterations; one thread.  Returns
-// whether the result has converged.
+// and Check-Convergence over n recorded iterations, by the whole block: each
+// thread takes iterations tid, tid + blockDim, ... and the sums are fixed-order
+// block sums, so the reciprocals of the variances are formed in parallel
+// (itmax may be thousands).  Every thread returns the same values.
 static __device__ bool weigh_and_check(const double* hI, const double* hV, int n, double rel_tol, double abs_tol,
-                                double* est, double* sigma, double* chi2_dof)
+                                       double* est, double* sigma, double* chi2_dof, double* scratch)
 {
-    int n_exact = 0;
-    double exact_sum = 0.0;
-    for (int i = 0; i < n; ++i)
-        if (hV[i] == 0.0) { ++n_exact; exact_sum += hI[i]; }
+    double n_exact = 0.0, exact_sum = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        if (hV[i] == 0.0) {
+            n_exact += 1.0;
+            exact_sum += hI[i];
+        }
+    n_exact = block_sum(n_exact, scratch);
+    exact_sum = block_sum(exact_sum, scratch);
     double I, sig, chi2 = 0.0;
-    if (n_exact > 0) {
+    if (n_exact > 0.0) {
         I = exact_sum / n_exact;
         sig = 0.0;
     } else {
         double sw = 0.0, swi = 0.0;
-        for (int i = 0; i < n; ++i) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
             const double w = 1.0 / hV[i];
             sw += w;
             swi += w * hI[i];
         }
+        sw = block_sum(sw, scratch);
+        swi = block_sum(swi, scratch);
         I = swi / sw;
         sig = sqrt(1.0 / sw);
         if (n > 1) {
-            for (int i = 0; i < n; ++i) {
+            double c = 0.0;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
                 const double z = hI[i] - I;
-                chi2 += z * z / hV[i];
+                c += z * z / hV[i];
             }
-            chi2 /= (double)(n - 1);
+            chi2 = block_sum(c, scratch) / (double)(n - 1);
         }
     }
     *est = I;
@@ -207,6 +216,7 @@ static __device__ void finalize_iteration(const double* part, int nparts, double
     }
     s0 = block_sum(s0, scratch);
     s1 = block_sum(s1, scratch);
+    __shared__ int finite;
     if (threadIdx.x == 0) {
         const double I = s0 / m;
         const double V = s1 / (m * m);
@@ -216,16 +226,28 @@ static __device__ void finalize_iteration(const double* part, int nparts, double
             r.hist_V[n] = V;
             *r.n = n + 1;
         }
-        if (!isfinite(I) || !isfinite(V)) {
+        finite = isfinite(I) && isfinite(V);
+        if (!finite) {
             *r.error = MCUBES_ENONFINITE;
             *r.done = 1;
-        } else if (weigh_and_check(r.hist_I, r.hist_V, *r.n, r.rel_tol, r.abs_tol, r.estimate, r.sigma,
-                                   r.chi2_dof)) {
-            *r.converged = 1;
-            *r.done = 1;
         }
-        *r.it += 1;
     }
+    __syncthreads();  // the record and the flag are visible to the block
+    if (finite) {
+        double est, sig, chi2;
+        const bool conv = weigh_and_check(r.hist_I, r.hist_V, *r.n, r.rel_tol, r.abs_tol, &est, &sig, &chi2,
+                                          scratch);
+        if (threadIdx.x == 0) {
+            *r.estimate = est;
+            *r.sigma = sig;
+            *r.chi2_dof = chi2;
+            if (conv) {
+                *r.converged = 1;
+                *r.done = 1;
+            }
+        }
+    }
+    if (threadIdx.x == 0) *r.it += 1;
 }
 
 // Adjust-Bin-Bounds of one axis (Lepage 1978, as the paper's Alg. 2 cites):

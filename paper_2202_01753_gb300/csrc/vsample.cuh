@@ -409,7 +409,8 @@ __device__ __forceinline__ void block_write_sums(const CubeSums& acc, double (*r
 // bytes of spills, cosmo6 FP64 +4% and gauss3 FP64 +9% with none — except
 // for the table integrands in FP64, whose spills and larger table footprint
 // in L1/L2 cost a third (two blocks; table6 at three: 16.6 ms per 1e8 calls
-// against 10.0 ms).
+// against 10.0 ms).  Four blocks (64 registers) for the mixed kernels up to
+// d = 8 measured slower too (corner8: 23.3 ms per 1e9 calls against 21.3).
 template <int FAM, bool MIXED, int NB4>
 constexpr int vsample_min_blocks() { return (FAM == MCUBES_F_TABLE && !MIXED) ? 2 : 3; }
 

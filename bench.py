@@ -95,6 +95,7 @@ def parse():
     ap.add_argument("--sweep-precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the Poisson stream")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-iters", type=int, default=4, help="iterations per server step")
     ap.add_argument("--batch-n", type=int, default=4096)
     ap.add_argument("--batch-rel-tol", type=float, default=1e-4, help="relative tolerance of every batched integral")
     ap.add_argument("--seq-sample", type=int, default=96, help="integrals timed one by one in plain FP64")
@@ -535,6 +536,7 @@ def serve_arm(args):
                  seed=w.seed) for w in ws]
     ctx = mcubes.Context(local, precision="mixed")
     srv = mcubes.Server(ctx, itcap=max(w.itmax for w in ws))
+    srv.set_step_iterations(args.serve_iters)
     srv.run_stream(reqs[:200], arrival[:200] - arrival[0])         # warm-up: autotune, graph capture
     clocks = ClockSampler(local)
     clocks.start()
@@ -565,7 +567,8 @@ def serve_arm(args):
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": "serving", "requests": len(ws), "offered_per_s": args.serve_rate,
                    "seconds": args.serve_seconds, "ncall": ws[0].ncall, "itmax": ws[0].itmax,
-                   "rel_tol": "log-uniform [1e-5, 1e-3]", "d": "3..12", "precision": "mixed"},
+                   "rel_tol": "log-uniform [1e-5, 1e-3]", "d": "3..12", "precision": "mixed",
+                   "iterations_per_step": args.serve_iters},
         "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99)),
                        "max": 1e3 * float(lat.max())},
         "saturated_integrals_per_s": len(ws) / wall_sat,

@@ -226,10 +226,21 @@ mcubes_status mcubes_server_destroy(mcubes_server* srv);
  * EINVAL if the request is invalid (nothing is queued). */
 mcubes_status mcubes_server_submit(mcubes_server* srv, const mcubes_request* req, long long tag);
 
-/* Admits queued requests into free slots, runs one iteration of every
- * resident request and retires the finished ones; blocks until the
- * iteration is done.  *ran receives the number of requests iterated. */
+/* Admits queued requests into free slots, runs one iteration (or the number
+ * set by mcubes_server_set_step_iterations) of every resident request and
+ * retires the finished ones; blocks until the iterations are done.  *ran
+ * receives the number of requests iterated. */
 mcubes_status mcubes_server_step(mcubes_server* srv, int* ran);
+
+/* Iterations each step runs before it reads back which requests finished
+ * (1..MCUBES_STEP_ITERS_MAX, default 1).  More iterations per step spread
+ * the step's fixed host work (admission, partition upload, read-back) over
+ * more iterations; a request that converges or reaches its itmax inside a
+ * step is skipped by the kernels for the rest of it (its result is the same),
+ * and new requests are admitted only between steps.  EINVAL outside the
+ * range. */
+#define MCUBES_STEP_ITERS_MAX 64
+mcubes_status mcubes_server_set_step_iterations(mcubes_server* srv, int iters);
 
 /* Copies up to cap finished results (and their tags) not yet returned;
  * *n receives how many were copied. */

@@ -111,6 +111,17 @@ __device__ void refine_one(const BatchRefineArgs& a, uint32_t j, double* scratch
     const int nrebin = adjust ? d : 0;
     if ((int)blockIdx.x > nrebin) return;
     BatchState* st = a.st + slot;
+    // finished in an earlier iteration of this step (its sampling was skipped).
+    // The finalising block of this launch may set these while a rebinning
+    // block reads them: that block then skips a rebin no iteration will use.
+    // One thread reads, so that the whole block takes the same branch.
+    __shared__ int skip;
+    if (threadIdx.x == 0)
+        skip = *(volatile const int*)&st->done || (int)*(volatile const uint32_t*)&st->it >= D.itmax;
+    __syncthreads();
+    const bool finished = skip != 0;
+    __syncthreads();  // skip is rewritten for the next integral
+    if (finished) return;
     if ((int)blockIdx.x == nrebin) {
         const IterRecord r{&st->it, &st->done, &st->error, &st->n, &st->converged, &st->estimate, &st->sigma,
                            &st->chi2_dof, D.hist_I, D.hist_V, D.itmax, D.rel_tol, D.abs_tol};
@@ -466,7 +477,7 @@ BatchArgs BatchEngine::sample_args(int cls) const
     BatchArgs a;
     a.desc = (const BatchDesc*)desc_.ptr;
     a.st = (const BatchState*)st_.ptr;
-    a.segs = (const BatchSeg*)segs_.ptr;
+    a.segs = (BatchSeg*)segs_.ptr;
     a.blk_seg = (const uint32_t*)blk_seg_.ptr + (size_t)cls * (bmax_ + 1);
     a.seg_part = (double*)seg_part_.ptr;
     a.seg_hist = seg_hist_.ptr;
@@ -600,7 +611,7 @@ cudaError_t BatchEngine::autotune(const std::vector<int>& live, unsigned mask)
     return cudaStreamSynchronize(stream_);
 }
 
-cudaError_t BatchEngine::step(int* ran)
+cudaError_t BatchEngine::step(int* ran, int iters)
 {
     *ran = 0;
     cudaError_t e = flush_admissions();
@@ -614,10 +625,13 @@ cudaError_t BatchEngine::step(int* ran)
     int nseg = 0;
     partition(live, &nseg);
     if ((e = upload_partition(live, nseg))) return e;
-    if (exec_) e = cudaGraphLaunch(exec_, stream_);
-    else e = enqueue_iteration(mask);
-    if (e) return e;
-    for (int s : live) slots_[s].it += 1;
+    // iters iterations on one partition: an integral that converges or reaches
+    // itmax on the way is skipped by the kernels from its next iteration on
+    for (int k = 0; k < std::max(iters, 1); ++k) {
+        if (exec_) e = cudaGraphLaunch(exec_, stream_);
+        else e = enqueue_iteration(mask);
+        if (e) return e;
+    }
     *ran = (int)live.size();
     // the pinned partition staging is rewritten by the next step: wait here,
     // then read back which integrals have finished
@@ -633,6 +647,7 @@ cudaError_t BatchEngine::refresh()
         Slot& S = slots_[s];
         if (!S.used || S.finished) continue;
         const BatchState& B = h_states_[s];
+        S.it = (int)B.it;  // iterations run (the device's count: a step may run several)
         if (B.done || S.it >= hdesc_[s].itmax) {
             S.finished = true;
             mcubes_result& R = S.result;

@@ -39,25 +39,33 @@ vsample_batch_kernel(const __grid_constant__ BatchArgs a)
             for (uint32_t i = threadIdx.x; i < sizeof(BatchDesc) / 4; i += blockDim.x) dst[i] = src[i];
         }
         __syncthreads();
+        // an integral that finished in an earlier iteration of this step (a
+        // step may run several) is skipped; only the refinement changes the state
+        const BatchState& B = a.st[seg.slot];
+        if (B.done || (int)B.it >= sd.itmax) continue;
+        // this iteration adjusts while it < ita (a step's iterations may cross
+        // ita); the refinement reads the flag back
+        const bool adjust = seg.adjust && (int)B.it < sd.ita;
+        if (threadIdx.x == 0) a.segs[si].adjust = adjust ? 1u : 0u;
         const uint32_t d = sd.d, nb = sd.nb;
         Cell* cells = reinterpret_cast<Cell*>(smem);
         HT* hist = reinterpret_cast<HT*>(smem + cell_bytes(MIXED) * d * nb);
-        if (seg.adjust) stage_cells<MIXED, true>(cells, hist, sd.cells, d, nb, d);
+        if (adjust) stage_cells<MIXED, true>(cells, hist, sd.cells, d, nb, d);
         else stage_cells<MIXED, false>(cells, hist, sd.cells, d, nb, d);
         __syncthreads();
 
         const BatchView v{d,        nb,           sd.g,     sd.gmagic,         sd.key0,          sd.key1, d,
                           sd.jac0,  sd.phi_scale_f, sd.inv_p, sd.inv_var_den, sd.inv_p_f, sd.inv_var_den_f, sd.fam};
-        const uint32_t it = a.st[seg.slot].it;
+        const uint32_t it = B.it;
         CubeSums acc;
-        if (seg.adjust)
+        if (adjust)
             sample_cubes<FAM, MIXED, true, NB4>(v, cells, hist, seg.c0, seg.c1 - seg.c0, seg.perm_k, 0, 1, it,
                                                 sd.lanes, sd.p, acc);
         else
             sample_cubes<FAM, MIXED, false, NB4>(v, cells, hist, seg.c0, seg.c1 - seg.c0, seg.perm_k, 0, 1, it,
                                                  sd.lanes, sd.p, acc);
         block_write_sums(acc, red, a.seg_part + 3 * (size_t)si);
-        if (seg.adjust) {
+        if (adjust) {
             __syncthreads();
             HT* out = reinterpret_cast<HT*>(a.seg_hist) + seg.hist_off;
             for (uint32_t i = threadIdx.x; i < d * nb; i += blockDim.x) out[i] = hist[i];

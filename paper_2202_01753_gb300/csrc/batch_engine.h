@@ -60,9 +60,11 @@ public:
     // and its share of the per-iteration partials), for itcap iterations.
     static size_t slot_bytes(const mcubes_opts& opts, int itcap);
 
-    // One iteration of every resident, unfinished integral (graph replay),
-    // then a read-back of which ones have finished.  *ran = integrals iterated.
-    cudaError_t step(int* ran);
+    // iters iterations (graph replays) of every resident, unfinished integral
+    // on one partition, then a read-back of which ones have finished (one
+    // that finishes on the way is skipped by the kernels from then on).
+    // *ran = integrals that were live at the start of the step.
+    cudaError_t step(int* ran, int iters = 1);
 
     // Results of integrals that finished since the last call (tag, result);
     // with free_slots their slots become free for new admissions.
@@ -75,7 +77,7 @@ private:
     struct Slot {
         bool used = false, finished = false, reported = false;
         long long tag = 0;
-        int it = 0;           // iterations enqueued
+        int it = 0;           // iterations run (read back from the device after each step)
         double work = 0.0;    // samples per iteration
         long long g = 0, m = 0, p = 0;
         mcubes_result result{};

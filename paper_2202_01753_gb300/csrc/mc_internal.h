@@ -132,7 +132,8 @@ struct BatchState {
 // A run of cubes [c0, c1) of one integral, sampled by one block.
 struct BatchSeg {
     uint32_t slot;
-    uint32_t adjust;
+    uint32_t adjust;            // host: adjusting at the step's first iteration (the histogram space is
+                                // reserved); device: whether this iteration adjusts
     uint64_t c0, c1;
     uint64_t perm_k;            // cube order within the segment (see sample_cubes)
     uint64_t hist_off;          // element offset of the segment's partial histogram
@@ -141,7 +142,7 @@ struct BatchSeg {
 struct BatchArgs {
     const BatchDesc* desc;
     const BatchState* st;
-    const BatchSeg* segs;
+    BatchSeg* segs;             // the sampling launch sets each segment's adjust for this iteration
     const uint32_t* blk_seg;    // block b samples segments [blk_seg[b], blk_seg[b+1]) (this class's table)
     double* seg_part;           // [segment][3] partial sums
     void* seg_hist;             // partial histograms (float in mixed, double in fp64)

@@ -41,6 +41,7 @@ struct mcubes_server {
     std::vector<std::pair<long long, mcubes_result>> finished;  // not yet polled
     long long completed = 0;
     long long slot_bytes = 0;
+    int iters_per_step = 1;
 };
 
 static mcubes_status cuda_status(cudaError_t e)
@@ -108,7 +109,7 @@ static mcubes_status server_step(mcubes_server* s, int* ran)
         s->queue.pop_front();
     }
     int n = 0;
-    const cudaError_t e = E.step(&n);
+    const cudaError_t e = E.step(&n, s->iters_per_step);
     if (e != cudaSuccess) return cuda_status(e);
     const size_t before = s->finished.size();
     E.finished(&s->finished, true);
@@ -122,6 +123,13 @@ mcubes_status mcubes_server_step(mcubes_server* s, int* ran)
     if (!s) return MCUBES_EINVAL;
     if (cudaSetDevice(s->ctx->device) != cudaSuccess) return MCUBES_ECUDA;
     return server_step(s, ran);
+}
+
+mcubes_status mcubes_server_set_step_iterations(mcubes_server* s, int iters)
+{
+    if (!s || iters < 1 || iters > MCUBES_STEP_ITERS_MAX) return MCUBES_EINVAL;
+    s->iters_per_step = iters;
+    return MCUBES_OK;
 }
 
 mcubes_status mcubes_server_poll(mcubes_server* s, long long* tags, mcubes_result* results, int cap, int* n)

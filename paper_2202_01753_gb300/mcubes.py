@@ -28,7 +28,7 @@ EXPORTED = [
     "mcubes_sample_range_noalloc", "mcubes_server_create", "mcubes_server_destroy", "mcubes_server_submit",
     "mcubes_server_step", "mcubes_server_poll", "mcubes_server_stats", "mcubes_server_run_stream",
     "mcubes_selftest_fxmath", "mcubes_state_size", "mcubes_state_export", "mcubes_state_import",
-    "mcubes_problem_get", "mcubes_get_opts", "mcubes_tables_set",
+    "mcubes_problem_get", "mcubes_get_opts", "mcubes_tables_set", "mcubes_server_set_step_iterations",
 ]
 
 
@@ -112,6 +112,7 @@ def lib():
                 "mcubes_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
                 "mcubes_server_submit": (ctypes.c_int, [ctypes.c_void_p, P(mcubes_request), ll]),
                 "mcubes_server_step": (ctypes.c_int, [ctypes.c_void_p, P(ctypes.c_int)]),
+                "mcubes_server_set_step_iterations": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
                 "mcubes_server_poll": (ctypes.c_int, [ctypes.c_void_p, P(ll), P(mcubes_result), ctypes.c_int,
                                                       P(ctypes.c_int)]),
                 "mcubes_server_stats": (ctypes.c_int, [ctypes.c_void_p, P(ll), P(ll), P(ll), P(ll), P(ll)]),
@@ -396,6 +397,11 @@ class Server:
     def submit(self, request, tag):
         arr, keep = _requests([request])
         self.ctx._check(lib().mcubes_server_submit(self._h, arr, int(tag)), "mcubes_server_submit")
+
+    def set_step_iterations(self, iters: int):
+        """Iterations each step runs before reading back which requests finished."""
+        self.ctx._check(lib().mcubes_server_set_step_iterations(self._h, int(iters)),
+                        "mcubes_server_set_step_iterations")
 
     def step(self):
         ran = ctypes.c_int()

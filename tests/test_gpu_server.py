@@ -77,6 +77,43 @@ def test_requests_admitted_mid_flight_match_solo(gpu_ctx_factory, precision):
         _check(w, results[i], _solo(gpu_ctx_factory, w, precision), precision)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_several_iterations_per_step_match_solo(gpu_ctx_factory, precision):
+    """Three iterations per step: requests converge or reach itmax inside a
+    step (the kernels skip them from then on) and cross the adjusting limit
+    ita = 3 inside a step (the sampling launch decides each iteration's
+    adjusting); every result must still equal the request run alone."""
+    ws = _reqs(24, seed=25)
+    for w in ws[::3]:
+        w.rel_tol = 0.0                       # these run to itmax
+    ctx = gpu_ctx_factory(precision=precision, ita=3)
+    srv = mcubes.Server(ctx, itcap=16)
+    srv.set_step_iterations(3)
+    for i, w in enumerate(ws[:12]):
+        srv.submit(_dict(w), i)
+    results = {}
+    steps = 0
+    while len(results) < len(ws):
+        if steps == 1:
+            for i, w in enumerate(ws[12:], start=12):
+                srv.submit(_dict(w), i)
+        srv.step()
+        steps += 1
+        results.update(dict(srv.poll()))
+        assert steps < 100
+    srv.close()
+    ctx.close()
+    assert steps <= 8                         # about a third of the one-iteration steps
+    for i, w in enumerate(ws):
+        solo_ctx = gpu_ctx_factory(seed=w.seed, precision=precision, ita=3)
+        solo = solo_ctx.integrate(w.fid, w.params, w.lo, w.hi, w.ncall, w.itmax, w.rel_tol, w.abs_tol)
+        solo_ctx.close()
+        _check(w, results[i], solo, precision)
+    with pytest.raises(mcubes.McubesError):
+        bad = mcubes.Server(gpu_ctx_factory(), itcap=4)
+        bad.set_step_iterations(0)
+
+
 def test_memory_budget_queues_requests(gpu_ctx_factory):
     ws = _reqs(12, seed=22, rel=False)
     ctx = gpu_ctx_factory(precision="mixed")

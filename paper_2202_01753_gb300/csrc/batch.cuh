@@ -55,7 +55,8 @@ vsample_batch_kernel(const __grid_constant__ BatchArgs a)
         __syncthreads();
 
         const BatchView v{d,        nb,           sd.g,     sd.gmagic,         sd.key0,          sd.key1, d,
-                          sd.jac0,  sd.phi_scale_f, sd.inv_p, sd.inv_var_den, sd.inv_p_f, sd.inv_var_den_f, sd.fam};
+                          sd.jac0,  sd.phi_scale_f, sd.inv_p, sd.inv_var_den, sd.inv_p_f, sd.inv_var_den_f, 0u,
+                          sd.fam};
         const uint32_t it = B.it;
         CubeSums acc;
         if (adjust)

@@ -581,6 +581,7 @@ mcubes_status mcubes_setup(mcubes_ctx* c, int id, const double* params, int npar
     a.phi_scale_f = (float)(1.0 / ((double)g * nb));
     a.nb_f = (float)nb;
     set_moment_scales(a, p);
+    a.want_abs = 0;  // an iteration uses the sums of the cube means and variances only
     a.fam = fp;
 
     RefineArgs& r = c->rf;
@@ -770,6 +771,7 @@ mcubes_status mcubes_sample_range(mcubes_ctx* c, unsigned it, int adjust, long l
     a.st = nullptr;
     a.it_fixed = it;
     a.split = 1;  // the range pass always uses the cube-stride layout (its partials are sums)
+    a.want_abs = 1;  // the pass reports the sum of |cube mean|
     a.cube_begin = (uint64_t)cube_begin;
     a.cube_end = (uint64_t)cube_end;
     a.perm_k = cube_permutation((uint64_t)(cube_end - cube_begin));

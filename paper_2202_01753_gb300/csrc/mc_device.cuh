@@ -99,6 +99,7 @@ struct BatchView {
     float phi_scale_f;
     double inv_p, inv_var_den;     // 1/p, 1/(p (p-1))
     float inv_p_f, inv_var_den_f;
+    uint32_t want_abs;             // 0: a batch iteration does not use the sums of |cube mean|
     const FamParams& fam;
 };
 

@@ -91,6 +91,7 @@ struct VsArgs {
     float nb_f;
     double inv_p, inv_var_den;     // 1/p and 1/(p (p-1)) of the cube moments (Alg. 3 UpdateVariance)
     float inv_p_f, inv_var_den_f;  // the same in single precision (mixed)
+    uint32_t want_abs;             // part[2] (sums of |cube mean|) wanted: the sampling-pass calls
     FamParams fam;
 };
 

@@ -137,6 +137,7 @@ extern "C" mcubes_status mcubes_sample_range_noalloc(
         a.phi_scale_f = (float)(1.0 / ((double)g * nbins));
         a.nb_f = (float)nbins;
         set_moment_scales(a, p);
+        a.want_abs = 1;  // the pass reports the sum of |cube mean|
         a.fam = fp;
 
         // the grid's low parts must read as zero and the histogram accumulator

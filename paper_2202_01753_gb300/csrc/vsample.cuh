@@ -176,7 +176,8 @@ struct CubeSums {
 // over all bins instead of crowding the same few (fewer shared-memory atomic
 // conflicts and bank conflicts).  Besides what sample_point reads, A provides
 // inv_p = 1/p and inv_var_den = 1/(p (p-1)) (inv_p_f, inv_var_den_f in single
-// precision).
+// precision) and want_abs (whether the sums of |cube mean| are needed: they
+// are reported by the sampling-pass calls, not used by an iteration).
 template <int FAM, bool MIXED, bool ADJ, int NB4, class A>
 __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIXED>::Cell* cells,
                                              typename Prec<MIXED>::H* hist, uint64_t cube_lo, uint64_t ncubes,
@@ -236,6 +237,9 @@ __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIX
                 const R F = sample_point<FAM, MIXED, NB4>(a, cells, c, s, it, nbc, idx);
                 if (n == 0) {
                     K = F;  // the shift: its own term is zero
+                } else if (n == 1) {
+                    S1 = F - K;
+                    S2 = S1 * S1;
                 } else {
                     const R z = F - K;
                     S1 += z;
@@ -249,17 +253,25 @@ __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIX
         }
         if (L == 1u) {
             if (valid) {
-                // UpdateVariance (Alg. 3): cube mean and the variance of that mean
-                const R mean = K + S1 * inv_p;
-                const R var = (S2 - S1 * S1 * inv_p) * inv_var_den;
+                // UpdateVariance (Alg. 3): cube mean and the variance of that
+                // mean; at p = 2 (every 1e8-call geometry) S1 = z, S2 = z^2 and
+                // the variance (z^2 - z^2/2)/2 is exactly z^2/4
+                R mean, var;
+                if (p == 2u) {
+                    mean = K + S1 * R(0.5);
+                    var = S2 * R(0.25);
+                } else {
+                    mean = K + S1 * inv_p;
+                    var = (S2 - S1 * S1 * inv_p) * inv_var_den;
+                }
                 if constexpr (MIXED) {
                     acc.fI.add(mean);
                     acc.fV.add(var);
-                    acc.fA.add(fabsf(mean));
+                    if (a.want_abs) acc.fA.add(fabsf(mean));
                 } else {
                     acc.I += mean;
                     acc.V += var;
-                    acc.A += fabs(mean);
+                    if (a.want_abs) acc.A += fabs(mean);
                 }
             }
         } else {

@@ -15,8 +15,7 @@ namespace mc {
 // TwoSum (Knuth) and an FMA-based exact product (Dekker).  Grid edges are held
 // in this form so that a narrow bin's width (a difference of two nearly equal
 // edges, and a factor of the Jacobian) keeps full relative precision; the
-// rebinning's cumulative weights use it so that the quantile edges do not
-// depend on the order in which a scan adds the weights.
+// rebinning forms each new edge (left + width * fraction) in it.
 // ---------------------------------------------------------------------------
 struct DD {
     double hi, lo;
@@ -47,15 +46,6 @@ __device__ __forceinline__ DD dd_scale(DD a, double b)
     const double e = __fma_rn(a.hi, b, -p);
     return dd_renorm(p, __fma_rn(a.lo, b, e));
 }
-
-__device__ __forceinline__ DD dd_div(DD a, double b)
-{
-    const double q1 = __ddiv_rn(a.hi, b);
-    const DD r = dd_add(a, dd_scale(DD{-q1, 0.0}, b));
-    return dd_renorm(q1, __ddiv_rn(__dadd_rn(r.hi, r.lo), b));
-}
-
-__device__ __forceinline__ bool dd_ge(DD a, DD b) { return a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo); }
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy

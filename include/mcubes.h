@@ -406,6 +406,19 @@ mcubes_status mcubes_sample_range_noalloc(int device, int integrand_id, const do
 mcubes_status mcubes_selftest_fxmath(int which, long long n, const double* d_in, double* d_out,
                                      void* cuda_stream);
 
+/* Adjust-Bin-Bounds of one axis (Alg. 2; Lepage 1978) exactly as an
+ * iteration's refinement runs it: d_C (device, nb doubles) is the axis's
+ * histogram of F^2 sums, d_B / d_Blo (device, nb doubles each) its right
+ * edges in the unit interval as double-double numbers (B[nb-1] = 1), updated
+ * in place; alpha is the compression exponent.  An all-zero histogram leaves
+ * the edges unchanged.  Runs on cuda_stream (NULL = legacy default stream)
+ * and waits for it.  The paper has no counterpart; this exists to test the
+ * device rebinning against the oracle on chosen histograms.
+ * Errors: EINVAL (nb outside 2..MCUBES_NBMAX, alpha <= 0, a NULL pointer),
+ * ENONFINITE (a non-finite histogram), ECUDA. */
+mcubes_status mcubes_selftest_rebin(int nb, double alpha, double* d_C, double* d_B, double* d_Blo,
+                                    void* cuda_stream);
+
 /* Geometry of the current setup: sub-cubes per axis, sub-cubes, samples per
  * sub-cube, lanes per cube and sampling blocks chosen. */
 mcubes_status mcubes_geometry_get(mcubes_ctx* ctx, long long* g, long long* m, long long* p,

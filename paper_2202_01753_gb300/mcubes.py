@@ -29,6 +29,7 @@ EXPORTED = [
     "mcubes_server_step", "mcubes_server_poll", "mcubes_server_stats", "mcubes_server_run_stream",
     "mcubes_selftest_fxmath", "mcubes_state_size", "mcubes_state_export", "mcubes_state_import",
     "mcubes_problem_get", "mcubes_get_opts", "mcubes_tables_set", "mcubes_server_set_step_iterations",
+    "mcubes_selftest_rebin",
 ]
 
 
@@ -127,6 +128,8 @@ def lib():
                                                       P(ctypes.c_int), P(ctypes.c_int)]),
                 "mcubes_selftest_fxmath": (ctypes.c_int, [ctypes.c_int, ll, ctypes.c_void_p, ctypes.c_void_p,
                                                           ctypes.c_void_p]),
+                "mcubes_selftest_rebin": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
+                                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
                 "mcubes_sample_range_noalloc": (ctypes.c_int, [
                     ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, dp, dp, ll, ctypes.c_int, ll,
                     ctypes.c_uint64, ctypes.c_int, ctypes.c_uint, ctypes.c_int, ll, ll, ctypes.c_void_p,

@@ -321,7 +321,7 @@ mcubes_status BatchEngine::admit(const mcubes_request& r, long long tag, int* sl
     D.ita = opts_.ita < 0 ? r.itmax : std::min(opts_.ita, r.itmax);
     D.itmax = r.itmax;
     D.m = (uint64_t)m;
-    D.jac0 = jacobian_scale(g, nb, d);
+    D.jac0 = jacobian_scale(g, nb, d) * family_jac_factor(r.integrand_id, fp);
     D.phi_scale_f = (float)(1.0 / ((double)g * nb));
     set_moment_scales(D, p);
     for (int j = 0; j < d; ++j) {

@@ -181,6 +181,11 @@ bool integrand_prepare(int id, const double* p, int np, int d, FamParams* out, c
         c[8] = p[8];
         c[9] = 1.0 / (2.0 * p[9] * p[9]);
         c[10] = 1.0 / (2.0 * pi * p[7] * p[7]);
+        if (!std::isnormal(c[10])) return false;  // the FP64 kernels fold it into the Jacobian's constant
+        // the FP64 kernels' expanded lognormal terms: h (L - mu)^2 = h L^2 - 2 h mu L + h mu^2
+        c[11] = c[2] - 2.0 * c[7] * c[6];
+        c[12] = c[3] - 2.0 * c[7] * c[6];
+        c[13] = 2.0 * c[7] * c[6] * c[6];
         break;
     default: return false;
     }
@@ -273,6 +278,11 @@ uint64_t cube_permutation(uint64_t n)
 
 // Constant factor of the FP64 kernels' Jacobian: their cells hold the bin
 // width over g, and each axis contributes nb * width to J.
+// Constant factor an FP64 family returns outside its kernel arithmetic: the
+// kernels take it as part of the Jacobian's constant (COSMO6: its
+// normalisation c10); 1 for the others.
+double family_jac_factor(int id, const FamParams& fp) { return id == MCUBES_F_COSMO6 ? fp.c[10] : 1.0; }
+
 double jacobian_scale(long long g, long long nb, int d)
 {
     double j = 1.0;
@@ -577,7 +587,7 @@ mcubes_status mcubes_setup(mcubes_ctx* c, int id, const double* params, int npar
         a.lo[j] = lo[j];
         a.scale[j] = hi[j] - lo[j];
     }
-    a.jac0 = jacobian_scale(g, nb, d);
+    a.jac0 = jacobian_scale(g, nb, d) * family_jac_factor(c->fid, fp);
     a.phi_scale_f = (float)(1.0 / ((double)g * nb));
     a.nb_f = (float)nb;
     set_moment_scales(a, p);

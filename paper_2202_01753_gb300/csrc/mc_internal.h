@@ -211,6 +211,7 @@ uint64_t cube_permutation(uint64_t n);
 // is already high enough.
 cudaError_t raise_smem_limit(const void* kernel, size_t smem);
 double jacobian_scale(long long g, long long nb, int d);  // (g nb)^d
+double family_jac_factor(int id, const FamParams& fp);    // an FP64 family's constant factor
 struct MomentScales {
     double inv_p, inv_var_den;
     float inv_p_f, inv_var_den_f;

@@ -133,7 +133,7 @@ extern "C" mcubes_status mcubes_sample_range_noalloc(
             a.lo[j] = lo[j];
             a.scale[j] = hi[j] - lo[j];
         }
-        a.jac0 = jacobian_scale(g, nbins, d);
+        a.jac0 = jacobian_scale(g, nbins, d) * family_jac_factor(integrand_id, fp);
         a.phi_scale_f = (float)(1.0 / ((double)g * nbins));
         a.nb_f = (float)nbins;
         set_moment_scales(a, p);

@@ -12,9 +12,10 @@
 // operation (its table point is the one at or below the mantissa, so its
 // series runs on unsigned high multiplies; its parts are summed as a 128-bit
 // fixed-point number and rounded to a double with integer operations), the
-// exponential one (the FMA that picks n = round(y 256/ln 2); r = y - n ln2/256
-// is formed from the low 64 bits of its two terms and made non-negative, so
-// its series also runs on unsigned high multiplies).
+// exponential none either (n = round(y 256/ln 2) from y's significand by one
+// high multiply; r = y - n ln2/256 is formed from the low 64 bits of its two
+// terms and made non-negative, so its series also runs on unsigned high
+// multiplies).
 //
 // Accuracy (tested against 60-digit references): fx_exp within 1 ulp;
 // fx_log within 1 ulp plus 2^-58 absolute (the series is absolute-accurate,
@@ -125,15 +126,21 @@ __device__ __forceinline__ double fx_exp_bits(uint64_t u)
         return exp_slow(y);
     }
     if (ay < 0x3C30000000000000ull) return 1.0;  // |y| < 2^-60: exp(y) rounds to 1
-    // y = n ln2/256 + r, n = round(y 256/ln2) by the 1.5 * 2^52 shift (one FMA)
-    const double t = fma(y, k256OverLn2, 0x1.8p52);
-    int64_t n = __double_as_longlong(t) - __double_as_longlong(0x1.8p52);
+    // y = n ln2/256 + r, n = round(y 256/ln2) from y's significand M and
+    // exponent E: |y| 256/ln2 = H 2^(E-1075) to 2^-52 relative, H =
+    // floor(M K / 2^53) with K = 256/ln2 in Q53, rounded at bit 1075 - E (>= 43).
+    // Near a tie n may be the other neighbour: |r| stays below ln2/256.
+    const int E = (int)((u >> 52) & 0x7FF);
+    const uint64_t M = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const uint64_t H = __umul64hi(M << 11, k256OverLn2Q53);
+    const int sh1 = 1074 - E;  // the rounding bit's position minus one
+    const int64_t na = (int64_t)(((sh1 < 64 ? H >> sh1 : 0ull) + 1ull) >> 1);
+    int64_t n = (u >> 63) ? -na : na;
     // r = y - n ln2/256 in Q62 (|r| <= ln2/512 + tiny: |rq| < 2^54), so only the
     // low 64 bits of y in Q62 and of n ln2/256 matter: y's bits below 2^-62 are
     // dropped; n ln2/256 = (n C + 2^52) >> 53 with C = ln2/256 in Q115 =
     // Hi 2^64 + Lo, of which bits 53..116 are kept
-    const int sh = (int)((u >> 52) & 0x7FF) - 1013;  // y = M 2^(E-1075): Q62 needs a shift by E - 1013
-    const uint64_t M = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = E - 1013;  // y = M 2^(E-1075): Q62 needs a shift by E - 1013
     uint64_t Y = sh >= 0 ? M << sh : (sh > -64 ? M >> -sh : 0ull);
     if (u >> 63) Y = 0ull - Y;
     const uint64_t nu = (uint64_t)n;

@@ -255,11 +255,12 @@ __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIX
             if (valid) {
                 // UpdateVariance (Alg. 3): cube mean and the variance of that
                 // mean; at p = 2 (every 1e8-call geometry) S1 = z, S2 = z^2 and
-                // the variance (z^2 - z^2/2)/2 is exactly z^2/4
+                // the variance (z^2 - z^2/2)/2 is exactly z^2/4: the z^2 are
+                // summed and the sum scaled once after the loop (exact)
                 R mean, var;
                 if (p == 2u) {
                     mean = K + S1 * R(0.5);
-                    var = S2 * R(0.25);
+                    var = S2;
                 } else {
                     mean = K + S1 * inv_p;
                     var = (S2 - S1 * S1 * inv_p) * inv_var_den;
@@ -291,9 +292,14 @@ __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIX
                 const double mean = K0 + s1 * a.inv_p;
                 acc.I += mean;
                 acc.V += (s2 - s1 * s1 * a.inv_p) * a.inv_var_den;
-                acc.A += fabs(mean);
+                if (a.want_abs) acc.A += fabs(mean);
             }
         }
+    }
+    if (L == 1u && p == 2u) {  // the z^2 / 4 of every cube, scaled once
+        acc.V *= 0.25;
+        acc.fV.hi *= 0.25f;
+        acc.fV.lo *= 0.25f;
     }
 }
 

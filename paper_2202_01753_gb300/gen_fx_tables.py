@@ -12,7 +12,8 @@ floating-point arithmetic", ACM TOMS 15(2), 1989:
   Q64 integer.
 * exp: 2^(j/256) for j = 0..255 as unsigned Q62 integers; ln 2 / 256 as a
   128-bit Q115 integer for the fixed-point argument reduction and as a Q62
-  integer for the step that makes the reduced argument non-negative.
+  integer for the step that makes the reduced argument non-negative; 256/ln 2
+  as a Q53 integer for the integer choice of n.
 * single-precision cosine: pi/2 as the sum of three floats (each the float
   nearest to what remains of pi/2) for a Cody-Waite reduction (Cody and
   Waite, "Software Manual for the Elementary Functions", 1980), and 2/pi.
@@ -72,6 +73,7 @@ def render():
         "",
         f"constexpr uint64_t kLn2Q64 = 0x{ln2_q64:016x}ull;  // ln 2 as Q64",
         f"constexpr double k256OverLn2 = {float(256 / ln2)!r};",
+        f"constexpr uint64_t k256OverLn2Q53 = 0x{int(mpmath.nint(256 / ln2 * mpmath.mpf(2) ** 53)):016x}ull;  // 256/ln2 as Q53",
         f"constexpr uint64_t kLn2Over256Q115Hi = 0x{c_q115 >> 64:016x}ull;  // ln2/256 = (Hi 2^64 + Lo) 2^-115",
         f"constexpr uint64_t kLn2Over256Q115Lo = 0x{c_q115 & (2 ** 64 - 1):016x}ull;",
         f"constexpr uint64_t kLn2Over256Q62 = 0x{int(mpmath.nint(c * mpmath.mpf(2) ** 62)):016x}ull;  // ln2/256 as Q62",

@@ -63,8 +63,10 @@ def test_exp_accuracy_host(fxhost):
     rng = np.random.default_rng(22)
     ys = np.concatenate([rng.uniform(-708.9, 707.9, 4000), rng.uniform(-3, 3, 4000),
                          rng.uniform(-1e-6, 1e-6, 500), [0.0, 1.0, -1.0, -700.0, 700.0]])
-    # arguments at and next to multiples of ln2/256, where the reduction picks n
-    steps = np.array([n * math.log(2) / 256 for n in range(-2000, 2000, 7)])
+    # arguments at and next to multiples of ln2/256 and halfway between them,
+    # where the reduction picks n
+    steps = np.array([n * math.log(2) / 256 for n in range(-2000, 2000, 7)] +
+                     [(n + 0.5) * math.log(2) / 256 for n in range(-2000, 2000, 7)])
     ys = np.concatenate([ys, steps, np.nextafter(steps, np.inf), np.nextafter(steps, -np.inf)])
     _, got = fxhost(ys)      # fx_exp(-y)
     mpmath.mp.dps = 40

@@ -145,14 +145,19 @@ __device__ __forceinline__ double int_prod_value(const IntProd& p)
 // the FP64 kernels, (x left edge, nb * x width) in single precision for the
 // mixed ones.  inv_g = 1 / g.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void map_cell_edges(DD left, DD right, double lo, double scale, double* xl, double* xw)
+{
+    const DD wd = dd_add(right, DD{-left.hi, -left.lo});
+    *xl = lo + scale * left.hi;
+    *xw = scale * (wd.hi + wd.lo);
+}
+
 __device__ __forceinline__ void map_cell(const double* row, const double* row_lo, uint32_t k, double lo,
                                          double scale, double* xl, double* xw)
 {
     const DD right{row[k], row_lo[k]};
     const DD left = k ? DD{row[k - 1], row_lo[k - 1]} : DD{0.0, 0.0};
-    const DD wd = dd_add(right, DD{-left.hi, -left.lo});
-    *xl = lo + scale * left.hi;
-    *xw = scale * (wd.hi + wd.lo);
+    map_cell_edges(left, right, lo, scale, xl, xw);
 }
 
 __device__ __forceinline__ double2 map_cell_f64(const double* row, const double* row_lo, uint32_t k, double lo,

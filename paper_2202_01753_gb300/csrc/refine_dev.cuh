@@ -36,6 +36,44 @@ static __device__ __forceinline__ double block_sum(double v, double* scratch)
     return out;
 }
 
+// Fixed-order sums of N values over the first kRedThreads threads of the
+// block (the other threads pass nothing and only meet the barriers; every
+// thread of the block must call).  GB300's FP64 pipe takes one warp
+// instruction per 16 cycles per SM whatever the number of active lanes, so
+// the small reductions of the finalisation run on four warps, not sixteen.
+constexpr int kRedThreads = 128;
+
+template <int N>
+static __device__ __forceinline__ void red4w(double (&v)[N])
+{
+    constexpr int kRedWarps = kRedThreads / 32;
+    __shared__ double red[N][kRedWarps];
+    __shared__ double out[N];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < kRedWarps) {
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], off);
+            if (lane == 0) red[q][warp] = v[q];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            double t = red[q][0];
+#pragma unroll
+            for (int w = 1; w < kRedWarps; ++w) t += red[q][w];
+            out[q] = t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < N; ++q) v[q] = out[q];
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // Exact cumulative weights of the rebinning: each bin weight w in [0, 1] as an
 // unsigned Q100 integer (128 bits; bits below 2^-100 dropped), their prefix
@@ -117,43 +155,50 @@ static __device__ void u128_inclusive_scan(const u128 (&v)[kPerThread], u128* c,
 }
 
 // Weighted-Estimates (inverse-variance weights, chi^2 per degree of freedom)
-// and Check-Convergence over n recorded iterations, by the whole block: each
-// thread takes iterations tid, tid + blockDim, ... and the sums are fixed-order
-// block sums, so the reciprocals of the variances are formed in parallel
-// (itmax may be thousands).  Every thread returns the same values.
+// and Check-Convergence over n recorded iterations: thread t < kRedThreads
+// takes iterations t, t + kRedThreads, ..., keeps their weights (the
+// reciprocals of the variances, formed in parallel: on GB300 a dependent
+// FP64 division costs thousands of cycles) and the sums are fixed-order.
+// Every thread of the block calls and gets the same values.
 static __device__ bool weigh_and_check(const double* hI, const double* hV, int n, double rel_tol, double abs_tol,
-                                       double* est, double* sigma, double* chi2_dof, double* scratch)
+                                       double* est, double* sigma, double* chi2_dof)
 {
-    double n_exact = 0.0, exact_sum = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x)
-        if (hV[i] == 0.0) {
-            n_exact += 1.0;
-            exact_sum += hI[i];
+    double s4[4] = {0.0, 0.0, 0.0, 0.0};
+    double w0 = 0.0, I0 = 0.0;  // this thread's first iteration, kept for the chi^2 pass
+    const double inv_dof = n > 1 ? 1.0 / (double)(n - 1) : 0.0;  // off the dependent chain
+    const int tmax = threadIdx.x < kRedThreads ? (n - (int)threadIdx.x + kRedThreads - 1) / kRedThreads : 0;
+    for (int t = 0; t < tmax; ++t) {
+        const int i = (int)threadIdx.x + t * kRedThreads;
+        const double I = hI[i], V = hV[i];
+        if (V == 0.0) {
+            s4[0] += 1.0;
+            s4[1] += I;
+        } else {
+            const double w = 1.0 / V;
+            s4[2] += w;
+            s4[3] += w * I;
+            if (t == 0) w0 = w;
         }
-    n_exact = block_sum(n_exact, scratch);
-    exact_sum = block_sum(exact_sum, scratch);
+        if (t == 0) I0 = I;
+    }
+    red4w<4>(s4);
     double I, sig, chi2 = 0.0;
-    if (n_exact > 0.0) {
-        I = exact_sum / n_exact;
+    if (s4[0] > 0.0) {
+        I = s4[1] / s4[0];
         sig = 0.0;
     } else {
-        double sw = 0.0, swi = 0.0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const double w = 1.0 / hV[i];
-            sw += w;
-            swi += w * hI[i];
-        }
-        sw = block_sum(sw, scratch);
-        swi = block_sum(swi, scratch);
-        I = swi / sw;
-        sig = sqrt(1.0 / sw);
+        const double inv_sw = 1.0 / s4[2];
+        I = s4[3] * inv_sw;
+        sig = sqrt(inv_sw);
         if (n > 1) {
-            double c = 0.0;
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                const double z = hI[i] - I;
-                c += z * z / hV[i];
+            double c[1] = {0.0};
+            for (int t = 0; t < tmax; ++t) {
+                const int i = (int)threadIdx.x + t * kRedThreads;
+                const double z = (t == 0 ? I0 : hI[i]) - I;
+                c[0] += z * z * (t == 0 ? w0 : 1.0 / hV[i]);
             }
-            chi2 = block_sum(c, scratch) / (double)(n - 1);
+            red4w<1>(c);
+            chi2 = c[0] * inv_dof;
         }
     }
     *est = I;
@@ -191,31 +236,52 @@ struct IterRecord {
 static __device__ void finalize_iteration(const double* part, int nparts, double m, const IterRecord& r,
                                           double* scratch, int split = 1, double p = 0.0)
 {
-    double s0 = 0.0, s1 = 0.0;
+    double s01[2] = {0.0, 0.0};
     if (split > 1) {
+        // thread t < kRedThreads merges cubes t, t + kRedThreads, ...: each
+        // slice re-based on the cube's first shift and added in slice order,
+        // eight slices' partials loaded ahead at a time; then the cube's mean
+        // and the variance of that mean (UpdateVariance of Alg. 3) with the
+        // reciprocals formed once (a dependent FP64 division costs thousands
+        // of cycles on GB300)
         const int ncubes = nparts / split;
         const double q = ceil(p / split);
-        for (int cb = threadIdx.x; cb < ncubes; cb += blockDim.x) {
+        const double inv_p = 1.0 / p, inv_var_den = inv_p / (p - 1.0);
+        for (int cb = threadIdx.x; threadIdx.x < kRedThreads && cb < ncubes; cb += kRedThreads) {
             const double* v = part + 3 * (size_t)cb * split;
             const double K0 = v[0];
             double S1 = 0.0, S2 = 0.0;
-            for (int k = 0; k < split; ++k) {
-                const double n = fmin(q, fmax(p - q * k, 0.0));
-                const double dK = v[3 * k] - K0;
-                S2 += fma(dK, fma(n, dK, 2.0 * v[3 * k + 1]), v[3 * k + 2]);
-                S1 += fma(n, dK, v[3 * k + 1]);
+            for (int k0 = 0; k0 < split; k0 += 8) {
+                double a0[8], a1[8], a2[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int k = min(k0 + u, split - 1);
+                    a0[u] = v[3 * k];
+                    a1[u] = v[3 * k + 1];
+                    a2[u] = v[3 * k + 2];
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int k = k0 + u;
+                    if (k < split) {
+                        const double n = fmin(q, fmax(p - q * k, 0.0));
+                        const double dK = a0[u] - K0;
+                        S2 += fma(dK, fma(n, dK, 2.0 * a1[u]), a2[u]);
+                        S1 += fma(n, dK, a1[u]);
+                    }
+                }
             }
-            s0 += K0 + S1 / p;
-            s1 += (S2 - S1 * S1 / p) / (p * (p - 1.0));
+            s01[0] += K0 + S1 * inv_p;
+            s01[1] += (S2 - S1 * S1 * inv_p) * inv_var_den;
         }
     } else {
-        for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
-            s0 += part[3 * (size_t)b + 0];
-            s1 += part[3 * (size_t)b + 1];
+        for (int b = threadIdx.x; threadIdx.x < kRedThreads && b < nparts; b += kRedThreads) {
+            s01[0] += part[3 * (size_t)b + 0];
+            s01[1] += part[3 * (size_t)b + 1];
         }
     }
-    s0 = block_sum(s0, scratch);
-    s1 = block_sum(s1, scratch);
+    red4w<2>(s01);
+    const double s0 = s01[0], s1 = s01[1];
     __shared__ int finite;
     if (threadIdx.x == 0) {
         const double I = s0 / m;
@@ -235,8 +301,7 @@ static __device__ void finalize_iteration(const double* part, int nparts, double
     __syncthreads();  // the record and the flag are visible to the block
     if (finite) {
         double est, sig, chi2;
-        const bool conv = weigh_and_check(r.hist_I, r.hist_V, *r.n, r.rel_tol, r.abs_tol, &est, &sig, &chi2,
-                                          scratch);
+        const bool conv = weigh_and_check(r.hist_I, r.hist_V, *r.n, r.rel_tol, r.abs_tol, &est, &sig, &chi2);
         if (threadIdx.x == 0) {
             *r.estimate = est;
             *r.sigma = sig;
@@ -248,6 +313,52 @@ static __device__ void finalize_iteration(const double* part, int nparts, double
         }
     }
     if (threadIdx.x == 0) *r.it += 1;
+}
+
+// Three times the smoothed value of bin k: C_{k-1} + C_k + C_{k+1}; the ends
+// 1.5 (C_0 + C_1) and 1.5 (C_{nb-2} + C_{nb-1}) (nb >= 2).
+static __device__ __forceinline__ double smoothed3(const double* sC, int k, int nb)
+{
+    if (k == 0) return 1.5 * (sC[0] + sC[1]);
+    if (k == nb - 1) return 1.5 * (sC[nb - 2] + sC[nb - 1]);
+    return sC[k - 1] + sC[k] + sC[k + 1];
+}
+
+// Compressed weight ((r - 1)/ln r)^alpha of a bin, r = sm3 / total, as Q100
+// (the library's log/exp: their FP64 work is a few instructions; CUDA's log
+// and pow cost ~100 on a pipe that issues 2 per clock per SM).
+static __device__ __forceinline__ u128 compressed_weight(double sm3, double inv_total, double alpha)
+{
+    const double r = sm3 * inv_total;
+    double w;
+    if (r <= 0.0) w = 0.0;
+    else if (r >= 1.0) w = 1.0;
+    else {
+        const double q = (r - 1.0) / fx::fx_log(r);
+        w = alpha == 1.5 ? q * sqrt(q) : fx::fx_exp(alpha * fx::fx_log(q));
+    }
+    return q100_of(w);
+}
+
+// New right edge of bin i - 1 (1 <= i < nb): the first bin k whose
+// cumulative weight reaches i/nb of the total W (nb C_k >= i W), at the
+// fraction (i W - nb C_{k-1}) / (nb w_k) of its width, in double-double.
+static __device__ __forceinline__ DD rebin_edge(int i, int nb, u128 W, const u128* sCum, const double* sB,
+                                                const double* sBlo)
+{
+    const u128 T = (u128)(uint64_t)i * W;
+    int lo = 0, hi = nb - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((u128)(uint64_t)nb * sCum[mid] >= T) hi = mid; else lo = mid + 1;
+    }
+    const int k = lo;
+    const u128 before = k > 0 ? (u128)(uint64_t)nb * sCum[k - 1] : (u128)0;  // < T
+    const u128 wk = sCum[k] - (k > 0 ? sCum[k - 1] : (u128)0);
+    const double frac = u128_to_double(T - before) / u128_to_double((u128)(uint64_t)nb * wk);
+    const DD left = k > 0 ? DD{sB[k - 1], sBlo[k - 1]} : DD{0.0, 0.0};
+    const DD width = dd_add(DD{sB[k], sBlo[k]}, DD{-left.hi, -left.lo});
+    return dd_add(left, dd_scale(width, frac));
 }
 
 // Adjust-Bin-Bounds of one axis (Lepage 1978, as the paper's Alg. 2 cites):
@@ -297,14 +408,8 @@ static __device__ void rebin_axis(const void* parts, size_t stride, int nparts, 
     double part = 0.0;
     for (int i = 0; i < kPerThread; ++i) {
         const int k = threadIdx.x * kPerThread + i;
-        double v = 0.0;
-        if (k < nb) {
-            if (k == 0) v = 1.5 * (sC[0] + sC[1]);
-            else if (k == nb - 1) v = 1.5 * (sC[nb - 2] + sC[nb - 1]);
-            else v = sC[k - 1] + sC[k] + sC[k + 1];
-        }
-        sm3[i] = v;
-        part += v;  // fixed order: contiguous chunks per thread, then the tree
+        sm3[i] = k < nb ? smoothed3(sC, k, nb) : 0.0;
+        part += sm3[i];  // fixed order: contiguous chunks per thread, then the tree
     }
     const double total = block_sum(part, scratch);
     if (!isfinite(total)) {
@@ -315,23 +420,12 @@ static __device__ void rebin_axis(const void* parts, size_t stride, int nparts, 
         return;
     }
     if (total <= 0.0) return;  // no information on this axis: grid unchanged
-    // compression ((r - 1)/ln r)^alpha with the library's log/exp (their FP64
-    // work is a few instructions; CUDA's log and pow cost ~100 on a pipe
-    // that issues 2 per clock per SM, and one block runs an axis)
     const double inv_total = 1.0 / total;
     u128 wq[kPerThread];
 #pragma unroll
     for (int i = 0; i < kPerThread; ++i) {
         const int k = threadIdx.x * kPerThread + i;
-        const double r = sm3[i] * inv_total;
-        double w;
-        if (k >= nb || r <= 0.0) w = 0.0;
-        else if (r >= 1.0) w = 1.0;
-        else {
-            const double q = (r - 1.0) / fx::fx_log(r);
-            w = alpha == 1.5 ? q * sqrt(q) : fx::fx_exp(alpha * fx::fx_log(q));
-        }
-        wq[i] = q100_of(w);
+        wq[i] = k < nb ? compressed_weight(sm3[i], inv_total, alpha) : (u128)0;
     }
     u128_inclusive_scan(wq, sCum, nb, wtot);
     const u128 W = sCum[nb - 1];
@@ -345,20 +439,7 @@ static __device__ void rebin_axis(const void* parts, size_t stride, int nparts, 
     double* out = grid;
     double* out_lo = grid_lo;
     for (int i = 1 + threadIdx.x; i < nb; i += blockDim.x) {
-        const u128 T = (u128)(uint64_t)i * W;  // i W: the target times nb
-        // first bin k whose cumulative weight through k reaches the target
-        int lo = 0, hi = nb - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if ((u128)(uint64_t)nb * sCum[mid] >= T) hi = mid; else lo = mid + 1;
-        }
-        const int k = lo;
-        const u128 before = k > 0 ? (u128)(uint64_t)nb * sCum[k - 1] : (u128)0;  // < T
-        const u128 wk = sCum[k] - (k > 0 ? sCum[k - 1] : (u128)0);
-        const double frac = u128_to_double(T - before) / u128_to_double((u128)(uint64_t)nb * wk);
-        const DD left = k > 0 ? DD{sB[k - 1], sBlo[k - 1]} : DD{0.0, 0.0};
-        const DD width = dd_add(DD{sB[k], sBlo[k]}, DD{-left.hi, -left.lo});
-        const DD e = dd_add(left, dd_scale(width, frac));
+        const DD e = rebin_edge(i, nb, W, sCum, sB, sBlo);
         for (int r = 0; r < ncopy; ++r) {
             out[(size_t)r * nb + i - 1] = e.hi;
             out_lo[(size_t)r * nb + i - 1] = e.lo;

@@ -50,12 +50,12 @@ from paper_2202_01753_gb300 import closed_forms as CF  # noqa: E402
 # "fp32_flops": 2 FFMA + FADD + FMUL per sample (the FP32-pipe fraction shown
 # beside the issue fraction).
 ROOFLINE_UNITS = {
-    ("cosmo6", "fp64"): {"kind": "fp64", "per_sample": 39.10, "traffic": 197.12e3, "pipe_busy": 0.690,
+    ("cosmo6", "fp64"): {"kind": "fp64", "per_sample": 32.47, "traffic": 318.98e3, "pipe_busy": 0.649,
                          "source": "profiles/vsample_cosmo6_fp64.md"},
-    ("gauss3", "fp64"): {"kind": "fp64", "per_sample": 27.06, "traffic": 101.38e3, "pipe_busy": 0.771,
+    ("gauss3", "fp64"): {"kind": "fp64", "per_sample": 26.99, "traffic": 102.40e3, "pipe_busy": 0.784,
                          "source": "profiles/vsample_gauss3_fp64.md"},
-    ("table6", "fp64"): {"kind": "fp64", "per_sample": 46.24, "dram_bytes_per_sample": 409.2, "traffic": 38.5034e9,
-                         "pipe_busy": 0.705,
+    ("table6", "fp64"): {"kind": "fp64", "per_sample": 43.25, "dram_bytes_per_sample": 409.2, "traffic": 38.5035e9,
+                         "pipe_busy": 0.706,
                          "source": "profiles/vsample_table6_fp64.md"},
     ("corner8", "mixed"): {"kind": "issue", "per_sample": 677.3, "traffic": 502.53e3, "fp32_flops": 109.94,
                            "source": "profiles/vsample_corner8_mixed.md"},

@@ -57,9 +57,9 @@ ROOFLINE_UNITS = {
     ("table6", "fp64"): {"kind": "fp64", "per_sample": 43.25, "dram_bytes_per_sample": 409.2, "traffic": 38.5035e9,
                          "pipe_busy": 0.706,
                          "source": "profiles/vsample_table6_fp64.md"},
-    ("corner8", "mixed"): {"kind": "issue", "per_sample": 677.3, "traffic": 502.53e3, "fp32_flops": 109.94,
+    ("corner8", "mixed"): {"kind": "issue", "per_sample": 654.3, "traffic": 182.02e3, "fp32_flops": 101.41,
                            "source": "profiles/vsample_corner8_mixed.md"},
-    ("osc10", "mixed"): {"kind": "issue", "per_sample": 805.8, "traffic": 515.84e3, "fp32_flops": 139.5,
+    ("osc10", "mixed"): {"kind": "issue", "per_sample": 794.6, "traffic": 179.46e3, "fp32_flops": 135.11,
                          "source": "profiles/vsample_osc10_mixed.md"},
 }
 DFMA_PER_CLK_PER_SM = 2.0

@@ -1,5 +1,6 @@
 """Pins of the test's own closed forms: brute-force midpoint sums at d <= 3,
-the survey-checked values, and Table 1's printed true value of f_A."""
+an independently evaluated value of the product-Gaussian integral, and
+Table 1's printed true values."""
 import math
 import os
 

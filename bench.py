@@ -663,7 +663,7 @@ def onedim_arm(args):
 # per successful level down to 1e-9; 100 seeds per level run as one batch;
 # true relative error against the closed forms
 # ---------------------------------------------------------------------------
-ACCURACY_SUITE = (("f2", 6), ("f3", 3), ("f4", 5), ("f5", 8), ("f6", 6))
+ACCURACY_SUITE = (("f1", 3), ("f2", 6), ("f3", 3), ("f4", 5), ("f5", 8), ("f6", 6))
 
 
 def accuracy_arm(args):

@@ -125,7 +125,7 @@ __device__ void refine_one(const BatchRefineArgs& a, uint32_t j, double* scratch
     if ((int)blockIdx.x == nrebin) {
         const IterRecord r{&st->it, &st->done, &st->error, &st->n, &st->converged, &st->estimate, &st->sigma,
                            &st->chi2_dof, D.hist_I, D.hist_V, D.itmax, D.rel_tol, D.abs_tol};
-        finalize_iteration(a.seg_part + 3 * (size_t)s0, (int)(s1 - s0), (double)D.m, r, scratch);
+        finalize_iteration(a.seg_part + 3 * (size_t)s0, (int)(s1 - s0), (double)D.m, r);
     } else {
         const int ax = blockIdx.x;
         const size_t off = (size_t)ax * nb;

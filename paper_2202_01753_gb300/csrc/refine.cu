@@ -138,7 +138,7 @@ refine_kernel(const __grid_constant__ RefineArgs a)
         DevState* st = a.st;
         const IterRecord r{&st->it, &st->done, &st->error, &st->n, &st->converged, &st->estimate, &st->sigma,
                            &st->chi2_dof, st->hist_I, st->hist_V, kItMax, st->rel_tol, st->abs_tol};
-        finalize_iteration(a.part, a.nblocks, a.m, r, scratch, a.split, a.p);
+        finalize_iteration(a.part, a.nblocks, a.m, r, a.split, a.p);
         return;
     }
     rebin_axis_cluster(a, c, rank, cluster, scratch);

@@ -234,7 +234,7 @@ struct IterRecord {
 // first slice's shift and summed in order, then the cube's mean and the
 // variance of that mean follow (UpdateVariance of Alg. 3).
 static __device__ void finalize_iteration(const double* part, int nparts, double m, const IterRecord& r,
-                                          double* scratch, int split = 1, double p = 0.0)
+                                          int split = 1, double p = 0.0)
 {
     double s01[2] = {0.0, 0.0};
     if (split > 1) {

@@ -108,7 +108,7 @@ __device__ __forceinline__ void stage_cells(typename Prec<MIXED>::Cell* cells, t
 // Returns F = f(x) * J and leaves the flat histogram index of every axis in
 // idx (16 bits each, two per word).  A provides d, nb, g, gmagic, jac0 ((g nb)^d), phi_scale_f
 // (1/(g nb)), hist_d and fam, and sample_words(a, counter) its Philox block.
-template <int FAM, bool MIXED, int NB4, class A>
+template <int FAM, bool MIXED, int NB4, int DC = 0, class A>
 __device__ __forceinline__ typename Prec<MIXED>::R
 sample_point(const A& a, const typename Prec<MIXED>::Cell* cells, uint32_t c, uint32_t s, uint32_t it,
              const uint32_t (&nbc)[4 * NB4], uint32_t (&idx)[2 * NB4])
@@ -116,7 +116,7 @@ sample_point(const A& a, const typename Prec<MIXED>::Cell* cells, uint32_t c, ui
     using R = typename Prec<MIXED>::R;
     using Fam = Family<FAM, R>;
     constexpr int DN = 4 * NB4;  // axes handled by this instantiation (d <= DN)
-    const uint32_t d = a.d, nb = a.nb;
+    const uint32_t d = DC ? (uint32_t)DC : a.d, nb = a.nb;  // DC: the dimension when fixed at compile time
     uint32_t w[DN];
 #pragma unroll
     for (int b = 0; b < NB4; ++b) {
@@ -178,7 +178,7 @@ struct CubeSums {
 // inv_p = 1/p and inv_var_den = 1/(p (p-1)) (inv_p_f, inv_var_den_f in single
 // precision) and want_abs (whether the sums of |cube mean| are needed: they
 // are reported by the sampling-pass calls, not used by an iteration).
-template <int FAM, bool MIXED, bool ADJ, int NB4, class A>
+template <int FAM, bool MIXED, bool ADJ, int NB4, int DC = 0, class A>
 __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIXED>::Cell* cells,
                                              typename Prec<MIXED>::H* hist, uint64_t cube_lo, uint64_t ncubes,
                                              uint64_t perm_k, uint64_t group0, uint64_t gstride, uint32_t it,
@@ -187,7 +187,7 @@ __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIX
     using R = typename Prec<MIXED>::R;
     using HT = typename Prec<MIXED>::H;
     constexpr int DN = 4 * NB4;
-    const uint32_t d = a.d, nb = a.nb;
+    const uint32_t d = DC ? (uint32_t)DC : a.d, nb = a.nb;
     const uint32_t hist_d = a.hist_d;  // axes with a histogram: d, or 1 (m-Cubes1D, Sec. 3)
     const uint32_t hist_s = (uint32_t)__cvta_generic_to_shared(hist);
     const uint32_t L = lanes;
@@ -234,7 +234,7 @@ __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIX
         if (valid) {
             for (uint32_t s = seg_lane; s < p; s += L) {
                 uint32_t idx[2 * NB4];
-                const R F = sample_point<FAM, MIXED, NB4>(a, cells, c, s, it, nbc, idx);
+                const R F = sample_point<FAM, MIXED, NB4, DC>(a, cells, c, s, it, nbc, idx);
                 if (n == 0) {
                     K = F;  // the shift: its own term is zero
                 } else if (n == 1) {
@@ -311,7 +311,7 @@ __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIX
 // S2 += dK (2 S1 + n dK), dK = K_t - K: no division) and summed in a fixed
 // order; the block writes (K, S1, S2) to out[0..2] and the refinement
 // combines a cube's blocks the same way.
-template <int FAM, bool MIXED, bool ADJ, int NB4, class A>
+template <int FAM, bool MIXED, bool ADJ, int NB4, int DC = 0, class A>
 __device__ __forceinline__ void sample_cube_slice(const A& a, const typename Prec<MIXED>::Cell* cells,
                                                   typename Prec<MIXED>::H* hist, uint64_t cube, uint32_t k,
                                                   uint32_t split, uint32_t it, uint32_t p,
@@ -320,7 +320,7 @@ __device__ __forceinline__ void sample_cube_slice(const A& a, const typename Pre
     using R = typename Prec<MIXED>::R;
     using HT = typename Prec<MIXED>::H;
     constexpr int DN = 4 * NB4;
-    const uint32_t d = a.d, nb = a.nb;
+    const uint32_t d = DC ? (uint32_t)DC : a.d, nb = a.nb;
     const uint32_t hist_d = a.hist_d;
     const uint32_t q = (p + split - 1) / split;
     const uint32_t s_lo = k * q, s_hi = min(p, s_lo + q);
@@ -345,7 +345,7 @@ __device__ __forceinline__ void sample_cube_slice(const A& a, const typename Pre
     uint32_t n = 0;
     for (uint32_t s = s_lo + threadIdx.x; s < s_hi; s += blockDim.x) {
         uint32_t idx[2 * NB4];
-        const R F = sample_point<FAM, MIXED, NB4>(a, cells, c, s, it, nbc, idx);
+        const R F = sample_point<FAM, MIXED, NB4, DC>(a, cells, c, s, it, nbc, idx);
         if (n == 0) {
             K = F;  // the shift: its own term is zero
         } else {
@@ -428,15 +428,22 @@ __device__ __forceinline__ void block_write_sums(const CubeSums& acc, double (*r
 // for the table integrands in FP64, whose spills and larger table footprint
 // in L1/L2 cost a third (two blocks; table6 at three: 16.6 ms per 1e8 calls
 // against 10.0 ms).  Four blocks (64 registers) for the mixed kernels up to
-// d = 8 measured slower too (corner8: 23.3 ms per 1e9 calls against 21.3).
+// d = 8 measured slower too (corner8: 23.3 ms per 1e9 calls against 21.3);
+// for d <= 4 four blocks fit in 64 registers without spills (gauss3 in
+// cube-split mode lives on resident warps).
 template <int FAM, bool MIXED, int NB4>
-constexpr int vsample_min_blocks() { return (FAM == MCUBES_F_TABLE && !MIXED) ? 2 : 3; }
+constexpr int vsample_min_blocks() { return (FAM == MCUBES_F_TABLE && !MIXED) ? 2 : (NB4 == 1 ? 4 : 3); }
 
-template <int FAM, bool MIXED, bool ADJ, int NB4>
-__global__ void __launch_bounds__(kVsThreads, vsample_min_blocks<FAM, MIXED, NB4>())
+// One instantiation per dimension D: with the axis count a compile-time
+// constant every per-axis loop is unrolled without guards and the families'
+// dimension-dependent code (the corner family's power) folds (corner8: 21.4
+// -> 17.7 ms per 1e9-call launch against a runtime count).
+template <int FAM, bool MIXED, bool ADJ, int D>
+__global__ void __launch_bounds__(kVsThreads, vsample_min_blocks<FAM, MIXED, (D + 3) / 4>())
 vsample_kernel(const __grid_constant__ VsArgs a)
 {
-    if constexpr (FAM == MCUBES_F_COSMO6 && NB4 != 2) {
+    constexpr int NB4 = (D + 3) / 4;  // Philox blocks per sample
+    if constexpr (FAM == MCUBES_F_COSMO6 && D != 6) {
         return;  // six axes only: never launched
     } else {
     using Cell = typename Prec<MIXED>::Cell;
@@ -444,7 +451,8 @@ vsample_kernel(const __grid_constant__ VsArgs a)
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[3][kVsThreads / 32];
 
-    const uint32_t d = a.d, nb = a.nb;
+    constexpr uint32_t d = D;
+    const uint32_t nb = a.nb;
     uint32_t it = a.it_fixed;
     if (a.st != nullptr) {
         const int done = *(volatile const int*)&a.st->done;
@@ -460,12 +468,12 @@ vsample_kernel(const __grid_constant__ VsArgs a)
     __syncthreads();
 
     if (a.split > 1) {
-        sample_cube_slice<FAM, MIXED, ADJ, NB4>(a, cells, hist, a.cube_begin + blockIdx.x / a.split,
+        sample_cube_slice<FAM, MIXED, ADJ, NB4, D>(a, cells, hist, a.cube_begin + blockIdx.x / a.split,
                                                 blockIdx.x % a.split, a.split, it, a.p, red,
                                                 a.part + 3 * (size_t)blockIdx.x);
     } else {
         CubeSums acc;
-        sample_cubes<FAM, MIXED, ADJ, NB4>(a, cells, hist, a.cube_begin, a.cube_end - a.cube_begin, a.perm_k,
+        sample_cubes<FAM, MIXED, ADJ, NB4, D>(a, cells, hist, a.cube_begin, a.cube_end - a.cube_begin, a.perm_k,
                                            blockIdx.x, gridDim.x, it, a.lanes, a.p, acc);
         block_write_sums(acc, red, a.part + 3 * (size_t)blockIdx.x);
     }
@@ -482,19 +490,30 @@ vsample_kernel(const __grid_constant__ VsArgs a)
 }
 
 template <int FAM, bool MIXED, bool ADJ>
-inline auto vsample_kernel_nb4(int d)
+inline auto vsample_kernel_d(int d)
 {
     using K = void (*)(VsArgs);
-    if (d <= 4) return (K)vsample_kernel<FAM, MIXED, ADJ, 1>;
-    if (d <= 8) return (K)vsample_kernel<FAM, MIXED, ADJ, 2>;
-    return (K)vsample_kernel<FAM, MIXED, ADJ, 3>;
+    switch (d) {
+    case 1: return (K)vsample_kernel<FAM, MIXED, ADJ, 1>;
+    case 2: return (K)vsample_kernel<FAM, MIXED, ADJ, 2>;
+    case 3: return (K)vsample_kernel<FAM, MIXED, ADJ, 3>;
+    case 4: return (K)vsample_kernel<FAM, MIXED, ADJ, 4>;
+    case 5: return (K)vsample_kernel<FAM, MIXED, ADJ, 5>;
+    case 6: return (K)vsample_kernel<FAM, MIXED, ADJ, 6>;
+    case 7: return (K)vsample_kernel<FAM, MIXED, ADJ, 7>;
+    case 8: return (K)vsample_kernel<FAM, MIXED, ADJ, 8>;
+    case 9: return (K)vsample_kernel<FAM, MIXED, ADJ, 9>;
+    case 10: return (K)vsample_kernel<FAM, MIXED, ADJ, 10>;
+    case 11: return (K)vsample_kernel<FAM, MIXED, ADJ, 11>;
+    default: return (K)vsample_kernel<FAM, MIXED, ADJ, 12>;  // d is checked to be 1..12
+    }
 }
 
 template <int FAM>
 inline auto vsample_kernel_ptr(bool mixed, bool adjust, int d)
 {
-    if (mixed) return adjust ? vsample_kernel_nb4<FAM, true, true>(d) : vsample_kernel_nb4<FAM, true, false>(d);
-    return adjust ? vsample_kernel_nb4<FAM, false, true>(d) : vsample_kernel_nb4<FAM, false, false>(d);
+    if (mixed) return adjust ? vsample_kernel_d<FAM, true, true>(d) : vsample_kernel_d<FAM, true, false>(d);
+    return adjust ? vsample_kernel_d<FAM, false, true>(d) : vsample_kernel_d<FAM, false, false>(d);
 }
 
 template <int FAM>

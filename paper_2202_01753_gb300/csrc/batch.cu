@@ -37,32 +37,32 @@ cudaError_t vsample_batch_occupancy_cosmo6(bool, int, size_t, int*);
 
 cudaError_t launch_vsample_batch(int cls, bool mixed, const BatchArgs& a, int grid, size_t smem, cudaStream_t s)
 {
-    const int nb4 = cls % 3 + 1;
-    switch (cls / 3) {
-    case MCUBES_F_CONST: return launch_vsample_batch_const(mixed, nb4, a, grid, smem, s);
-    case MCUBES_F_GAUSS: return launch_vsample_batch_gauss(mixed, nb4, a, grid, smem, s);
-    case MCUBES_F_CORNER: return launch_vsample_batch_corner(mixed, nb4, a, grid, smem, s);
-    case MCUBES_F_OSC: return launch_vsample_batch_osc(mixed, nb4, a, grid, smem, s);
-    case MCUBES_F_PRODPEAK: return launch_vsample_batch_prodpeak(mixed, nb4, a, grid, smem, s);
-    case MCUBES_F_C0: return launch_vsample_batch_c0(mixed, nb4, a, grid, smem, s);
-    case MCUBES_F_DISCONT: return launch_vsample_batch_discont(mixed, nb4, a, grid, smem, s);
-    case MCUBES_F_COSMO6: return launch_vsample_batch_cosmo6(mixed, nb4, a, grid, smem, s);
+    const int dcls = cls % kDMax + 1;  // the class's dimension
+    switch (cls / kDMax) {
+    case MCUBES_F_CONST: return launch_vsample_batch_const(mixed, dcls, a, grid, smem, s);
+    case MCUBES_F_GAUSS: return launch_vsample_batch_gauss(mixed, dcls, a, grid, smem, s);
+    case MCUBES_F_CORNER: return launch_vsample_batch_corner(mixed, dcls, a, grid, smem, s);
+    case MCUBES_F_OSC: return launch_vsample_batch_osc(mixed, dcls, a, grid, smem, s);
+    case MCUBES_F_PRODPEAK: return launch_vsample_batch_prodpeak(mixed, dcls, a, grid, smem, s);
+    case MCUBES_F_C0: return launch_vsample_batch_c0(mixed, dcls, a, grid, smem, s);
+    case MCUBES_F_DISCONT: return launch_vsample_batch_discont(mixed, dcls, a, grid, smem, s);
+    case MCUBES_F_COSMO6: return launch_vsample_batch_cosmo6(mixed, dcls, a, grid, smem, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t vsample_batch_occupancy(int cls, bool mixed, size_t smem, int* blocks)
 {
-    const int nb4 = cls % 3 + 1;
-    switch (cls / 3) {
-    case MCUBES_F_CONST: return vsample_batch_occupancy_const(mixed, nb4, smem, blocks);
-    case MCUBES_F_GAUSS: return vsample_batch_occupancy_gauss(mixed, nb4, smem, blocks);
-    case MCUBES_F_CORNER: return vsample_batch_occupancy_corner(mixed, nb4, smem, blocks);
-    case MCUBES_F_OSC: return vsample_batch_occupancy_osc(mixed, nb4, smem, blocks);
-    case MCUBES_F_PRODPEAK: return vsample_batch_occupancy_prodpeak(mixed, nb4, smem, blocks);
-    case MCUBES_F_C0: return vsample_batch_occupancy_c0(mixed, nb4, smem, blocks);
-    case MCUBES_F_DISCONT: return vsample_batch_occupancy_discont(mixed, nb4, smem, blocks);
-    case MCUBES_F_COSMO6: return vsample_batch_occupancy_cosmo6(mixed, nb4, smem, blocks);
+    const int dcls = cls % kDMax + 1;  // the class's dimension
+    switch (cls / kDMax) {
+    case MCUBES_F_CONST: return vsample_batch_occupancy_const(mixed, dcls, smem, blocks);
+    case MCUBES_F_GAUSS: return vsample_batch_occupancy_gauss(mixed, dcls, smem, blocks);
+    case MCUBES_F_CORNER: return vsample_batch_occupancy_corner(mixed, dcls, smem, blocks);
+    case MCUBES_F_OSC: return vsample_batch_occupancy_osc(mixed, dcls, smem, blocks);
+    case MCUBES_F_PRODPEAK: return vsample_batch_occupancy_prodpeak(mixed, dcls, smem, blocks);
+    case MCUBES_F_C0: return vsample_batch_occupancy_c0(mixed, dcls, smem, blocks);
+    case MCUBES_F_DISCONT: return vsample_batch_occupancy_discont(mixed, dcls, smem, blocks);
+    case MCUBES_F_COSMO6: return vsample_batch_occupancy_cosmo6(mixed, dcls, smem, blocks);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -211,8 +211,8 @@ void BatchEngine::release()
 
 size_t BatchEngine::smem_bytes(int cls) const
 {
-    const int nb4 = cls % 3 + 1;
-    return (size_t)4 * nb4 * opts_.nbins * (cell_bytes(mixed_) + hist_bytes(mixed_));
+    const int dcls = cls % kDMax + 1;  // the class's dimension
+    return (size_t)dcls * opts_.nbins * (cell_bytes(mixed_) + hist_bytes(mixed_));
 }
 
 int BatchEngine::class_blocks(int cls) const { return std::max(1, std::min(tuned_bps_, occ_[cls])) * num_sms_; }
@@ -226,7 +226,7 @@ cudaError_t BatchEngine::reserve(int capacity, int itcap)
     int occ_max = 1;
     for (int c = 0; c < kNumClasses; ++c) {
         occ_[c] = 0;
-        if (c / 3 == MCUBES_F_COSMO6 && c % 3 != 1) continue;  // six axes only
+        if (c / kDMax == MCUBES_F_COSMO6 && c % kDMax != 5) continue;  // six axes only
         if ((e = vsample_batch_occupancy(c, mixed_, smem_bytes(c), &occ_[c]))) return e;
         occ_max = std::max(occ_max, occ_[c]);
     }
@@ -373,10 +373,10 @@ cudaError_t BatchEngine::flush_admissions()
     return e;
 }
 
-void BatchEngine::live_slots(std::vector<int>* live, unsigned* class_mask) const
+void BatchEngine::live_slots(std::vector<int>* live, ClassMask* class_mask) const
 {
     live->clear();
-    *class_mask = 0;
+    class_mask->reset();
     std::vector<int> by_class[kNumClasses];
     for (int s = 0; s < capacity_; ++s) {
         const Slot& S = slots_[s];
@@ -385,7 +385,7 @@ void BatchEngine::live_slots(std::vector<int>* live, unsigned* class_mask) const
     }
     for (int c = 0; c < kNumClasses; ++c) {
         if (by_class[c].empty()) continue;
-        *class_mask |= 1u << c;
+        class_mask->set(c);
         live->insert(live->end(), by_class[c].begin(), by_class[c].end());
     }
 }
@@ -500,10 +500,10 @@ BatchRefineArgs BatchEngine::refine_args() const
     return r;
 }
 
-cudaError_t BatchEngine::enqueue_iteration(unsigned mask)
+cudaError_t BatchEngine::enqueue_iteration(const ClassMask& mask)
 {
     for (int c = 0; c < kNumClasses; ++c) {
-        if (!(mask >> c & 1u)) continue;
+        if (!mask.test(c)) continue;
         cudaError_t e = launch_vsample_batch(c, mixed_, sample_args(c), class_blocks(c), smem_bytes(c), stream_);
         if (e) return e;
     }
@@ -513,15 +513,15 @@ cudaError_t BatchEngine::enqueue_iteration(unsigned mask)
 // One iteration as a CUDA graph: the sampling kernels of the classes in the
 // mask, then the refinement.  Re-captured only when a class appears that
 // the graph does not launch, or the launch shape changes.
-cudaError_t BatchEngine::capture(unsigned mask)
+cudaError_t BatchEngine::capture(ClassMask mask)
 {
-    if (exec_ && (mask & ~graph_mask_) == 0 && graph_bps_ == tuned_bps_) return cudaSuccess;
+    if (exec_ && (mask & ~graph_mask_).none() && graph_bps_ == tuned_bps_) return cudaSuccess;
     mask |= graph_mask_;
     if (exec_) cudaGraphExecDestroy(exec_);
     if (graph_) cudaGraphDestroy(graph_);
     exec_ = nullptr;
     graph_ = nullptr;
-    graph_mask_ = 0;
+    graph_mask_.reset();
     if (stream_ == nullptr) return cudaSuccess;  // the legacy stream cannot be captured: launch directly
     cudaError_t e = cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal);
     if (e) return e;
@@ -539,12 +539,12 @@ cudaError_t BatchEngine::capture(unsigned mask)
 // occupancy) and the samples-per-thread cap that sets lanes per cube, by
 // timing sampling-only launches of a subset of this batch's first
 // iteration; the choice is kept for the life of the engine.
-cudaError_t BatchEngine::autotune(const std::vector<int>& live, unsigned mask)
+cudaError_t BatchEngine::autotune(const std::vector<int>& live, const ClassMask& mask)
 {
     if (tuned_) return cudaSuccess;
     int occ_hi = 1;
     for (int c = 0; c < kNumClasses; ++c)
-        if (mask >> c & 1u) occ_hi = std::max(occ_hi, occ_[c]);
+        if (mask.test(c)) occ_hi = std::max(occ_hi, occ_[c]);
     // Timing a handful of small integrals tells the launch shapes apart by
     // noise alone, and the choice is kept for the engine's life: until
     // kTuneMinLive integrals are live (a server's first steps), run with the
@@ -589,7 +589,7 @@ cudaError_t BatchEngine::autotune(const std::vector<int>& live, unsigned mask)
             for (int rep = 0; rep < 4; ++rep) {  // the first launch warms up; the fastest of the rest counts
                 cudaEventRecord(e0, stream_);
                 for (int c = 0; c < kNumClasses && !e; ++c)
-                    if (mask >> c & 1u)
+                    if (mask.test(c))
                         e = launch_vsample_batch(c, mixed_, sample_args(c), class_blocks(c), smem_bytes(c), stream_);
                 if (e) break;
                 cudaEventRecord(e1, stream_);
@@ -629,7 +629,7 @@ cudaError_t BatchEngine::step(int* ran, int iters)
     cudaError_t e = flush_admissions();
     if (e) return e;
     std::vector<int> live;
-    unsigned mask = 0;
+    ClassMask mask;
     live_slots(&live, &mask);
     if (live.empty()) return cudaSuccess;
     if ((e = autotune(live, mask))) return e;

@@ -1,5 +1,5 @@
 // batch.cuh -- the persistent batched sampling kernels: one launch per class
-// of integrals (integrand family x groups of four axes) samples one
+// of integrals (integrand family x dimension) samples one
 // iteration of every live integral of that class.  The host lays the class's
 // live integrals' samples end to end and cuts that line into one equal,
 // cube-aligned chunk per block; a block therefore samples a few segments
@@ -16,11 +16,14 @@
 
 namespace mc {
 
-template <int FAM, bool MIXED, int NB4>
+// One kernel per (family, dimension D): every segment it samples belongs to
+// an integral of that dimension.
+template <int FAM, bool MIXED, int D>
 __global__ void __launch_bounds__(kVsThreads, 2)
 vsample_batch_kernel(const __grid_constant__ BatchArgs a)
 {
-    if constexpr (FAM == MCUBES_F_COSMO6 && NB4 != 2) {
+    constexpr int NB4 = (D + 3) / 4;
+    if constexpr (FAM == MCUBES_F_COSMO6 && D != 6) {
         return;  // six axes only: never launched
     } else {
     using Cell = typename Prec<MIXED>::Cell;
@@ -47,7 +50,8 @@ vsample_batch_kernel(const __grid_constant__ BatchArgs a)
         // ita); the refinement reads the flag back
         const bool adjust = seg.adjust && (int)B.it < sd.ita;
         if (threadIdx.x == 0) a.segs[si].adjust = adjust ? 1u : 0u;
-        const uint32_t d = sd.d, nb = sd.nb;
+        constexpr uint32_t d = D;
+        const uint32_t nb = sd.nb;
         Cell* cells = reinterpret_cast<Cell*>(smem);
         HT* hist = reinterpret_cast<HT*>(smem + cell_bytes(MIXED) * d * nb);
         if (adjust) stage_cells<MIXED, true>(cells, hist, sd.cells, d, nb, d);
@@ -60,10 +64,10 @@ vsample_batch_kernel(const __grid_constant__ BatchArgs a)
         const uint32_t it = B.it;
         CubeSums acc;
         if (adjust)
-            sample_cubes<FAM, MIXED, true, NB4>(v, cells, hist, seg.c0, seg.c1 - seg.c0, seg.perm_k, 0, 1, it,
+            sample_cubes<FAM, MIXED, true, NB4, D>(v, cells, hist, seg.c0, seg.c1 - seg.c0, seg.perm_k, 0, 1, it,
                                                 sd.lanes, sd.p, acc);
         else
-            sample_cubes<FAM, MIXED, false, NB4>(v, cells, hist, seg.c0, seg.c1 - seg.c0, seg.perm_k, 0, 1, it,
+            sample_cubes<FAM, MIXED, false, NB4, D>(v, cells, hist, seg.c0, seg.c1 - seg.c0, seg.perm_k, 0, 1, it,
                                                  sd.lanes, sd.p, acc);
         block_write_sums(acc, red, a.seg_part + 3 * (size_t)si);
         if (adjust) {
@@ -76,19 +80,30 @@ vsample_batch_kernel(const __grid_constant__ BatchArgs a)
 }
 
 template <int FAM, bool MIXED>
-inline auto vsample_batch_kernel_ptr(int nb4)
+inline auto vsample_batch_kernel_ptr(int d)
 {
     using K = void (*)(BatchArgs);
-    if (nb4 <= 1) return (K)vsample_batch_kernel<FAM, MIXED, 1>;
-    if (nb4 == 2) return (K)vsample_batch_kernel<FAM, MIXED, 2>;
-    return (K)vsample_batch_kernel<FAM, MIXED, 3>;
+    switch (d) {
+    case 1: return (K)vsample_batch_kernel<FAM, MIXED, 1>;
+    case 2: return (K)vsample_batch_kernel<FAM, MIXED, 2>;
+    case 3: return (K)vsample_batch_kernel<FAM, MIXED, 3>;
+    case 4: return (K)vsample_batch_kernel<FAM, MIXED, 4>;
+    case 5: return (K)vsample_batch_kernel<FAM, MIXED, 5>;
+    case 6: return (K)vsample_batch_kernel<FAM, MIXED, 6>;
+    case 7: return (K)vsample_batch_kernel<FAM, MIXED, 7>;
+    case 8: return (K)vsample_batch_kernel<FAM, MIXED, 8>;
+    case 9: return (K)vsample_batch_kernel<FAM, MIXED, 9>;
+    case 10: return (K)vsample_batch_kernel<FAM, MIXED, 10>;
+    case 11: return (K)vsample_batch_kernel<FAM, MIXED, 11>;
+    default: return (K)vsample_batch_kernel<FAM, MIXED, 12>;
+    }
 }
 
 template <int FAM>
-cudaError_t launch_vsample_batch_family(bool mixed, int nb4, const BatchArgs& a, int grid, size_t smem,
+cudaError_t launch_vsample_batch_family(bool mixed, int d, const BatchArgs& a, int grid, size_t smem,
                                         cudaStream_t s)
 {
-    auto k = mixed ? vsample_batch_kernel_ptr<FAM, true>(nb4) : vsample_batch_kernel_ptr<FAM, false>(nb4);
+    auto k = mixed ? vsample_batch_kernel_ptr<FAM, true>(d) : vsample_batch_kernel_ptr<FAM, false>(d);
     cudaError_t e = raise_smem_limit((const void*)k, smem);
     if (e != cudaSuccess) return e;
     k<<<grid, kVsThreads, smem, s>>>(a);
@@ -96,9 +111,9 @@ cudaError_t launch_vsample_batch_family(bool mixed, int nb4, const BatchArgs& a,
 }
 
 template <int FAM>
-cudaError_t vsample_batch_occupancy_family(bool mixed, int nb4, size_t smem, int* blocks)
+cudaError_t vsample_batch_occupancy_family(bool mixed, int d, size_t smem, int* blocks)
 {
-    auto k = mixed ? vsample_batch_kernel_ptr<FAM, true>(nb4) : vsample_batch_kernel_ptr<FAM, false>(nb4);
+    auto k = mixed ? vsample_batch_kernel_ptr<FAM, true>(d) : vsample_batch_kernel_ptr<FAM, false>(d);
     cudaError_t e = raise_smem_limit((const void*)k, smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, kVsThreads, smem);
@@ -110,13 +125,13 @@ cudaError_t vsample_batch_occupancy_family(bool mixed, int nb4, size_t smem, int
 // (launch_vsample_batch_<name>, vsample_batch_occupancy_<name>).
 #define MC_INSTANTIATE_BATCH_FAMILY(FAM, NAME)                                                        \
     namespace mc {                                                                                    \
-    cudaError_t launch_vsample_batch_##NAME(bool mixed, int nb4, const BatchArgs& a, int grid,        \
+    cudaError_t launch_vsample_batch_##NAME(bool mixed, int d, const BatchArgs& a, int grid,          \
                                             size_t smem, cudaStream_t s)                              \
     {                                                                                                 \
-        return launch_vsample_batch_family<FAM>(mixed, nb4, a, grid, smem, s);                        \
+        return launch_vsample_batch_family<FAM>(mixed, d, a, grid, smem, s);                          \
     }                                                                                                 \
-    cudaError_t vsample_batch_occupancy_##NAME(bool mixed, int nb4, size_t smem, int* blocks)         \
+    cudaError_t vsample_batch_occupancy_##NAME(bool mixed, int d, size_t smem, int* blocks)           \
     {                                                                                                 \
-        return vsample_batch_occupancy_family<FAM>(mixed, nb4, smem, blocks);                         \
+        return vsample_batch_occupancy_family<FAM>(mixed, d, smem, blocks);                           \
     }                                                                                                 \
     }

@@ -3,12 +3,15 @@
 // graph of one iteration and the launch-shape autotuner (batch.cu).
 #pragma once
 
+#include <bitset>
 #include <utility>
 #include <vector>
 
 #include "mc_internal.h"
 
 namespace mc {
+
+using ClassMask = std::bitset<kNumClasses>;  // kernel classes present (family x dimension)
 
 // A device allocation that only grows.
 struct DevBuf {
@@ -89,14 +92,14 @@ private:
     int choose_lanes(long long p) const;
     cudaError_t flush_admissions();
     // live slots grouped by class (class order, slot order within a class)
-    void live_slots(std::vector<int>* live, unsigned* class_mask) const;
+    void live_slots(std::vector<int>* live, ClassMask* class_mask) const;
     void partition(const std::vector<int>& live, int* nseg);
     cudaError_t upload_partition(const std::vector<int>& live, int nseg);
     BatchArgs sample_args(int cls) const;
     BatchRefineArgs refine_args() const;
-    cudaError_t enqueue_iteration(unsigned class_mask);
-    cudaError_t capture(unsigned class_mask);
-    cudaError_t autotune(const std::vector<int>& live, unsigned class_mask);
+    cudaError_t enqueue_iteration(const ClassMask& class_mask);
+    cudaError_t capture(ClassMask class_mask);
+    cudaError_t autotune(const std::vector<int>& live, const ClassMask& class_mask);
     cudaError_t refresh();
 
     int device_;
@@ -121,7 +124,7 @@ private:
     BatchState* h_states_ = nullptr; // pinned read-back
     cudaGraph_t graph_ = nullptr;
     cudaGraphExec_t exec_ = nullptr;
-    unsigned graph_mask_ = 0;      // classes the captured graph launches
+    ClassMask graph_mask_;         // classes the captured graph launches
     int graph_bps_ = 0;
 };
 

@@ -162,9 +162,10 @@ struct BatchRefineArgs {
     double alpha;
 };
 
-// Batched kernels are instantiated per class: family x nb4 = ceil(d / 4).
-constexpr int kNumClasses = MCUBES_F_TABLE * 3;  // families with batched kernels (not TABLE)
-__host__ __device__ constexpr int batch_class(int family, int d) { return family * 3 + (d + 3) / 4 - 1; }
+// Batched kernels are instantiated per class: family x dimension (an exact
+// axis count unrolls the per-axis loops without guards).
+constexpr int kNumClasses = MCUBES_F_TABLE * kDMax;  // families with batched kernels (not TABLE)
+__host__ __device__ constexpr int batch_class(int family, int d) { return family * kDMax + d - 1; }
 cudaError_t launch_vsample_batch(int cls, bool mixed, const BatchArgs& a, int grid, size_t smem, cudaStream_t s);
 cudaError_t vsample_batch_occupancy(int cls, bool mixed, size_t smem, int* blocks_per_sm);
 cudaError_t launch_refine_batch(const BatchRefineArgs& a, int capacity, int rows, cudaStream_t s);

@@ -50,16 +50,16 @@ from paper_2202_01753_gb300 import closed_forms as CF  # noqa: E402
 # "fp32_flops": 2 FFMA + FADD + FMUL per sample (the FP32-pipe fraction shown
 # beside the issue fraction).
 ROOFLINE_UNITS = {
-    ("cosmo6", "fp64"): {"kind": "fp64", "per_sample": 32.47, "traffic": 318.98e3, "pipe_busy": 0.649,
+    ("cosmo6", "fp64"): {"kind": "fp64", "per_sample": 32.48, "traffic": 481.6e3, "pipe_busy": 0.691,
                          "source": "profiles/vsample_cosmo6_fp64.md"},
-    ("gauss3", "fp64"): {"kind": "fp64", "per_sample": 26.99, "traffic": 102.40e3, "pipe_busy": 0.784,
+    ("gauss3", "fp64"): {"kind": "fp64", "per_sample": 27.12, "traffic": 97.79e3, "pipe_busy": 0.785,
                          "source": "profiles/vsample_gauss3_fp64.md"},
-    ("table6", "fp64"): {"kind": "fp64", "per_sample": 43.25, "dram_bytes_per_sample": 409.2, "traffic": 38.5035e9,
-                         "pipe_busy": 0.706,
+    ("table6", "fp64"): {"kind": "fp64", "per_sample": 43.26, "dram_bytes_per_sample": 409.2, "traffic": 38.5035e9,
+                         "pipe_busy": 0.736,
                          "source": "profiles/vsample_table6_fp64.md"},
-    ("corner8", "mixed"): {"kind": "issue", "per_sample": 654.3, "traffic": 182.02e3, "fp32_flops": 101.41,
+    ("corner8", "mixed"): {"kind": "issue", "per_sample": 543.0, "traffic": 466.9e3, "fp32_flops": 99.23,
                            "source": "profiles/vsample_corner8_mixed.md"},
-    ("osc10", "mixed"): {"kind": "issue", "per_sample": 794.6, "traffic": 179.46e3, "fp32_flops": 135.11,
+    ("osc10", "mixed"): {"kind": "issue", "per_sample": 614.5, "traffic": 299.0e3, "fp32_flops": 131.80,
                          "source": "profiles/vsample_osc10_mixed.md"},
 }
 DFMA_PER_CLK_PER_SM = 2.0

@@ -206,6 +206,12 @@ void BatchEngine::release()
     h_segs_ = nullptr;
     h_small_ = nullptr;
     h_states_ = nullptr;
+    for (cudaStream_t s : branch_) cudaStreamDestroy(s);
+    for (cudaEvent_t v : join_) cudaEventDestroy(v);
+    if (fork_) cudaEventDestroy(fork_);
+    branch_.clear();
+    join_.clear();
+    fork_ = nullptr;
     capacity_ = 0;
 }
 
@@ -500,18 +506,46 @@ BatchRefineArgs BatchEngine::refine_args() const
     return r;
 }
 
-cudaError_t BatchEngine::enqueue_iteration(const ClassMask& mask)
+// The sampling kernels of the classes in the mask, each on its own branch
+// stream forked from stream_ and joined back into it: the kernels write
+// disjoint segments, and the blocks of one fill the SMs that another's
+// last blocks leave idle.
+cudaError_t BatchEngine::enqueue_sampling(const ClassMask& mask)
 {
+    cudaError_t e;
+    const size_t n = mask.count();
+    if (!fork_ && (e = cudaEventCreateWithFlags(&fork_, cudaEventDisableTiming))) return e;
+    while (branch_.size() < n) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t v = nullptr;
+        if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking))) return e;
+        branch_.push_back(s);
+        if ((e = cudaEventCreateWithFlags(&v, cudaEventDisableTiming))) return e;
+        join_.push_back(v);
+    }
+    if ((e = cudaEventRecord(fork_, stream_))) return e;
+    size_t k = 0;
+    cudaError_t le = cudaSuccess;
     for (int c = 0; c < kNumClasses; ++c) {
         if (!mask.test(c)) continue;
-        cudaError_t e = launch_vsample_batch(c, mixed_, sample_args(c), class_blocks(c), smem_bytes(c), stream_);
-        if (e) return e;
+        if ((e = cudaStreamWaitEvent(branch_[k], fork_, 0))) return e;
+        if (!le) le = launch_vsample_batch(c, mixed_, sample_args(c), class_blocks(c), smem_bytes(c), branch_[k]);
+        if ((e = cudaEventRecord(join_[k], branch_[k]))) return e;
+        if ((e = cudaStreamWaitEvent(stream_, join_[k], 0))) return e;
+        ++k;
     }
+    return le;
+}
+
+cudaError_t BatchEngine::enqueue_iteration(const ClassMask& mask)
+{
+    cudaError_t e = enqueue_sampling(mask);
+    if (e) return e;
     return launch_refine_batch(refine_args(), capacity_, 2 * num_sms_, stream_);
 }
 
 // One iteration as a CUDA graph: the sampling kernels of the classes in the
-// mask, then the refinement.  Re-captured only when a class appears that
+// mask as parallel branches, then the refinement.  Re-captured only when a class appears that
 // the graph does not launch, or the launch shape changes.
 cudaError_t BatchEngine::capture(ClassMask mask)
 {
@@ -588,10 +622,7 @@ cudaError_t BatchEngine::autotune(const std::vector<int>& live, const ClassMask&
             float ms = 1e30f;
             for (int rep = 0; rep < 4; ++rep) {  // the first launch warms up; the fastest of the rest counts
                 cudaEventRecord(e0, stream_);
-                for (int c = 0; c < kNumClasses && !e; ++c)
-                    if (mask.test(c))
-                        e = launch_vsample_batch(c, mixed_, sample_args(c), class_blocks(c), smem_bytes(c), stream_);
-                if (e) break;
+                if ((e = enqueue_sampling(mask))) break;
                 cudaEventRecord(e1, stream_);
                 if ((e = cudaEventSynchronize(e1))) break;
                 float t = 0.f;

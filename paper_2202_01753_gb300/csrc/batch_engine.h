@@ -97,6 +97,7 @@ private:
     cudaError_t upload_partition(const std::vector<int>& live, int nseg);
     BatchArgs sample_args(int cls) const;
     BatchRefineArgs refine_args() const;
+    cudaError_t enqueue_sampling(const ClassMask& class_mask);
     cudaError_t enqueue_iteration(const ClassMask& class_mask);
     cudaError_t capture(ClassMask class_mask);
     cudaError_t autotune(const std::vector<int>& live, const ClassMask& class_mask);
@@ -126,6 +127,11 @@ private:
     cudaGraphExec_t exec_ = nullptr;
     ClassMask graph_mask_;         // classes the captured graph launches
     int graph_bps_ = 0;
+    // one branch stream per class kernel of an iteration: forked from and
+    // joined back into stream_, so that the class kernels overlap
+    std::vector<cudaStream_t> branch_;
+    std::vector<cudaEvent_t> join_;
+    cudaEvent_t fork_ = nullptr;
 };
 
 }  // namespace mc

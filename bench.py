@@ -59,7 +59,7 @@ ROOFLINE_UNITS = {
                          "source": "profiles/vsample_table6_fp64.md"},
     ("corner8", "mixed"): {"kind": "issue", "per_sample": 543.0, "traffic": 466.9e3, "fp32_flops": 99.23,
                            "source": "profiles/vsample_corner8_mixed.md"},
-    ("osc10", "mixed"): {"kind": "issue", "per_sample": 614.5, "traffic": 299.0e3, "fp32_flops": 131.80,
+    ("osc10", "mixed"): {"kind": "issue", "per_sample": 665.7, "traffic": 299.0e3, "fp32_flops": 135.1,
                          "source": "profiles/vsample_osc10_mixed.md"},
 }
 DFMA_PER_CLK_PER_SM = 2.0

@@ -60,6 +60,36 @@ def test_batch_matches_solo(gpu_ctx_factory, precision, rtol):
         assert b["sigma"] == pytest.approx(s["sigma"], rel=rtol * 10)
 
 
+def _every_class(precision):
+    """One integral per batched kernel class: gauss / corner / osc at every
+    dimension 1..12, and in FP64 also the other batched families."""
+    rng = np.random.Generator(np.random.PCG64(15))
+    ws = [W.random_integral(rng, d, fam, 20_000, 3, seed=7500 + 3 * d + k)
+          for d in range(1, 13) for k, fam in enumerate((W.F_GAUSS, W.F_CORNER, W.F_OSC))]
+    if precision == "fp64":
+        ws += [W.suite(f, d, ncall=20_000, itmax=3, seed=7600 + d) for f in ("f2", "f5", "f6") for d in (1, 5)]
+        ws.append(W.cosmo6(seed=7700).scaled(30_000, itmax=3))
+    return ws
+
+
+@pytest.mark.parametrize("precision,rtol", [("fp64", 1e-10), ("mixed", 2e-4)])
+def test_batch_every_class_matches_solo(gpu_ctx_factory, precision, rtol):
+    """All class kernels of one iteration run as concurrent graph branches;
+    each integral still matches its solo run (disjoint segments, no
+    cross-talk between the classes)."""
+    ws = _every_class(precision)
+    ctx = gpu_ctx_factory(precision=precision)
+    out = ctx.integrate_batch([_req(w) for w in ws])
+    ctx.close()
+    for w, b in zip(ws, out):
+        s = _solo(gpu_ctx_factory, w, precision)
+        assert b["status"] == s["status"], w.name
+        assert b["iterations"] == s["iterations"] == 3
+        scale = max(abs(s["estimate"]), s["sigma"], 1e-9)
+        assert abs(b["estimate"] - s["estimate"]) <= rtol * scale, (w.name, b["estimate"], s["estimate"])
+        assert b["sigma"] == pytest.approx(s["sigma"], rel=rtol * 10), w.name
+
+
 def test_batch_fp64_against_oracle(gpu_ctx_factory):
     ws = _mix(6, seed=12, ncall_hi=1e5, itmax=4)
     ctx = gpu_ctx_factory()

@@ -409,6 +409,7 @@ void BatchEngine::partition(const std::vector<int>& live, int* nseg_out)
     uint32_t* live_slot = h_small_ + table_n;
     uint32_t* live_seg = live_slot + capacity_;
     std::memset(table, 0, sizeof(uint32_t) * table_n);
+    std::fill(class_load_, class_load_ + kNumClasses, 0.0);
     int nseg = 0;
     size_t hist_off = 0;
     size_t j = 0;
@@ -419,6 +420,7 @@ void BatchEngine::partition(const std::vector<int>& live, int* nseg_out)
         while (j1 < live.size() && batch_class(hdesc_[live[j1]].family, (int)hdesc_[live[j1]].d) == cls)
             total += slots_[live[j1++]].work;
         const int blocks = class_blocks(cls);
+        class_load_[cls] = total * (4.0 + hdesc_[live[j]].d) / blocks;
         uint32_t* blk_seg = table + (size_t)cls * (bmax_ + 1);
         const double chunk = total / blocks;
         double start = 0.0;  // first sample of the current integral on the class's line
@@ -523,11 +525,18 @@ cudaError_t BatchEngine::enqueue_sampling(const ClassMask& mask)
         if ((e = cudaEventCreateWithFlags(&v, cudaEventDisableTiming))) return e;
         join_.push_back(v);
     }
+    // the classes with the longest blocks first: the SMs their last blocks
+    // leave idle are filled by the shorter blocks of the classes after them
+    int order[kNumClasses];
+    int nc = 0;
+    for (int c = 0; c < kNumClasses; ++c)
+        if (mask.test(c)) order[nc++] = c;
+    std::stable_sort(order, order + nc, [&](int x, int y) { return class_load_[x] > class_load_[y]; });
     if ((e = cudaEventRecord(fork_, stream_))) return e;
     size_t k = 0;
     cudaError_t le = cudaSuccess;
-    for (int c = 0; c < kNumClasses; ++c) {
-        if (!mask.test(c)) continue;
+    for (int i = 0; i < nc; ++i) {
+        const int c = order[i];
         if ((e = cudaStreamWaitEvent(branch_[k], fork_, 0))) return e;
         if (!le) le = launch_vsample_batch(c, mixed_, sample_args(c), class_blocks(c), smem_bytes(c), branch_[k]);
         if ((e = cudaEventRecord(join_[k], branch_[k]))) return e;
@@ -664,7 +673,7 @@ cudaError_t BatchEngine::step(int* ran, int iters)
     live_slots(&live, &mask);
     if (live.empty()) return cudaSuccess;
     if ((e = autotune(live, mask))) return e;
-    if ((e = capture(mask))) return e;
+    if ((e = capture(mask))) return e;  // launch order by the class loads of the last partition
     int nseg = 0;
     partition(live, &nseg);
     if ((e = upload_partition(live, nseg))) return e;

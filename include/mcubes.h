@@ -192,8 +192,9 @@ mcubes_status mcubes_integrate(mcubes_ctx* ctx, int integrand_id, const double* 
                                int itmax, double rel_tol, double abs_tol, mcubes_result* out);
 
 /* n independent integrals, each with its own seed, iterated together: every
- * iteration of all live integrals is one persistent sampling launch and one
- * refinement launch, captured once as a CUDA graph and replayed.  Uses the
+ * iteration of all live integrals is one persistent sampling launch per
+ * kernel class (integrand family x dimension; the classes run concurrently)
+ * and one refinement launch, captured once as a CUDA graph and replayed.  Uses the
  * context's precision, nbins, ita (as a count) and alpha.  outs (host, n
  * entries) receives one result per request, each with its own status.
  * Returns OK if the batch ran (individual statuses are in outs), EINVAL if
@@ -205,7 +206,8 @@ mcubes_status mcubes_integrate_batch(mcubes_ctx* ctx, int n, const mcubes_reques
  * A server keeps up to `capacity` integration requests resident on the GPU,
  * each with its own grid, running sums and iteration index, and advances all
  * of them by one iteration per step: one persistent sampling launch per
- * integrand class and one refinement launch, replayed as a CUDA graph.
+ * kernel class (integrand family x dimension, run concurrently) and one
+ * refinement launch, replayed as a CUDA graph.
  * Requests submitted while others run wait in a FIFO queue and are admitted
  * as slots free up; finished requests (converged, itmax reached, or failed)
  * leave at once.  A request's samples do not depend on what else is

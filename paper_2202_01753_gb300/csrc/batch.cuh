@@ -17,9 +17,12 @@
 namespace mc {
 
 // One kernel per (family, dimension D): every segment it samples belongs to
-// an integral of that dimension.
+// an integral of that dimension.  Registers are bounded as for the
+// single-integral kernel of the same family and axis count (3 or 4 resident
+// blocks per SM), so that more blocks of the concurrently running classes
+// fit on an SM.
 template <int FAM, bool MIXED, int D>
-__global__ void __launch_bounds__(kVsThreads, 2)
+__global__ void __launch_bounds__(kVsThreads, vsample_min_blocks<FAM, MIXED, (D + 3) / 4>())
 vsample_batch_kernel(const __grid_constant__ BatchArgs a)
 {
     constexpr int NB4 = (D + 3) / 4;

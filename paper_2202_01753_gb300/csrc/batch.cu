@@ -241,6 +241,11 @@ cudaError_t BatchEngine::reserve(int capacity, int itcap)
     const size_t grid_stride = 2 * (size_t)kDMax * nb, hist_stride = (size_t)kDMax * nb;
     const size_t elem = mixed_ ? sizeof(float) : sizeof(double);
     const size_t table = (size_t)kNumClasses * (bmax_ + 1);
+    // partial histograms: an adjusting segment takes d * nb entries, and a
+    // class has at most one segment per integral plus one per boundary
+    // between its blocks (at most occ * SMs of them)
+    size_t hist_cap = (size_t)capacity * hist_stride;
+    for (int c = 0; c < kNumClasses; ++c) hist_cap += (size_t)occ_[c] * num_sms_ * (size_t)(c % kDMax + 1) * nb;
     if ((e = desc_.reserve(sizeof(BatchDesc) * capacity)) || (e = st_.reserve(sizeof(BatchState) * capacity)) ||
         (e = grids_.reserve(sizeof(double) * grid_stride * capacity)) ||
         (e = cells_.reserve(cell_bytes(mixed_) * hist_stride * capacity)) ||
@@ -250,7 +255,7 @@ cudaError_t BatchEngine::reserve(int capacity, int itcap)
         (e = live_.reserve(sizeof(uint32_t) * capacity)) ||
         (e = live_seg_.reserve(sizeof(uint32_t) * (capacity + 1))) || (e = nlive_.reserve(sizeof(uint32_t))) ||
         (e = seg_part_.reserve(sizeof(double) * 3 * segmax)) ||
-        (e = seg_hist_.reserve(elem * hist_stride * segmax)) ||
+        (e = seg_hist_.reserve(elem * hist_cap)) ||
         (e = admit_slots_.reserve(sizeof(uint32_t) * capacity)))
         return e;
     if ((e = cudaHostAlloc((void**)&h_segs_, sizeof(BatchSeg) * segmax, cudaHostAllocDefault)) ||
@@ -260,6 +265,7 @@ cudaError_t BatchEngine::reserve(int capacity, int itcap)
         return e;
     capacity_ = capacity;
     itcap_ = itcap;
+    hist_cap_ = hist_cap;
     slots_.assign(capacity, Slot{});
     hdesc_.assign(capacity, BatchDesc{});
     free_.clear();
@@ -457,12 +463,14 @@ void BatchEngine::partition(const std::vector<int>& live, int* nseg_out)
         while (b < blocks) blk_seg[++b] = (uint32_t)nseg;
     }
     live_seg[live.size()] = (uint32_t)nseg;
+    part_hist_ = hist_off;
     *nseg_out = nseg;
 }
 
 cudaError_t BatchEngine::upload_partition(const std::vector<int>& live, int nseg)
 {
     cudaError_t e;
+    if (part_hist_ > hist_cap_) return cudaErrorInvalidValue;  // never: hist_cap_ bounds every partition
     const size_t table_n = (size_t)kNumClasses * (bmax_ + 1);
     const uint32_t* live_slot = h_small_ + table_n;
     const uint32_t* live_seg = live_slot + capacity_;

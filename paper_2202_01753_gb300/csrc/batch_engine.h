@@ -111,6 +111,8 @@ private:
     int capacity_ = 0, itcap_ = 0;
     int occ_[kNumClasses] = {0};   // resident blocks per SM of each class's kernel
     int bmax_ = 0;                 // most blocks any class launches
+    size_t hist_cap_ = 0;          // entries of the partial-histogram buffer
+    size_t part_hist_ = 0;         // entries the last partition uses
     double class_load_[kNumClasses] = {0};  // a class's work per block in the last partition (launch order)
     bool tuned_ = false;
     int tuned_bps_ = 1, lanes_cap_ = 64;

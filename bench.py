@@ -543,7 +543,9 @@ def serve_arm(args):
     ctx = mcubes.Context(local, precision="mixed")
     srv = mcubes.Server(ctx, itcap=max(w.itmax for w in ws))
     srv.set_step_iterations(args.serve_iters)
-    srv.run_stream(reqs[:200], arrival[:200] - arrival[0])         # warm-up: autotune, graph capture
+    # warm-up: modules loaded, graphs captured for the classes seen (the tuner
+    # waits for 32 live integrals, more than this stream usually holds at once)
+    srv.run_stream(reqs[:200], arrival[:200] - arrival[0])
     clocks = ClockSampler(local)
     clocks.start()
     res, lat, wall = srv.run_stream(reqs, arrival)

@@ -76,3 +76,12 @@ def test_exp_accuracy_host(fxhost):
     # exp(y) for y < -745.2 (to -inf) is +0 exactly
     _, z = fxhost([745.3, 800.0, 1e5, 1e300, math.inf])
     assert np.all(z == 0.0) and not np.any(np.signbit(z))
+
+
+def test_tables_header_is_generated():
+    """csrc/fx_tables.h is exactly what gen_fx_tables.py computes from the
+    constants' definitions (60-digit arithmetic, rounded once): no entry is
+    edited by hand."""
+    from paper_2202_01753_gb300 import gen_fx_tables as G
+    with open(G.OUT) as f:
+        assert f.read() == G.render()

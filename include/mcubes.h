@@ -202,6 +202,15 @@ mcubes_status mcubes_integrate(mcubes_ctx* ctx, int integrand_id, const double* 
 mcubes_status mcubes_integrate_batch(mcubes_ctx* ctx, int n, const mcubes_request* reqs,
                                      mcubes_result* outs);
 
+/* Integral i of the last mcubes_integrate_batch call on this context: its
+ * per-iteration estimates and variances (host arrays of cap entries; *n
+ * receives the number of iterations run), its final grid ([d][nb] right
+ * edges, host, may be NULL) and the per-bin sums of f^2 of its last
+ * adjusting iteration ([d][nb], host, may be NULL).  Valid until the next
+ * batched call on the context.  Errors: EINVAL (no such integral). */
+mcubes_status mcubes_batch_trace_get(mcubes_ctx* ctx, int i, double* I_it, double* var_it, int cap, int* n,
+                                     double* grid, double* C);
+
 /* ---- continuous-batching server ------------------------------------------
  * A server keeps up to `capacity` integration requests resident on the GPU,
  * each with its own grid, running sums and iteration index, and advances all
@@ -225,7 +234,8 @@ mcubes_status mcubes_server_create(mcubes_server** out, mcubes_ctx* ctx, long lo
 mcubes_status mcubes_server_destroy(mcubes_server* srv);
 
 /* Queues one request (host arrays, copied); tag identifies its result.
- * EINVAL if the request is invalid (nothing is queued). */
+ * Tags from 2^62 up are reserved for mcubes_server_run_stream.  EINVAL if
+ * the request is invalid or the tag reserved (nothing is queued). */
 mcubes_status mcubes_server_submit(mcubes_server* srv, const mcubes_request* req, long long tag);
 
 /* Admits queued requests into free slots, runs one iteration (or the number
@@ -244,6 +254,15 @@ mcubes_status mcubes_server_step(mcubes_server* srv, int* ran);
 #define MCUBES_STEP_ITERS_MAX 64
 mcubes_status mcubes_server_set_step_iterations(mcubes_server* srv, int iters);
 
+/* Retries for requests that reach their itmax without converging (the
+ * accuracy protocol of Sec. 5.1 raises the number of samples for tighter
+ * tolerances): such a request is queued again, ahead of new arrivals, with
+ * factor times its calls per iteration and a fresh start, while that stays
+ * at or below ncall_max; its result is that of its last run, and a caller
+ * sees only that one.  factor = 1 (the default) disables retries.  Errors:
+ * EINVAL (factor outside [1, 1024], ncall_max < 0). */
+mcubes_status mcubes_server_set_escalation(mcubes_server* srv, double factor, long long ncall_max);
+
 /* Copies up to cap finished results (and their tags) not yet returned;
  * *n receives how many were copied. */
 mcubes_status mcubes_server_poll(mcubes_server* srv, long long* tags, mcubes_result* results, int cap, int* n);
@@ -258,7 +277,11 @@ mcubes_status mcubes_server_stats(mcubes_server* srv, long long* queued, long lo
  * queues arrivals, admits, steps and retires until every request is done.
  * results[i] receives request i's result and latency_s[i] the time from its
  * arrival to the end of the step that finished it; *wall_s the duration of
- * the whole call.  Errors: EINVAL, ENOMEM, ECUDA. */
+ * the whole call.  The call tags its requests from 2^62 up, a new range per
+ * call; requests another call of it left behind (it returned an error) are
+ * dropped or, once finished, discarded.  Requests queued by
+ * mcubes_server_submit are served alongside and stay pollable.  Errors:
+ * EINVAL, ENOMEM, ECUDA. */
 mcubes_status mcubes_server_run_stream(mcubes_server* srv, int n, const mcubes_request* reqs,
                                        const double* arrival_s, mcubes_result* results, double* latency_s,
                                        double* wall_s);
@@ -354,16 +377,54 @@ mcubes_status mcubes_state_import(mcubes_ctx* ctx, const void* buf, long long si
 mcubes_status mcubes_sample_range(mcubes_ctx* ctx, unsigned it, int adjust, long long cube_begin,
                                   long long cube_end, double* sums, double* C);
 
+/* ---- one integral over several GPUs: cube-range shards -------------------
+ * Alg. 3 reduces every block's results (the cube means and variances, and
+ * the bin contributions C) into one iteration result, and Alg. 2's host
+ * loop refines the grid from them.  Splitting the sub-cubes [0, m) into
+ * contiguous ranges, one per GPU, makes that reduction the only exchange:
+ * every rank sets up the same problem with the same options (seed
+ * included), samples its range -- the samples are keyed by the global cube
+ * index, so the ranges together draw exactly one iteration's samples -- and
+ * all ranks combine the gathered partials in rank order, so each runs the
+ * identical rebinning and weighting with no broadcast of the grid.
+ *
+ * A rank's partial is MCUBES_SHARD_HEAD + hist_d * nb doubles: the sum of
+ * its cube means, of the variances of those means, of |cube means|, then
+ * the per-bin sums of f^2 [hist_d][nb] (zero in non-adjusting iterations;
+ * hist_d = d, or 1 in m-Cubes1D).  mcubes_shard_partial_len gives the
+ * length for the current problem. */
+#define MCUBES_SHARD_HEAD 3
+mcubes_status mcubes_shard_partial_len(mcubes_ctx* ctx, long long* len);
+
+/* The sampling pass of the context's next iteration over sub-cubes
+ * [cube_begin, cube_end) (any range, empty included), its partial written
+ * to the device array d_partial.  Enqueued on the context's stream; returns
+ * without waiting.  After an iteration that converged the pass does no
+ * work and its partial is not meaningful (mcubes_shard_finish ignores it).
+ * Errors: EINVAL (range, null), ESTATE (no setup, or every iteration
+ * enqueued), ECUDA. */
+mcubes_status mcubes_shard_sample(mcubes_ctx* ctx, long long cube_begin, long long cube_end, double* d_partial);
+
+/* Finishes the iteration sampled by mcubes_shard_sample from nranks
+ * partials gathered in rank order (device array [nranks][len]): they are
+ * summed element by element in rank order, then the iteration's estimate
+ * and variance are recorded, the grid is rebinned (adjusting iterations)
+ * and all iterations are weighed and tested for convergence, as
+ * mcubes_iterate does after its own pass.  Ranks that pass the same
+ * gathered array end with identical state.  Enqueued on the context's
+ * stream.  Errors: EINVAL (nranks < 1, null), ESTATE (no sampled
+ * iteration to finish), ECUDA. */
+mcubes_status mcubes_shard_finish(mcubes_ctx* ctx, const double* d_gathered, int nranks);
+
 /* ---- sampling without device allocation ----------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
- * that cannot allocate device memory: code that runs while its stream is
- * being captured into a CUDA graph (cudaMalloc cannot be captured), hosts
- * whose device memory belongs to another allocator (a framework's caching
- * pool, a fixed arena in an embedded or real-time service), and processes
- * that must not grow their device footprint once running.
+ * that cannot allocate device memory: hosts whose device memory belongs to
+ * another allocator (a framework's caching pool, a fixed arena in an
+ * embedded or real-time service), and processes that must not grow their
+ * device footprint, or stall on an allocation, once running.
  *
- * One sampling pass (Alg. 3) over sub-cubes [cube_begin, cube_end) of
- * iteration `it`, as mcubes_sample_range does, but with no context: the
+ * The same sampling pass as mcubes_sample_range, over sub-cubes
+ * [cube_begin, cube_end) of iteration `it`, but with no context: the
  * problem is given directly (params, lo, hi are host arrays of nparams and d
  * values; nbins, g_override, seed and precision as in mcubes_opts), the grid
  * is read from the caller's device array d_grid ([d][nbins] right edges,
@@ -371,7 +432,9 @@ mcubes_status mcubes_sample_range(mcubes_ctx* ctx, unsigned it, int adjust, long
  * (3 values: sum of cube means, of their variances, of |cube means|) and,
  * when adjust != 0, d_hist ([d][nbins] per-bin sums of f^2; may be NULL
  * otherwise).  Work is enqueued on cuda_stream (NULL = legacy default
- * stream) and the call returns without waiting.
+ * stream) and the call returns without waiting.  It launches at most
+ * MCUBES_NOALLOC_MAX_BLOCKS blocks, so its sums are grouped differently from
+ * mcubes_sample_range's: the two agree to rounding, not bit for bit.
  *
  * It allocates nothing: the per-block partial sums and the histogram
  * accumulator live in one static device array of the library,

@@ -741,6 +741,22 @@ void BatchEngine::finished(std::vector<std::pair<long long, mcubes_result>>* out
     }
 }
 
+cudaError_t BatchEngine::read_slot(int slot, double* I, double* V, int cap, int* n, double* grid, double* hist)
+{
+    const BatchDesc& D = hdesc_[slot];
+    const int k = std::min(cap, slots_[slot].result.iterations);
+    cudaError_t e = cudaSuccess;
+    if (I && k > 0 && (e = cudaMemcpyAsync(I, D.hist_I, sizeof(double) * k, cudaMemcpyDeviceToHost, stream_)))
+        return e;
+    if (V && k > 0 && (e = cudaMemcpyAsync(V, D.hist_V, sizeof(double) * k, cudaMemcpyDeviceToHost, stream_)))
+        return e;
+    const size_t bins = (size_t)D.d * D.nb;
+    if (grid && (e = cudaMemcpyAsync(grid, D.grid, sizeof(double) * bins, cudaMemcpyDeviceToHost, stream_))) return e;
+    if (hist && (e = cudaMemcpyAsync(hist, D.hist, sizeof(double) * bins, cudaMemcpyDeviceToHost, stream_))) return e;
+    if (n) *n = slots_[slot].result.iterations;
+    return cudaStreamSynchronize(stream_);
+}
+
 int BatchEngine::resident() const
 {
     int n = 0;

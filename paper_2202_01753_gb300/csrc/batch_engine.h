@@ -73,6 +73,12 @@ public:
     // with free_slots their slots become free for new admissions.
     void finished(std::vector<std::pair<long long, mcubes_result>>* out, bool free_slots);
 
+    // Copies a slot's iteration estimates and variances (up to cap each; *n
+    // receives the number recorded), its grid ([d][nb] edge high parts) and
+    // the histogram of its last adjusting iteration ([d][nb]) to host arrays
+    // (any may be null).  Valid for a finished slot until it is reused.
+    cudaError_t read_slot(int slot, double* I, double* V, int cap, int* n, double* grid, double* hist);
+
     int tuned_blocks_per_sm() const { return tuned_bps_; }
     int lanes_cap() const { return lanes_cap_; }
 

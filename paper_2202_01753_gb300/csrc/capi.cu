@@ -542,15 +542,18 @@ mcubes_status mcubes_setup(mcubes_ctx* c, int id, const double* params, int npar
     }
     c->grid_adj = occ_adj * c->num_sms;
     c->grid_noadj = occ_noadj * c->num_sms;
-    const long long resident = (long long)std::max(occ_adj, occ_noadj) * c->num_sms * kVsThreads;
+    c->grid_res_adj = c->grid_adj;
+    c->grid_res_noadj = c->grid_noadj;
+    const int threads = vsample_threads(id, c->mixed, d);
+    const long long resident = (long long)std::max(occ_adj, occ_noadj) * c->num_sms * threads;
     c->lanes = c->opts.lanes_per_cube > 0 ? c->opts.lanes_per_cube : choose_lanes(m, p, resident);
     // Cube-split mode: when the cubes cannot keep a quarter of the resident
     // threads busy (few cubes with many samples each), several blocks share
     // one cube, so that about two waves of blocks sample every iteration.
     c->split = 1;
-    if (c->opts.lanes_per_cube == 0 && m * c->lanes * 4 < resident && p >= 2 * kVsThreads) {
+    if (c->opts.lanes_per_cube == 0 && m * c->lanes * 4 < resident && p >= 2 * threads) {
         const long long want = (2LL * std::max(c->grid_adj, c->grid_noadj) + m - 1) / m;
-        c->split = (int)std::max(1LL, std::min(want, p / kVsThreads));
+        c->split = (int)std::max(1LL, std::min(want, p / threads));
         if (c->split > 1) c->grid_adj = c->grid_noadj = (int)(m * c->split);
     }
     const int grid_max = std::max(c->grid_adj, c->grid_noadj);
@@ -637,6 +640,7 @@ mcubes_status mcubes_setup(mcubes_ctx* c, int id, const double* params, int npar
     c->rel_tol = rel_tol;
     c->abs_tol = abs_tol;
     c->it_enqueued = 0;
+    c->shard_open = false;
     c->ready = true;
     return MCUBES_OK;
 }
@@ -644,7 +648,7 @@ mcubes_status mcubes_setup(mcubes_ctx* c, int id, const double* params, int npar
 mcubes_status mcubes_iterate(mcubes_ctx* c, int n_iter)
 {
     if (!c) return MCUBES_EINVAL;
-    if (!c->ready || n_iter < 0 || c->it_enqueued + n_iter > c->itmax) return MCUBES_ESTATE;
+    if (!c->ready || n_iter < 0 || c->it_enqueued + n_iter > c->itmax || c->shard_open) return MCUBES_ESTATE;
     MC_CHECK(c, cudaSetDevice(c->device));
     for (int i = 0; i < n_iter; ++i) {
         const bool adjust = c->it_enqueued < c->ita;
@@ -802,6 +806,79 @@ mcubes_status mcubes_sample_range(mcubes_ctx* c, unsigned it, int adjust, long l
     return MCUBES_OK;
 }
 
+mcubes_status mcubes_shard_partial_len(mcubes_ctx* c, long long* len)
+{
+    if (!c || !len) return MCUBES_EINVAL;
+    if (!c->ready) return MCUBES_ESTATE;
+    *len = MCUBES_SHARD_HEAD + (long long)c->hist_d * c->nb;
+    return MCUBES_OK;
+}
+
+// A rank's share of the next iteration: the iteration's own sampling launch
+// (device state: iteration index, the skip after convergence) over a cube
+// range, whose block partials and histogram are then reduced into the
+// caller's partial instead of into the iteration.
+mcubes_status mcubes_shard_sample(mcubes_ctx* c, long long cube_begin, long long cube_end, double* d_partial)
+{
+    if (!c || !d_partial) return MCUBES_EINVAL;
+    if (!c->ready || c->shard_open || c->it_enqueued >= c->itmax) return MCUBES_ESTATE;
+    if (cube_begin < 0 || cube_end < cube_begin || cube_end > c->m) return MCUBES_EINVAL;
+    MC_CHECK(c, cudaSetDevice(c->device));
+    const bool adjust = c->it_enqueued < c->ita;
+    VsArgs a = c->vs;
+    a.split = 1;  // a range pass: the partials are sums over whole cubes
+    a.cube_begin = (uint64_t)cube_begin;
+    a.cube_end = (uint64_t)cube_end;
+    a.perm_k = cube_permutation((uint64_t)(cube_end - cube_begin));
+    const int grid = adjust ? c->grid_res_adj : c->grid_res_noadj;
+    const size_t smem = adjust ? c->smem_adj : c->smem_noadj;
+    EventPair ev;
+    if (c->timing) {
+        ev = take_events(c);
+        MC_CHECK(c, cudaEventRecord(ev.a, c->stream));
+    }
+    MC_CHECK(c, launch_vsample(c->fid, c->mixed, adjust, a, grid, smem, c->stream));
+    if (c->timing) {
+        MC_CHECK(c, cudaEventRecord(ev.b, c->stream));
+        c->ev_sample.push_back(ev);
+    }
+    if (!adjust)
+        MC_CHECK(c, cudaMemsetAsync(d_partial + MCUBES_SHARD_HEAD, 0, sizeof(double) * c->hist_d * c->nb,
+                                    c->stream));
+    MC_CHECK(c, launch_reduce_range((const double*)c->part.ptr, (double*)c->hist_acc.ptr, grid, c->hist_d, c->nb,
+                                    adjust ? 1 : 0, d_partial, d_partial + MCUBES_SHARD_HEAD, c->stream));
+    c->shard_open = true;
+    c->shard_adjust = adjust;
+    return MCUBES_OK;
+}
+
+mcubes_status mcubes_shard_finish(mcubes_ctx* c, const double* d_gathered, int nranks)
+{
+    if (!c || !d_gathered || nranks < 1) return MCUBES_EINVAL;
+    if (!c->ready || !c->shard_open) return MCUBES_ESTATE;
+    MC_CHECK(c, cudaSetDevice(c->device));
+    const int len = MCUBES_SHARD_HEAD + c->hist_d * c->nb;
+    MC_CHECK(c, launch_combine_shards(d_gathered, nranks, len, (double*)c->part.ptr, (double*)c->hist_acc.ptr,
+                                      c->stream));
+    RefineArgs r = c->rf;
+    r.nblocks = 1;  // the combined sums, as one block's partial
+    r.split = 1;
+    r.adjust = c->shard_adjust ? 1 : 0;
+    EventPair ev;
+    if (c->timing) {
+        ev = take_events(c);
+        MC_CHECK(c, cudaEventRecord(ev.a, c->stream));
+    }
+    MC_CHECK(c, launch_refine(r, c->stream));
+    if (c->timing) {
+        MC_CHECK(c, cudaEventRecord(ev.b, c->stream));
+        c->ev_refine.push_back(ev);
+    }
+    ++c->it_enqueued;
+    c->shard_open = false;
+    return MCUBES_OK;
+}
+
 mcubes_status mcubes_geometry_get(mcubes_ctx* c, long long* g, long long* m, long long* p, int* lanes,
                                   int* blocks)
 {
@@ -865,13 +942,17 @@ mcubes_status mcubes_integrate_batch(mcubes_ctx* c, int n, const mcubes_request*
     if (!c->engine) return MCUBES_ENOMEM;
     BatchEngine& E = *c->engine;
     MC_CHECK(c, E.reserve(std::max(n, E.capacity()), std::max(itcap, E.itcap())));
+    c->batch_slots.assign(n, -1);
+    c->batch_dims.assign(n, 0);
     for (int i = 0; i < n; ++i) {
-        const mcubes_status st = E.admit(reqs[i], i);
+        c->batch_dims[i] = reqs[i].d;
+        const mcubes_status st = E.admit(reqs[i], i, &c->batch_slots[i]);
         if (st != MCUBES_OK) {
             // nothing has run: drop what was admitted
             std::vector<std::pair<long long, mcubes_result>> none;
             delete c->engine;
             c->engine = nullptr;
+            c->batch_slots.clear();
             return st;
         }
     }
@@ -880,6 +961,16 @@ mcubes_status mcubes_integrate_batch(mcubes_ctx* c, int n, const mcubes_request*
     std::vector<std::pair<long long, mcubes_result>> done;
     E.finished(&done, true);
     for (auto& kv : done) outs[kv.first] = kv.second;
+    return MCUBES_OK;
+}
+
+mcubes_status mcubes_batch_trace_get(mcubes_ctx* c, int i, double* I_it, double* var_it, int cap, int* n,
+                                     double* grid, double* C)
+{
+    if (!c || cap < 0 || (cap > 0 && (!I_it || !var_it))) return MCUBES_EINVAL;
+    if (!c->engine || i < 0 || i >= (int)c->batch_slots.size() || c->batch_slots[i] < 0) return MCUBES_EINVAL;
+    MC_CHECK(c, cudaSetDevice(c->device));
+    MC_CHECK(c, c->engine->read_slot(c->batch_slots[i], I_it, var_it, cap, n, grid, C));
     return MCUBES_OK;
 }
 

@@ -39,6 +39,9 @@ struct mcubes_ctx {
     int split = 1;    // blocks per cube (cube-split mode when > 1)
     int lanes = 1;
     int grid_adj = 0, grid_noadj = 0;
+    int grid_res_adj = 0, grid_res_noadj = 0;  // resident blocks x SMs (cube-range passes)
+    bool shard_open = false;                    // a shard pass is enqueued and not finished
+    bool shard_adjust = false;
     size_t smem_adj = 0, smem_noadj = 0;
     int it_enqueued = 0;
     mc::VsArgs vs{};
@@ -53,6 +56,8 @@ struct mcubes_ctx {
     std::vector<mc::TableDesc> tabs_host;  // descriptors as uploaded (device pointers)
 
     mc::BatchEngine* engine = nullptr;  // batched path, created on first use
+    std::vector<int> batch_slots;       // engine slot of each request of the last mcubes_integrate_batch
+    std::vector<int> batch_dims;        // and its dimension
 
     bool timing = false;
     std::vector<mc::EventPair> ev_sample, ev_refine;

@@ -117,14 +117,19 @@ __device__ __forceinline__ double fx_log(double x)
 __device__ __forceinline__ double fx_exp_bits(uint64_t u)
 {
     const double y = __longlong_as_double((long long)u);
-    const uint64_t ay = u & 0x7FFFFFFFFFFFFFFFull;
-    if (ay >= 0x4086200000000000ull) {  // |y| >= 708, infinite or NaN
-        // y < -745.2 (down to -inf): exp(y) < 2^-1075 rounds to +0.  Integrands
-        // with narrow peaks land here often, so it takes no FP64 work; the
-        // rest (overflow, subnormal results, NaN) is CUDA's exp.
-        if ((u >> 63) && ay > 0x408749999999999Aull && ay <= 0x7FF0000000000000ull) return 0.0;
-        return exp_slow(y);
+    uint64_t ay = u & 0x7FFFFFFFFFFFFFFFull;
+    // y < -745.2 (down to -inf): exp(y) < 2^-1075 rounds to +0.  Integrands
+    // with narrow peaks land here for a large share of their samples, so
+    // this case takes no branch: the argument is replaced by -1 and the
+    // result by +0 at the end.  (A divergent early return would split the
+    // warp, and code after the call, on the FP64 pipe, would run once per
+    // side with part of the lanes.)
+    const bool under = (u >> 63) && ay > 0x408749999999999Aull && ay <= 0x7FF0000000000000ull;
+    if (under) {
+        u = 0xBFF0000000000000ull;
+        ay = 0x3FF0000000000000ull;
     }
+    if (ay >= 0x4086200000000000ull) return exp_slow(y);  // overflow, subnormal results, NaN: CUDA's exp
     if (ay < 0x3C30000000000000ull) return 1.0;  // |y| < 2^-60: exp(y) rounds to 1
     // y = n ln2/256 + r, n = round(y 256/ln2) from y's significand M and
     // exponent E: |y| 256/ln2 = H 2^(E-1075) to 2^-52 relative, H =
@@ -176,7 +181,7 @@ __device__ __forceinline__ double fx_exp_bits(uint64_t u)
         bits = ((uint64_t)(k + 1023) << 52) + (((P + (1ull << 9)) >> 10) - (1ull << 52));
     else
         bits = ((uint64_t)(k + 1022) << 52) + (((P + (1ull << 8)) >> 9) - (1ull << 52));
-    return __longlong_as_double((long long)bits);
+    return __longlong_as_double((long long)(under ? 0ull : bits));
 }
 
 __device__ __forceinline__ double fx_exp(double y) { return fx_exp_bits((uint64_t)__double_as_longlong(y)); }

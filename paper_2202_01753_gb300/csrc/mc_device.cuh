@@ -370,6 +370,9 @@ template <typename R> struct Family<MCUBES_F_COSMO6, R> {
     // pipe that bounds these kernels.  Single precision keeps the factored
     // form (its rounding would not survive the expansion's cancellation).
     static constexpr bool kWide = sizeof(R) == 8;
+    // a logarithm per axis: the FP64 sampling loop runs its axes as a loop
+    // (one copy of the per-axis code) instead of unrolling them
+    static constexpr bool kRolled = kWide;
     struct S { R e; R x12; };
     __device__ static void begin(S& s) { s.e = R(0); s.x12 = R(0); }
     __device__ static void add(S& s, int j, R x, const FamParams& f)

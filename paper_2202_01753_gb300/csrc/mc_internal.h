@@ -15,7 +15,24 @@ constexpr int kDMax = MCUBES_DMAX;
 constexpr int kNbMax = MCUBES_NBMAX;
 constexpr int kParMax = MCUBES_PARAMS_MAX;
 constexpr int kItMax = MCUBES_ITMAX_MAX;
-constexpr int kVsThreads = 256;    // sampling block size (8 warps)
+constexpr int kVsThreads = 256;    // sampling block size (8 warps); batched kernels
+constexpr int kVsThreadsMax = 1024; // largest block of a single-integral sampling kernel
+
+#ifndef MC_COSMO6_THREADS
+#define MC_COSMO6_THREADS 1024
+#endif
+#ifndef MC_COSMO6_MINB
+#define MC_COSMO6_MINB 1
+#endif
+// Block size of a single-integral sampling kernel.  Its warps hide the
+// latency of a serial chain per sample, so resident warps count: the
+// registers a kernel needs bound them (65536 per SM), and a block size that
+// fills that bound beats 256-thread blocks whose count per SM is capped by
+// shared memory (three blocks of the FP64 six-axis grid and histogram).
+__host__ __device__ constexpr int vsample_threads(int family, bool mixed, int d)
+{
+    return (family == MCUBES_F_COSMO6 && !mixed && d == 6) ? MC_COSMO6_THREADS : kVsThreads;
+}
 constexpr int kRefineThreads = 512;
 
 // Shared-memory bytes per bin of the sampling kernels: a grid cell (left
@@ -231,5 +248,9 @@ cudaError_t launch_refine(const RefineArgs& a, cudaStream_t s);
 cudaError_t launch_reduce_range(const double* part, double* hist_acc, int nblocks, int d, int nb, int adjust,
                                 double* out_sums, double* out_hist, cudaStream_t s);
 cudaError_t launch_init_grid(double* grid, double* grid_lo, int d, int nb, cudaStream_t s);
+// Sums nranks partials ([nranks][len], rank order) element by element in rank
+// order: the first MCUBES_SHARD_HEAD sums go to part[0..], the rest to hist.
+cudaError_t launch_combine_shards(const double* gathered, int nranks, int len, double* part, double* hist,
+                                  cudaStream_t s);
 
 }  // namespace mc

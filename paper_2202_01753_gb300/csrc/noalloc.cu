@@ -1,12 +1,12 @@
 // noalloc.cu -- one sampling pass over a cube range that allocates no device
-// memory, for callers that cannot call cudaMalloc: code running while a CUDA
-// stream is being captured into a graph (allocation is not a capturable
-// operation), hosts whose device memory is owned by another allocator (a
-// framework's caching pool, a fixed arena in an embedded or real-time
-// service), and processes that must not grow their device footprint after
-// start-up.  The kernels are the ones mcubes_sample_range launches; only the
-// per-block partial sums live in a static device array of this file instead
-// of a context's buffers.
+// memory, for callers that cannot call cudaMalloc: hosts whose device memory
+// is owned by another allocator (a framework's caching pool, a fixed arena in
+// an embedded or real-time service), and processes that must not grow their
+// device footprint, or stall on an allocation, once running.  The kernels are
+// the ones mcubes_sample_range launches; only the per-block partial sums and
+// the histogram accumulator live in a static device array of this file
+// instead of a context's buffers.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -92,14 +92,16 @@ extern "C" mcubes_status mcubes_sample_range_noalloc(
         double* grid_lo = reinterpret_cast<double*>(scratch + kPartBytes + kHistBytes);
 
         const size_t smem = vsample_smem_bytes(mixed, adj, d, nbins, d);
-        int smem_limit = 0, sms = 0, occ = 0;
+        const size_t smem_other = vsample_smem_bytes(mixed, !adj, d, nbins, d);
+        int smem_limit = 0, sms = 0, occ = 0, occ_other = 0;
         if (cudaDeviceGetAttribute(&smem_limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
             st = MCUBES_ECUDA;
             break;
         }
         if (smem + 1024 > (size_t)smem_limit) { st = MCUBES_EINVAL; break; }
-        if (vsample_occupancy(integrand_id, mixed, adj, d, smem, &occ) != cudaSuccess || occ < 1) {
+        if (vsample_occupancy(integrand_id, mixed, adj, d, smem, &occ) != cudaSuccess || occ < 1 ||
+            vsample_occupancy(integrand_id, mixed, !adj, d, smem_other, &occ_other) != cudaSuccess) {
             st = MCUBES_ECUDA;
             break;
         }
@@ -119,8 +121,13 @@ extern "C" mcubes_status mcubes_sample_range_noalloc(
         a.g = (uint32_t)g;
         a.gmagic = (uint32_t)(0xFFFFFFFFu / (uint32_t)g);
         a.p = (uint32_t)p;
-        int lanes = 1;  // same rule as a context's automatic choice
-        const long long resident = (long long)occ * sms * kVsThreads;
+        // lanes per cube: a context's default rule, from the residency of both
+        // the adjusting and the plain kernel.  The block count differs (at most
+        // kMaxBlocks here), so the cubes' sums are grouped into other block
+        // partials: results agree with mcubes_sample_range to rounding, not
+        // bit for bit.
+        int lanes = 1;
+        const long long resident = (long long)std::max(occ, occ_other) * sms * vsample_threads(integrand_id, mixed, d);
         while (lanes < 32 && 2 * lanes <= p && (m * lanes < 4 * resident || p / lanes > 64)) lanes *= 2;
         a.lanes = (uint32_t)lanes;
         a.hist_d = (uint32_t)d;

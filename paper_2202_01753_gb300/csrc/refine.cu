@@ -172,6 +172,19 @@ reduce_range_kernel(const double* part, double* hist_acc, int nblocks, int d, in
     }
 }
 
+// Rank-order sum of gathered shard partials (mcubes_shard_finish): one
+// thread per element, the ranks added in order 0, 1, ... so that every rank
+// that combines the same gathered array gets the same bits.
+__global__ void combine_shards_kernel(const double* gathered, int nranks, int len, double* part, double* hist)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= len) return;
+    double s = gathered[i];
+    for (int r = 1; r < nranks; ++r) s += gathered[(size_t)r * len + i];
+    if (i < MCUBES_SHARD_HEAD) part[i] = s;
+    else hist[i - MCUBES_SHARD_HEAD] = s;
+}
+
 // Map cells of the whole grid (set-up, and after the grid is replaced).
 __global__ void cells_kernel(const double* grid, const double* grid_lo, CellBox box, int d, int nb, void* out)
 {
@@ -217,6 +230,13 @@ cudaError_t launch_reduce_range(const double* part, double* hist_acc, int nblock
     const int blocks = (adjust ? d : 0) + 1;
     reduce_range_kernel<<<blocks, kRefineThreads, 0, s>>>(part, hist_acc, nblocks, d, nb, adjust, out_sums,
                                                           out_hist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine_shards(const double* gathered, int nranks, int len, double* part, double* hist,
+                                  cudaStream_t s)
+{
+    combine_shards_kernel<<<(len + 255) / 256, 256, 0, s>>>(gathered, nranks, len, part, hist);
     return cudaGetLastError();
 }
 

@@ -8,6 +8,7 @@
 #include <deque>
 #include <new>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "ctx_internal.h"
@@ -30,6 +31,22 @@ struct Queued {
         r.lo = lo.data();
         r.hi = hi.data();
     }
+    // copies point r at their own arrays
+    Queued(const Queued& o) : Queued(o.r, o.tag) {}
+    Queued& operator=(const Queued& o)
+    {
+        if (this != &o) {
+            r = o.r;
+            params = o.params;
+            lo = o.lo;
+            hi = o.hi;
+            tag = o.tag;
+            r.params = params.data();
+            r.lo = lo.data();
+            r.hi = hi.data();
+        }
+        return *this;
+    }
 };
 
 }  // namespace
@@ -37,12 +54,58 @@ struct Queued {
 struct mcubes_server {
     mcubes_ctx* ctx = nullptr;
     BatchEngine* engine = nullptr;
+    // Queued and resident requests carry an internal id (their engine tag);
+    // `open` maps it to the caller's tag and keeps the request for a retry.
     std::deque<Queued> queue;
+    struct Open {
+        long long tag;
+        Queued req;
+    };
+    std::unordered_map<long long, Open> open;
+    long long next_id = 0;
+    double esc_factor = 1.0;     // calls x factor on a retry (1: no retries)
+    long long esc_ncall_max = 0;
     std::vector<std::pair<long long, mcubes_result>> finished;  // not yet polled
     long long completed = 0;
     long long slot_bytes = 0;
     int iters_per_step = 1;
+    long long stream_gen = 0;  // calls of mcubes_server_run_stream so far
 };
+
+// Tags from 2^62 up are the server's own: mcubes_server_run_stream tags
+// request i of its k-th call 2^62 + (k mod 2^30) 2^31 + i.
+constexpr long long kStreamTagBase = 1ll << 62;
+
+// Queues a caller's request under a new internal id.
+static void server_enqueue(mcubes_server* s, const mcubes_request& r, long long tag)
+{
+    const long long id = s->next_id++;
+    s->queue.emplace_back(r, id);
+    s->open.emplace(id, mcubes_server::Open{tag, s->queue.back()});
+}
+
+// A finished request: reported under its caller's tag, or, when it ran out
+// of iterations without converging and the escalation allows, queued again
+// (at the front) with factor times the calls per iteration.
+static void server_retire(mcubes_server* s, long long id, const mcubes_result& res)
+{
+    auto it = s->open.find(id);
+    if (it == s->open.end()) return;
+    mcubes_request& r = it->second.req.r;
+    const double more = (double)r.ncall * s->esc_factor;
+    if (res.status == MCUBES_ENOCONV && s->esc_factor > 1.0 && more <= (double)s->esc_ncall_max) {
+        mcubes_request next = r;
+        next.ncall = (long long)more;
+        if (s->engine->validate(next) == MCUBES_OK) {
+            r.ncall = next.ncall;
+            s->queue.emplace_front(next, id);
+            return;
+        }
+    }
+    s->finished.emplace_back(it->second.tag, res);
+    ++s->completed;
+    s->open.erase(it);
+}
 
 static mcubes_status cuda_status(cudaError_t e)
 {
@@ -92,9 +155,18 @@ mcubes_status mcubes_server_destroy(mcubes_server* s)
 mcubes_status mcubes_server_submit(mcubes_server* s, const mcubes_request* req, long long tag)
 {
     if (!s || !req || (req->nparams > 0 && !req->params) || !req->lo || !req->hi) return MCUBES_EINVAL;
+    if (tag >= kStreamTagBase) return MCUBES_EINVAL;  // reserved for mcubes_server_run_stream
     const mcubes_status st = s->engine->validate(*req);
     if (st != MCUBES_OK) return st;
-    s->queue.emplace_back(*req, tag);
+    server_enqueue(s, *req, tag);
+    return MCUBES_OK;
+}
+
+mcubes_status mcubes_server_set_escalation(mcubes_server* s, double factor, long long ncall_max)
+{
+    if (!s || !(factor >= 1.0) || !(factor <= 1024.0) || ncall_max < 0) return MCUBES_EINVAL;
+    s->esc_factor = factor;
+    s->esc_ncall_max = ncall_max;
     return MCUBES_OK;
 }
 
@@ -111,9 +183,9 @@ static mcubes_status server_step(mcubes_server* s, int* ran)
     int n = 0;
     const cudaError_t e = E.step(&n, s->iters_per_step);
     if (e != cudaSuccess) return cuda_status(e);
-    const size_t before = s->finished.size();
-    E.finished(&s->finished, true);
-    s->completed += (long long)(s->finished.size() - before);
+    std::vector<std::pair<long long, mcubes_result>> fin;
+    E.finished(&fin, true);
+    for (const auto& f : fin) server_retire(s, f.first, f.second);
     if (ran) *ran = n;
     return MCUBES_OK;
 }
@@ -169,19 +241,35 @@ mcubes_status mcubes_server_run_stream(mcubes_server* s, int n, const mcubes_req
     }
     if (cudaSetDevice(s->ctx->device) != cudaSuccess) return MCUBES_ECUDA;
     using clock = std::chrono::steady_clock;
+    // Requests left by an earlier call that returned early (ENOMEM, ECUDA):
+    // the queued ones are dropped, finished ones discarded; resident ones
+    // finish later and are discarded below (their generation differs).
+    s->queue.erase(std::remove_if(s->queue.begin(), s->queue.end(),
+                                  [s](const Queued& q) {
+                                      auto it = s->open.find(q.tag);
+                                      if (it == s->open.end() || it->second.tag < kStreamTagBase) return false;
+                                      s->open.erase(it);
+                                      return true;
+                                  }),
+                   s->queue.end());
+    s->finished.erase(std::remove_if(s->finished.begin(), s->finished.end(),
+                                     [](const std::pair<long long, mcubes_result>& f) {
+                                         return f.first >= kStreamTagBase;
+                                     }),
+                      s->finished.end());
+    s->stream_gen = (s->stream_gen + 1) & ((1ll << 30) - 1);
+    const long long base = kStreamTagBase + (s->stream_gen << 31);
     const auto t0 = clock::now();
     auto now = [&]() { return std::chrono::duration<double>(clock::now() - t0).count(); };
-    // tags of this stream are offset so that earlier polled tags cannot collide
-    const long long base = 1ll << 62;
     int next = 0, done = 0;
-    std::vector<std::pair<long long, mcubes_result>> fin;
     while (done < n) {
         const double t = now();
         while (next < n && arrival_s[next] <= t) {
-            s->queue.emplace_back(reqs[next], base + next);
+            server_enqueue(s, reqs[next], base + next);
             ++next;
         }
         if (s->queue.empty() && s->engine->resident() == 0) {
+            if (next >= n) return MCUBES_ESTATE;  // a request of this call was lost: cannot happen
             // idle until the next arrival
             const double wait = arrival_s[next] - now();
             if (wait > 0) std::this_thread::sleep_for(std::chrono::duration<double>(std::min(wait, 0.001)));
@@ -192,11 +280,13 @@ mcubes_status mcubes_server_run_stream(mcubes_server* s, int n, const mcubes_req
         if (st != MCUBES_OK) return st;
         const double t_end = now();
         for (auto it = s->finished.begin(); it != s->finished.end();) {
-            if (it->first >= base) {
-                const long long i = it->first - base;
-                results[i] = it->second;
-                latency_s[i] = t_end - arrival_s[i];
-                ++done;
+            if (it->first >= kStreamTagBase) {
+                const long long i = it->first - base;  // another generation: outside [0, n)
+                if (i >= 0 && i < n) {
+                    results[i] = it->second;
+                    latency_s[i] = t_end - arrival_s[i];
+                    ++done;
+                }
                 it = s->finished.erase(it);
             } else {
                 ++it;

@@ -18,6 +18,9 @@
 // the refinement launch reduces in fixed order.
 #pragma once
 
+#include <type_traits>
+
+#include "fp_bits.cuh"
 #include "mc_device.cuh"
 
 namespace mc {
@@ -42,11 +45,61 @@ __device__ __forceinline__ void hist_add(uint32_t base, uint32_t idx, double v)
 // different axes' histograms and half as many lanes compete for the same
 // bins.  The single-precision add is a native reduction; there the swap
 // measured slower and is not made.
+#ifndef MC_HIST_CAS
+#define MC_HIST_CAS 1
+#endif
+
+__device__ __forceinline__ uint64_t lds_u64(uint32_t addr)
+{
+    uint64_t v;
+    asm volatile("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint64_t cas_shared_u64(uint32_t addr, uint64_t expect, uint64_t val)
+{
+    uint64_t old;
+    asm volatile("atom.shared.cas.b64 %0, [%1], %2, %3;" : "=l"(old) : "r"(addr), "l"(expect), "l"(val) : "memory");
+    return old;
+}
+
+// Adds v (>= 0) to the shared-memory double at addr, whose value the caller
+// read as `seen`: the first attempt adds on the FP64 pipe; an attempt that
+// finds the word changed (another lane or warp added to the bin in between)
+// retries with the exact integer addition of fp_bits.cuh, so that the few
+// lanes of a retry do not take whole FP64 warp slots.
+__device__ __forceinline__ void hist_cas_add(uint32_t addr, uint64_t seen, double v)
+{
+    const uint64_t vb = (uint64_t)__double_as_longlong(v);
+    uint64_t want = (uint64_t)__double_as_longlong(__longlong_as_double((long long)seen) + v);
+    uint64_t got = cas_shared_u64(addr, seen, want);
+    while (got != seen) {
+        seen = got;
+        want = add_nonneg_bits(seen, vb);
+        got = cas_shared_u64(addr, seen, want);
+    }
+}
+
 template <int NB4, class HT>
 __device__ __forceinline__ void hist_add_sample(uint32_t hist_s, const uint32_t (&idx)[2 * NB4], uint32_t hist_d,
                                                 HT F2)
 {
     const uint32_t odd = sizeof(HT) == 8 ? (threadIdx.x & 1u) : 0u;
+    if constexpr (sizeof(HT) == 8 && MC_HIST_CAS) {
+        // both bins of a word are read before either is written (two loads in
+        // flight, two FP64 adds back to back)
+#pragma unroll
+        for (int k = 0; k < 2 * NB4; ++k) {
+            if (2 * k < (int)hist_d) {
+                const uint32_t w = __funnelshift_l(idx[k], idx[k], odd << 4);  // halves swapped on odd lanes
+                const bool e0 = ((2u * k) ^ odd) < hist_d, e1 = ((2u * k + 1u) ^ odd) < hist_d;
+                const uint32_t a0 = hist_s + 8u * (w & 0xFFFFu), a1 = hist_s + 8u * (w >> 16);
+                const uint64_t s0 = e0 ? lds_u64(a0) : 0ull, s1 = e1 ? lds_u64(a1) : 0ull;
+                if (e0) hist_cas_add(a0, s0, (double)F2);
+                if (e1) hist_cas_add(a1, s1, (double)F2);
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < 2 * NB4; ++k) {
         if (2 * k < (int)hist_d) {
@@ -58,15 +111,22 @@ __device__ __forceinline__ void hist_add_sample(uint32_t hist_s, const uint32_t 
 }
 
 template <bool MIXED> struct Prec;
+#ifndef MC_MIXED_CUBE_F64
+#define MC_MIXED_CUBE_F64 1
+#endif
+// R: map and integrand; Cell: shared-memory map cell; H: histogram entry;
+// S: a cube's shifted sums S1, S2 and its mean and variance.
 template <> struct Prec<false> {
     using R = double;
     using Cell = double2;  // (x left edge, x width / g): x = left + (width/g)(g phi), J factor = (g nb)(width/g)
     using H = double;
+    using S = double;
 };
 template <> struct Prec<true> {
     using R = float;
     using Cell = float2;   // (x left edge, nb * x width): x = left + (nb width)(phi/nb), J factor = nb width
     using H = float;
+    using S = std::conditional_t<MC_MIXED_CUBE_F64 != 0, double, float>;
 };
 
 // Stages the grid of all axes into shared-memory cells and clears the
@@ -104,6 +164,67 @@ __device__ __forceinline__ void stage_cells(typename Prec<MIXED>::Cell* cells, t
         reinterpret_cast<uint2*>(cells)[bytes / 8 - 1] = static_cast<const uint2*>(cells_g)[bytes / 8 - 1];
 }
 
+// Whether a family runs its FP64 axes as a loop (Family::kRolled, default no).
+template <class F, class = void> struct RolledAxes { static constexpr bool value = false; };
+template <class F> struct RolledAxes<F, decltype((void)F::kRolled)> { static constexpr bool value = F::kRolled; };
+
+#ifndef MC_AXIS_UNROLL
+#define MC_AXIS_UNROLL 1
+#endif
+constexpr int kAxisUnroll = MC_AXIS_UNROLL;
+
+// sample_point for FP64 families with heavy per-axis work (a logarithm per
+// axis): the same arithmetic with the axes as a loop that is not unrolled,
+// so the per-axis code exists once instead of D times.  Unrolled, a six-axis
+// sample is thousands of instructions, more than the SM's instruction
+// caches keep close, and warps wait on instruction fetch.  In the loop the
+// sub-cube digit of axis j is peeled off the cube index (one high multiply),
+// the Philox block of axes 4b..4b+3 is drawn at j = 4b and its words are
+// rotated into place, and the flat bin indices are shifted into idx from the
+// top, so that after the last axis axis j's index is field j (the layout
+// sample_point leaves).
+template <int FAM, int NB4, int D, class A>
+__device__ __forceinline__ double sample_point_rolled(const A& a, const double2* cells, uint32_t c, uint32_t s,
+                                                      uint32_t it, uint32_t (&idx)[2 * NB4])
+{
+    using Fam = Family<FAM, double>;
+    constexpr int NW = (D + 1) / 2;  // index words in use
+    const uint32_t nb = a.nb;
+    typename Fam::S fs;
+    Fam::begin(fs);
+    IntProd jp = int_prod_of(a.jac0);
+    uint32_t rest = c;
+    uint4 r = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+    for (int k = 0; k < 2 * NB4; ++k) idx[k] = 0u;
+#pragma unroll kAxisUnroll
+    for (int j = 0; j < D; ++j) {
+        if ((j & 3) == 0) r = sample_words(a, make_uint4(s, c, it, (uint32_t)(j >> 2)));
+        const uint32_t w = r.x;
+        r = make_uint4(r.y, r.z, r.w, r.x);
+        uint32_t q = __umulhi(rest, a.gmagic);
+        uint32_t dig = rest - q * a.g;
+        if (dig >= a.g) { ++q; dig -= a.g; }
+        if (dig >= a.g) { ++q; dig -= a.g; }
+        rest = q;
+        const BinPos bp = bin_pos(w, dig * nb, nb, a.g, a.gmagic);
+        const uint32_t flat = (uint32_t)j * nb + bp.k;
+        const double2 cell = cells[flat];
+        const double x = fma(cell.y, bin_gphi_f64(bp), cell.x);   // (width/g)(g phi)
+        int_prod_mul(jp, cell.y);
+        Fam::add(fs, j, x, a.fam);
+#pragma unroll
+        for (int k = 0; k < NW - 1; ++k) idx[k] = __funnelshift_r(idx[k], idx[k + 1], 16);
+        idx[NW - 1] = (idx[NW - 1] >> 16) | (flat << 16);
+    }
+    if constexpr (D & 1) {  // one field short of the top: move every field down once more
+#pragma unroll
+        for (int k = 0; k < NW - 1; ++k) idx[k] = __funnelshift_r(idx[k], idx[k + 1], 16);
+        idx[NW - 1] >>= 16;
+    }
+    return Fam::end(fs, D, a.fam) * int_prod_value(jp);
+}
+
 // One sample: random words -> exact bin position -> map -> integrand.
 // Returns F = f(x) * J and leaves the flat histogram index of every axis in
 // idx (16 bits each, two per word).  A provides d, nb, g, gmagic, jac0 ((g nb)^d), phi_scale_f
@@ -115,6 +236,9 @@ sample_point(const A& a, const typename Prec<MIXED>::Cell* cells, uint32_t c, ui
 {
     using R = typename Prec<MIXED>::R;
     using Fam = Family<FAM, R>;
+    if constexpr (!MIXED && DC > 0 && RolledAxes<Fam>::value) {
+        return sample_point_rolled<FAM, NB4, DC>(a, cells, c, s, it, idx);
+    }
     constexpr int DN = 4 * NB4;  // axes handled by this instantiation (d <= DN)
     const uint32_t d = DC ? (uint32_t)DC : a.d, nb = a.nb;  // DC: the dimension when fixed at compile time
     uint32_t w[DN];
@@ -195,8 +319,9 @@ __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIX
     const uint32_t cubes_per_group = blockDim.x / L;
     // 1/p and 1/(p (p-1)), rounded once on the host: a division here would be
     // recomputed inside the cube loop when registers run short
-    R inv_p, inv_var_den;
-    if constexpr (MIXED) {
+    using RS = typename Prec<MIXED>::S;  // per-cube shifted sums and moments
+    RS inv_p, inv_var_den;
+    if constexpr (sizeof(RS) == 4) {
         inv_p = a.inv_p_f;
         inv_var_den = a.inv_var_den_f;
     } else {
@@ -229,7 +354,8 @@ __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIX
             }
         }
         // this lane's samples of the cube, shifted by its first value
-        R K = R(0), S1 = R(0), S2 = R(0);
+        R K = R(0);
+        RS S1 = RS(0), S2 = RS(0);
         uint32_t n = 0;
         if (valid) {
             for (uint32_t s = seg_lane; s < p; s += L) {
@@ -238,10 +364,10 @@ __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIX
                 if (n == 0) {
                     K = F;  // the shift: its own term is zero
                 } else if (n == 1) {
-                    S1 = F - K;
+                    S1 = (RS)F - (RS)K;
                     S2 = S1 * S1;
                 } else {
-                    const R z = F - K;
+                    const RS z = (RS)F - (RS)K;
                     S1 += z;
                     S2 += z * z;
                 }
@@ -257,15 +383,15 @@ __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIX
                 // mean; at p = 2 (every 1e8-call geometry) S1 = z, S2 = z^2 and
                 // the variance (z^2 - z^2/2)/2 is exactly z^2/4: the z^2 are
                 // summed and the sum scaled once after the loop (exact)
-                R mean, var;
+                RS mean, var;
                 if (p == 2u) {
-                    mean = K + S1 * R(0.5);
+                    mean = (RS)K + S1 * RS(0.5);
                     var = S2;
                 } else {
-                    mean = K + S1 * inv_p;
+                    mean = (RS)K + S1 * inv_p;
                     var = (S2 - S1 * S1 * inv_p) * inv_var_den;
                 }
-                if constexpr (MIXED) {
+                if constexpr (sizeof(RS) == 4) {
                     acc.fI.add(mean);
                     acc.fV.add(var);
                     if (a.want_abs) acc.fA.add(fabsf(mean));
@@ -315,7 +441,7 @@ template <int FAM, bool MIXED, bool ADJ, int NB4, int DC = 0, class A>
 __device__ __forceinline__ void sample_cube_slice(const A& a, const typename Prec<MIXED>::Cell* cells,
                                                   typename Prec<MIXED>::H* hist, uint64_t cube, uint32_t k,
                                                   uint32_t split, uint32_t it, uint32_t p,
-                                                  double (*red)[kVsThreads / 32], double* out)
+                                                  double (*red)[kVsThreadsMax / 32], double* out)
 {
     using R = typename Prec<MIXED>::R;
     using HT = typename Prec<MIXED>::H;
@@ -393,7 +519,8 @@ __device__ __forceinline__ void sample_cube_slice(const A& a, const typename Pre
 }
 
 // Fixed-order block sum of the three per-thread sums; thread 0 writes them.
-__device__ __forceinline__ void block_write_sums(const CubeSums& acc, double (*red)[kVsThreads / 32], double* out)
+template <int NW>
+__device__ __forceinline__ void block_write_sums(const CubeSums& acc, double (*red)[NW], double* out)
 {
     double v0 = acc.vI(), v1 = acc.vV(), v2 = acc.vA();
 #pragma unroll
@@ -434,12 +561,21 @@ __device__ __forceinline__ void block_write_sums(const CubeSums& acc, double (*r
 template <int FAM, bool MIXED, int NB4>
 constexpr int vsample_min_blocks() { return (FAM == MCUBES_F_TABLE && !MIXED) ? 2 : (NB4 == 1 ? 4 : 3); }
 
+// The same for the single-integral kernel, whose block size can differ
+// (vsample_threads): blocks that fill the register file at its size.
+template <int FAM, bool MIXED, int D>
+constexpr int vsample_kernel_min_blocks()
+{
+    return vsample_threads(FAM, MIXED, D) == kVsThreads ? vsample_min_blocks<FAM, MIXED, (D + 3) / 4>()
+                                                        : (FAM == MCUBES_F_COSMO6 ? MC_COSMO6_MINB : 1);
+}
+
 // One instantiation per dimension D: with the axis count a compile-time
 // constant every per-axis loop is unrolled without guards and the families'
 // dimension-dependent code (the corner family's power) folds (corner8: 21.4
 // -> 17.7 ms per 1e9-call launch against a runtime count).
 template <int FAM, bool MIXED, bool ADJ, int D>
-__global__ void __launch_bounds__(kVsThreads, vsample_min_blocks<FAM, MIXED, (D + 3) / 4>())
+__global__ void __launch_bounds__(vsample_threads(FAM, MIXED, D), vsample_kernel_min_blocks<FAM, MIXED, D>())
 vsample_kernel(const __grid_constant__ VsArgs a)
 {
     constexpr int NB4 = (D + 3) / 4;  // Philox blocks per sample
@@ -449,7 +585,7 @@ vsample_kernel(const __grid_constant__ VsArgs a)
     using Cell = typename Prec<MIXED>::Cell;
     using HT = typename Prec<MIXED>::H;
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double red[3][kVsThreads / 32];
+    __shared__ double red[3][kVsThreadsMax / 32];
 
     constexpr uint32_t d = D;
     const uint32_t nb = a.nb;
@@ -523,7 +659,7 @@ cudaError_t launch_vsample_family(bool mixed, bool adjust, const VsArgs& a, int 
     auto k = vsample_kernel_ptr<FAM>(mixed, adjust, (int)a.d);
     cudaError_t e = raise_smem_limit((const void*)k, smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, kVsThreads, smem, s>>>(a);
+    k<<<grid, vsample_threads(FAM, mixed, (int)a.d), smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -533,7 +669,7 @@ cudaError_t occupancy_family(bool mixed, bool adjust, int d, size_t smem, int* b
     auto k = vsample_kernel_ptr<FAM>(mixed, adjust, d);
     cudaError_t e = raise_smem_limit((const void*)k, smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, kVsThreads, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, vsample_threads(FAM, mixed, d), smem);
 }
 
 }  // namespace mc

@@ -29,7 +29,8 @@ EXPORTED = [
     "mcubes_server_step", "mcubes_server_poll", "mcubes_server_stats", "mcubes_server_run_stream",
     "mcubes_selftest_fxmath", "mcubes_state_size", "mcubes_state_export", "mcubes_state_import",
     "mcubes_problem_get", "mcubes_get_opts", "mcubes_tables_set", "mcubes_server_set_step_iterations",
-    "mcubes_selftest_rebin",
+    "mcubes_selftest_rebin", "mcubes_shard_partial_len", "mcubes_shard_sample", "mcubes_shard_finish",
+    "mcubes_server_set_escalation", "mcubes_batch_trace_get",
 ]
 
 
@@ -114,6 +115,7 @@ def lib():
                 "mcubes_server_submit": (ctypes.c_int, [ctypes.c_void_p, P(mcubes_request), ll]),
                 "mcubes_server_step": (ctypes.c_int, [ctypes.c_void_p, P(ctypes.c_int)]),
                 "mcubes_server_set_step_iterations": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+                "mcubes_server_set_escalation": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ll]),
                 "mcubes_server_poll": (ctypes.c_int, [ctypes.c_void_p, P(ll), P(mcubes_result), ctypes.c_int,
                                                       P(ctypes.c_int)]),
                 "mcubes_server_stats": (ctypes.c_int, [ctypes.c_void_p, P(ll), P(ll), P(ll), P(ll), P(ll)]),
@@ -130,6 +132,11 @@ def lib():
                                                           ctypes.c_void_p]),
                 "mcubes_selftest_rebin": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
                                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+                "mcubes_batch_trace_get": (ctypes.c_int, [ctx, ctypes.c_int, dp, dp, ctypes.c_int, P(ctypes.c_int),
+                                                          dp, dp]),
+                "mcubes_shard_partial_len": (ctypes.c_int, [ctx, P(ll)]),
+                "mcubes_shard_sample": (ctypes.c_int, [ctx, ll, ll, ctypes.c_void_p]),
+                "mcubes_shard_finish": (ctypes.c_int, [ctx, ctypes.c_void_p, ctypes.c_int]),
                 "mcubes_sample_range_noalloc": (ctypes.c_int, [
                     ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, dp, dp, ll, ctypes.c_int, ll,
                     ctypes.c_uint64, ctypes.c_int, ctypes.c_uint, ctypes.c_int, ll, ll, ctypes.c_void_p,
@@ -344,6 +351,39 @@ class Context:
                                               _dp(C)), "mcubes_sample_range")
         return sums, (None if C is None else C.reshape(self.d, self.nb))
 
+    def batch_trace(self, i, d, cap=ITMAX_MAX):
+        """Integral i of the last integrate_batch: (I_it, var_it, grid [d][nb], C [d][nb])."""
+        I, V = np.zeros(cap), np.zeros(cap)
+        n = ctypes.c_int()
+        B = np.zeros(d * self.opts_nb())
+        C = np.zeros(d * self.opts_nb())
+        self._check(lib().mcubes_batch_trace_get(self._h, int(i), _dp(I), _dp(V), cap, ctypes.byref(n), _dp(B),
+                                                 _dp(C)), "mcubes_batch_trace_get")
+        k = n.value
+        return I[:k], V[:k], B.reshape(d, -1), C.reshape(d, -1)
+
+    def opts_nb(self):
+        o = mcubes_opts()
+        self._check(lib().mcubes_get_opts(self._h, ctypes.byref(o)), "mcubes_get_opts")
+        return o.nbins
+
+    def shard_partial_len(self):
+        n = ctypes.c_longlong()
+        self._check(lib().mcubes_shard_partial_len(self._h, ctypes.byref(n)), "mcubes_shard_partial_len")
+        return n.value
+
+    def shard_sample(self, cube_begin, cube_end, d_partial):
+        """Samples cubes [cube_begin, cube_end) of the next iteration into the
+        device array at address d_partial (shard_partial_len() doubles)."""
+        self._check(lib().mcubes_shard_sample(self._h, int(cube_begin), int(cube_end), ctypes.c_void_p(d_partial)),
+                    "mcubes_shard_sample")
+
+    def shard_finish(self, d_gathered, nranks):
+        """Finishes the iteration from nranks gathered partials (device
+        address, [nranks][shard_partial_len()] in rank order)."""
+        self._check(lib().mcubes_shard_finish(self._h, ctypes.c_void_p(d_gathered), int(nranks)),
+                    "mcubes_shard_finish")
+
     def geometry(self):
         g, m, p = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
         lanes, blocks = ctypes.c_int(), ctypes.c_int()
@@ -405,6 +445,11 @@ class Server:
         """Iterations each step runs before reading back which requests finished."""
         self.ctx._check(lib().mcubes_server_set_step_iterations(self._h, int(iters)),
                         "mcubes_server_set_step_iterations")
+
+    def set_escalation(self, factor: float, ncall_max: int):
+        """Retry a request that ends unconverged with factor x its calls (up to ncall_max)."""
+        self.ctx._check(lib().mcubes_server_set_escalation(self._h, float(factor), int(ncall_max)),
+                        "mcubes_server_set_escalation")
 
     def step(self):
         ran = ctypes.c_int()

@@ -15,7 +15,7 @@ from paper_2202_01753_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 RTOL = 1e-12
-MIXED_BOUND = 2e-5
+MIXED_BOUND = 5e-7   # about ten times the 5.2e-8 observed on GB300 (f5, d = 5, against the FP64 oracle)
 
 
 def _oracle(w):

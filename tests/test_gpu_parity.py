@@ -336,7 +336,16 @@ def test_empty_and_single_cube_ranges(gpu_ctx_factory):
 # ---------------------------------------------------------------------------
 # mixed precision against the double-precision oracle
 # ---------------------------------------------------------------------------
-MIXED_BOUND = 2e-5   # relative error of an iteration estimate (single-precision map and f)
+# Mixed precision against the FP64 oracle: per configuration, about ten
+# times the error observed on GB300 (single-precision map and integrand; the
+# grids then differ by the single-precision histogram sums, whose atomic
+# order varies from run to run).  Iteration estimates relative to their
+# conditioning scale, variances relative.  Observed (I, var): corner8 2.7e-9,
+# 8.2e-7; osc10 9.2e-8, 3.7e-8; gauss3 1.3e-8, 7.1e-8.
+MIXED_BOUND = {"corner8": (3e-8, 1e-5), "osc10": (1e-6, 5e-7), "gauss3": (1.5e-7, 1e-6)}
+# full-size corner8 geometry on sampled ranges: observed 4.7e-8 (sum of cube
+# means relative to the sum of |means|), 1.9e-6 per histogram bin
+MIXED_FULL_SIZE = (5e-7, 2e-5)
 
 
 @pytest.mark.parametrize("make,ncall", [(W.corner8, 400_000), (W.osc10, 400_000), (W.gauss3, 2 ** 18)])
@@ -345,9 +354,10 @@ def test_mixed_precision_bound(gpu_ctx_factory, make, ncall):
     o = oracle_run(w)
     g = gpu_run(gpu_ctx_factory, w, precision="mixed")
     scale = cond_scale(w, o)
+    bound_I, bound_V = MIXED_BOUND[make.__name__]
     err = np.max(np.abs(g["I"] - o["trace_I"])) / scale
-    assert err < MIXED_BOUND, err
-    np.testing.assert_allclose(g["V"], o["trace_var"], rtol=1e-3)
+    assert err < bound_I, err
+    np.testing.assert_allclose(g["V"], o["trace_var"], rtol=bound_V)
     exact = CF.exact(w)
     assert abs(g["res"]["estimate"] - exact) < 5 * g["res"]["sigma"]
 
@@ -362,6 +372,6 @@ def test_mixed_full_size_sampled(gpu_ctx_factory):
     for c0, c1 in _ranges(pb.m, 20_000):
         s_o, C_o, _, _ = pb.vsample(B, 3, True, c0, c1)
         s_g, C_g = ctx.sample_range(3, True, c0, c1)
-        assert abs(s_g[0] - s_o[0]) / s_o[2] < MIXED_BOUND
-        np.testing.assert_allclose(C_g, C_o, rtol=1e-3, atol=1e-6 * C_o.max())
+        assert abs(s_g[0] - s_o[0]) / s_o[2] < MIXED_FULL_SIZE[0]
+        np.testing.assert_allclose(C_g, C_o, rtol=MIXED_FULL_SIZE[1], atol=1e-6 * C_o.max())
     ctx.close()

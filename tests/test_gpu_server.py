@@ -12,7 +12,14 @@ from paper_2202_01753_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-RTOL = {"fp64": 1e-10, "mixed": 2e-4}
+# Served against solo, estimate relative to max(|I|, sigma) and sigma
+# relative: about ten times the differences observed on GB300 -- FP64 at
+# rounding level; mixed 1.1e-5 and 7.0e-4: the single-precision histogram
+# sums are grouped by the step's segments, which depend on which requests
+# share the step, and the rebinning carries their rounding from iteration to
+# iteration, most on the narrow high-dimensional peaks.
+RTOL = {"fp64": 1e-13, "mixed": 1e-4}
+STOL = {"fp64": 1e-13, "mixed": 7e-3}
 
 
 def _reqs(n, seed, itmax=8, rel=True):
@@ -48,7 +55,7 @@ def _check(w, got, solo, precision):
     # zero (oscillatory ones) a floor far below the integrands' O(1) values
     scale = max(abs(solo["estimate"]), solo["sigma"], 1e-9)
     assert abs(got["estimate"] - solo["estimate"]) <= RTOL[precision] * scale
-    assert got["sigma"] == pytest.approx(solo["sigma"], rel=10 * RTOL[precision])
+    assert got["sigma"] == pytest.approx(solo["sigma"], rel=STOL[precision])
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -165,5 +172,63 @@ def test_invalid_submission_is_rejected(gpu_ctx_factory):
         srv.submit(bad, 0)
     assert e.value.status == mcubes.EINVAL
     assert srv.stats()["queued"] == 0
+    srv.close()
+    ctx.close()
+
+
+def _solo_escalated(make_ctx, w, precision, factor, ncall_max):
+    """The retry rule written out on solo runs: more calls while unconverged."""
+    ncall = w.ncall
+    while True:
+        ctx = make_ctx(seed=w.seed, precision=precision)
+        r = ctx.integrate(w.fid, w.params, w.lo, w.hi, ncall, w.itmax, w.rel_tol, w.abs_tol)
+        ctx.close()
+        if r["converged"] or r["status"] != mcubes.ENOCONV or ncall * factor > ncall_max:
+            return r
+        ncall = int(ncall * factor)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_escalation_retries_unconverged_requests_with_more_calls(gpu_ctx_factory, precision):
+    ws = _reqs(24, seed=31, itmax=6)
+    for w in ws:
+        w.rel_tol = 2e-4                      # most need more than 1e4..1e5 calls x 6 iterations
+    factor, ncall_max = 4.0, 2_000_000
+    ctx = gpu_ctx_factory(precision=precision)
+    srv = mcubes.Server(ctx, itcap=16)
+    srv.set_escalation(factor, ncall_max)
+    for i, w in enumerate(ws):
+        srv.submit(_dict(w), i)
+    results, steps = {}, 0
+    while len(results) < len(ws):
+        srv.step()
+        steps += 1
+        results.update(dict(srv.poll()))
+        assert steps < 400
+    st = srv.stats()
+    assert st["completed"] == len(ws) and st["resident"] == 0 and st["queued"] == 0
+    srv.close()
+    ctx.close()
+    retried = 0
+    for i, w in enumerate(ws):
+        solo = _solo_escalated(gpu_ctx_factory, w, precision, factor, ncall_max)
+        assert results[i]["samples_per_iter"] == solo["samples_per_iter"]
+        retried += solo["samples_per_iter"] > w.ncall
+        _check(w, results[i], solo, precision)
+    assert retried > 0                        # the rule was exercised
+    assert sum(r["converged"] for r in results.values()) > sum(
+        _solo(gpu_ctx_factory, w, precision)["converged"] for w in ws)
+
+
+def test_reserved_tags_and_escalation_arguments(gpu_ctx_factory):
+    ctx = gpu_ctx_factory()
+    srv = mcubes.Server(ctx, itcap=8)
+    w = _reqs(1, seed=33)[0]
+    with pytest.raises(mcubes.McubesError):
+        srv.submit(_dict(w), 1 << 62)         # the range mcubes_server_run_stream tags with
+    srv.submit(_dict(w), (1 << 62) - 1)
+    for bad in ((0.5, 10 ** 6), (2.0, -1), (float("nan"), 10 ** 6)):
+        with pytest.raises(mcubes.McubesError):
+            srv.set_escalation(*bad)
     srv.close()
     ctx.close()

@@ -15,7 +15,7 @@ from paper_2202_01753_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 RTOL = 1e-12
-MIXED_BOUND = 2e-5
+MIXED_BOUND = 2e-7   # about ten times the 1.7e-8 observed on GB300 (257^2 / 4097-knot tables)
 
 
 def _gpu(make_ctx, w, precision="fp64"):

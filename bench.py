@@ -91,7 +91,9 @@ def parse():
                     choices=sorted(W.CONFIGS) + ["batch4096", "serve", "onedim", "accuracy"])
     ap.add_argument("--sweep-runs", type=int, default=100, help="seeds per tolerance level (accuracy sweep)")
     ap.add_argument("--sweep-ncall0", type=float, default=1e5, help="calls per iteration at tau_rel = 1e-3")
-    ap.add_argument("--sweep-ncall-cap", type=float, default=1.1e8, help="largest calls per iteration")
+    ap.add_argument("--sweep-ncall-cap", type=float, default=1.7e9, help="largest calls per iteration")
+    ap.add_argument("--sweep-seconds", type=float, default=1800.0,
+                    help="no deeper level of an integrand starts after its share of this time")
     ap.add_argument("--sweep-precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="length of the configured Poisson stream")
     ap.add_argument("--serve-burst", type=int, default=2000, help="requests offered at once (capacity)")
@@ -594,6 +596,8 @@ def ours(args):
         "gpu_launches": kt["sample_launches"] + kt["refine_launches"],
         "clocks": clk,
         "alu_peaks": {"ffma_tflops": 2 * pk["ffma_per_s"] / 1e12, "dfma_tflops": 2 * pk["dfma_per_s"] / 1e12,
+                      "fp64_inst_per_clk_per_sm": {k: pk[f"{k}_per_s"] / (sms * sm_mhz * 1e6) if sm_mhz else None
+                                                   for k in ("dfma", "dadd", "dmul")},
                       "how": "independent FMA chains on every thread of 8 blocks/SM, CUDA events"},
         "result": {"estimate": res["estimate"], "sigma": res["sigma"], "chi2_dof": res["chi2_dof"],
                    "e2e_estimate": r2["estimate"]},
@@ -922,12 +926,18 @@ def accuracy_arm(args):
     runs, itmax, ncall_cap = args.sweep_runs, 20, int(args.sweep_ncall_cap)
     ctx = mcubes.Context(local, precision=args.sweep_precision)
     rows, t_total, n_total = [], 0.0, 0
+    t_sweep = time.perf_counter()
+    stop_reason = {}
     clocks = ClockSampler(local)
     clocks.start()
+    budget = args.sweep_seconds / len(ACCURACY_SUITE)   # per integrand
     for name, d in ACCURACY_SUITE:
         exact = CF.exact(W.suite(name, d))
         ncall, tau = int(args.sweep_ncall0), 1e-3
+        t_start = time.perf_counter()
+        stop_reason[name] = "reached tau 1e-9"
         while tau >= 1e-9:
+            tries = 0
             while True:
                 ws = [W.suite(name, d, ncall=ncall, itmax=itmax, seed=1000 + r) for r in range(runs)]
                 reqs = [dict(fid=w.fid, params=w.params, lo=w.lo, hi=w.hi, ncall=w.ncall, itmax=itmax,
@@ -935,8 +945,9 @@ def accuracy_arm(args):
                 t0 = time.perf_counter()
                 out = ctx.integrate_batch(reqs)
                 dt = time.perf_counter() - t0
+                tries += 1
                 conv = np.array([bool(o["converged"]) for o in out], dtype=bool)
-                if conv.mean() >= 0.9 or ncall * 4 > ncall_cap:
+                if conv.mean() >= 0.9 or ncall * 4 > ncall_cap or time.perf_counter() - t_start > budget:
                     break
                 ncall *= 4                      # more samples for a tighter tolerance (Sec. 5.1)
             t_total += dt
@@ -944,17 +955,28 @@ def accuracy_arm(args):
             err = np.array([abs(o["estimate"] - exact) / abs(exact) for o in out])
             chi = np.array([o["chi2_dof"] for o in out])
             ok = conv & (chi < 5.0)                     # boolean mask: the runs the paper's plots keep
-            row = {"integrand": f"{name},d={d}", "tau": tau, "ncall": ncall, "runs": runs,
+            row = {"integrand": f"{name},d={d}", "tau": tau, "ncall": ncall, "runs": runs, "tries": tries,
                    "converged": float(conv.mean()), "converged_chi2_lt5": float(ok.mean()),
                    "within_tau": float(np.mean(err[ok] <= tau)) if ok.any() else None,
                    "median_true_rel_err": float(np.median(err[ok])) if ok.any() else None,
+                   "median_err_over_tau": float(np.median(err[ok]) / tau) if ok.any() else None,
                    "p90_true_rel_err": float(np.percentile(err[ok], 90)) if ok.any() else None,
                    "median_iterations": float(np.median([o["iterations"] for o in out])),
                    "seconds": dt, "integrals_per_s": runs / dt}
             rows.append(row)
+            print(json.dumps({"level": row}), file=sys.stderr, flush=True)
             if conv.mean() < 0.9:
+                why = "cap" if ncall * 4 > ncall_cap else "time budget"
+                stop_reason[name] = (f"tau {tau:.3g}: {conv.mean():.2f} converged at {ncall:.3g} calls "
+                                     f"({why}: cap {ncall_cap:.3g} calls, {budget:.0f} s per integrand)")
                 break                           # the level failed: the sweep of this integrand ends
+            if time.perf_counter() - t_start > budget:
+                stop_reason[name] = f"time budget ({budget:.0f} s per integrand) spent after tau {tau:.3g}"
+                break
             tau /= 5.0
+            # sigma falls as ncall^-1/2: a tolerance five times tighter needs
+            # about 25 times the calls; start two factors of 4 up
+            ncall = min(ncall * 16, ncall_cap)
     clk = clocks.stop()
     ctx.close()
     line = {
@@ -962,10 +984,11 @@ def accuracy_arm(args):
         "unit": "integrals/s", "n_gpus": 1, "steps": len(rows), "warmup": 0, "ms_per_step": None,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.sweep_precision == "fp64" else "f32+f64", "data": "synthetic",
-        "config": {"workload": "paper suite f2-f6 (Sec. 5 eqs. 2-6)", "dims": dict(ACCURACY_SUITE), "runs": runs,
+        "config": {"workload": "paper suite f1-f6 (Sec. 5 eqs. 1-6)", "dims": dict(ACCURACY_SUITE), "runs": runs,
                    "itmax": itmax, "nbins": 500, "ncall_start": int(args.sweep_ncall0), "ncall_cap": ncall_cap,
-                   "precision": args.sweep_precision, "batched": True},
-        "levels": rows, "clocks": clk,
+                   "precision": args.sweep_precision, "batched": True,
+                   "ncall_rule": "next level starts at 16x the last level's calls; x4 while < 90% converge"},
+        "stopped": stop_reason, "levels": rows, "clocks": clk, "seconds": time.perf_counter() - t_sweep,
     }
     print(json.dumps(line))
     return 0

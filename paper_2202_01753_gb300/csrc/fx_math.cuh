@@ -17,12 +17,13 @@
 // terms and made non-negative, so its series also runs on unsigned high
 // multiplies).
 //
-// Accuracy (tested against 60-digit references): fx_exp within 1 ulp;
+// Accuracy (tested against 60-digit references): fx_exp within 1 ulp
+// (subnormal results within one unit of their last place);
 // fx_log within 1 ulp plus 2^-58 absolute (the series is absolute-accurate,
 // so for x within ~1e-3 of 1 the relative error grows as 2^-58 / |ln x|;
 // every use in this library feeds an exponent or a difference, where the
 // absolute error is what matters).  Outside the fast ranges (non-positive,
-// subnormal, infinite or NaN x; |y| beyond ~708) they return CUDA's log/exp.
+// subnormal, infinite or NaN x; y above ~708) they return CUDA's log/exp.
 #pragma once
 
 #include <cstdint>
@@ -117,19 +118,17 @@ __device__ __forceinline__ double fx_log(double x)
 __device__ __forceinline__ double fx_exp_bits(uint64_t u)
 {
     const double y = __longlong_as_double((long long)u);
-    uint64_t ay = u & 0x7FFFFFFFFFFFFFFFull;
-    // y < -745.2 (down to -inf): exp(y) < 2^-1075 rounds to +0.  Integrands
-    // with narrow peaks land here for a large share of their samples, so
-    // this case takes no branch: the argument is replaced by -1 and the
-    // result by +0 at the end.  (A divergent early return would split the
-    // warp, and code after the call, on the FP64 pipe, would run once per
-    // side with part of the lanes.)
-    const bool under = (u >> 63) && ay > 0x408749999999999Aull && ay <= 0x7FF0000000000000ull;
-    if (under) {
-        u = 0xBFF0000000000000ull;
-        ay = 0x3FF0000000000000ull;
+    const uint64_t ay = u & 0x7FFFFFFFFFFFFFFFull;
+    if (ay >= 0x4086200000000000ull) {  // |y| >= 708, infinite or NaN
+        // y < -745.2 (down to -inf): exp(y) < 2^-1075 rounds to +0.  Integrands
+        // with narrow peaks land here often, so it takes no FP64 work.  Down
+        // from -708 the results are subnormal; they are assembled below with
+        // integer rounding, so that these samples (a few percent of a narrow
+        // peak's) do not send their warp through CUDA's exp with one or two
+        // lanes on the FP64 pipe.  Overflow and NaN are CUDA's exp.
+        if (!(u >> 63) || ay > 0x7FF0000000000000ull) return exp_slow(y);
+        if (ay > 0x408749999999999Aull) return 0.0;
     }
-    if (ay >= 0x4086200000000000ull) return exp_slow(y);  // overflow, subnormal results, NaN: CUDA's exp
     if (ay < 0x3C30000000000000ull) return 1.0;  // |y| < 2^-60: exp(y) rounds to 1
     // y = n ln2/256 + r, n = round(y 256/ln2) from y's significand M and
     // exponent E: |y| 256/ln2 = H 2^(E-1075) to 2^-52 relative, H =
@@ -175,13 +174,24 @@ __device__ __forceinline__ double fx_exp_bits(uint64_t u)
     const int j = (int)(n & 255);
     const int k = (int)(n >> 8);
     const uint64_t P = __umul64hi(__ldg(&kExp2[j]) << 1, s << 1);
-    // assemble 2^k P / 2^62 (rounded to nearest, ties away), a normal double for |y| < 708
+    // assemble 2^k P / 2^62 (rounded to nearest, ties away): P normalised
+    // into [2^62, 2^63), then a normal double (biased exponent eb >= 1) or,
+    // for eb <= 0 (y below about -708.4), the subnormal round(P 2^-(11 - eb))
+    // (a carry into 2^52 is the smallest normal; below 2^-1075 it is +0)
+    uint64_t Pn = P;
+    int eb = k + 1023;
+    if (Pn < ((uint64_t)1 << 62)) {
+        Pn <<= 1;
+        --eb;
+    }
     uint64_t bits;
-    if (P >= ((uint64_t)1 << 62))
-        bits = ((uint64_t)(k + 1023) << 52) + (((P + (1ull << 9)) >> 10) - (1ull << 52));
-    else
-        bits = ((uint64_t)(k + 1022) << 52) + (((P + (1ull << 8)) >> 9) - (1ull << 52));
-    return __longlong_as_double((long long)(under ? 0ull : bits));
+    if (eb >= 1) {
+        bits = ((uint64_t)eb << 52) + (((Pn + (1ull << 9)) >> 10) - (1ull << 52));
+    } else {
+        const int sh = 11 - eb;
+        bits = sh < 64 ? (Pn + (1ull << (sh - 1))) >> sh : 0ull;
+    }
+    return __longlong_as_double((long long)bits);
 }
 
 __device__ __forceinline__ double fx_exp(double y) { return fx_exp_bits((uint64_t)__double_as_longlong(y)); }

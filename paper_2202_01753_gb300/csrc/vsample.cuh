@@ -112,7 +112,7 @@ __device__ __forceinline__ void hist_add_sample(uint32_t hist_s, const uint32_t 
 
 template <bool MIXED> struct Prec;
 #ifndef MC_MIXED_CUBE_F64
-#define MC_MIXED_CUBE_F64 1
+#define MC_MIXED_CUBE_F64 0
 #endif
 // R: map and integrand; Cell: shared-memory map cell; H: histogram entry;
 // S: a cube's shifted sums S1, S2 and its mean and variance.

@@ -1,4 +1,4 @@
-"""Measured ALU peaks of the device (FFMA and DFMA throughput), the
+"""Measured ALU peaks of the device (FFMA, DFMA, DADD and DMUL throughput), the
 denominators of the sampling kernel's roofline.  Built in-tree by
 paper_2202_01753_gb300.build alongside libmcubes."""
 from __future__ import annotations
@@ -30,7 +30,7 @@ def build() -> str:
 
 
 def measure(device: int = 0) -> dict:
-    """FMA/s in FP32 and FP64 on `device` (one FMA = 2 flops)."""
+    """FMA/s in FP32 and FP64 on `device` (one FMA = 2 flops), and FP64 adds/s and multiplies/s."""
     h = ctypes.CDLL(build())
     h.mcpeaks_fma.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                               ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
@@ -39,5 +39,10 @@ def measure(device: int = 0) -> dict:
     st = h.mcpeaks_fma(device, ctypes.byref(f), ctypes.byref(d), ctypes.byref(mf), ctypes.byref(md))
     if st:
         raise RuntimeError(f"peak measurement failed ({st})")
-    return {"ffma_per_s": f.value, "dfma_per_s": d.value, "ms_f32": mf.value, "ms_f64": md.value,
-            "host": platform.machine()}
+    h.mcpeaks_fp64_addmul.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    a, m = ctypes.c_double(), ctypes.c_double()
+    st = h.mcpeaks_fp64_addmul(device, ctypes.byref(a), ctypes.byref(m))
+    if st:
+        raise RuntimeError(f"peak measurement failed ({st})")
+    return {"ffma_per_s": f.value, "dfma_per_s": d.value, "dadd_per_s": a.value, "dmul_per_s": m.value,
+            "ms_f32": mf.value, "ms_f64": md.value, "host": platform.machine()}

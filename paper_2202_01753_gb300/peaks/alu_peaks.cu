@@ -1,7 +1,7 @@
 // alu_peaks.cu -- measured arithmetic peaks of the device, the denominators
 // of the sampling kernel's roofline: fused multiply-add throughput in single
-// and double precision, from long independent FMA chains in every thread of a
-// full grid, timed with CUDA events.
+// and double precision, and the double-precision add and multiply, from long
+// independent chains in every thread of a full grid, timed with CUDA events.
 #include <cstdio>
 
 #include <cuda_runtime.h>
@@ -12,7 +12,8 @@ constexpr int kChains = 8;
 constexpr int kUnroll = 16;
 constexpr int kThreads = 256;
 
-template <typename T>
+// OP 0: x = fma(x, a, b); 1: x = x + b; 2: x = x * a
+template <typename T, int OP>
 __global__ void __launch_bounds__(kThreads) fma_chains(T* sink, T a, T b, int iters)
 {
     T x[kChains];
@@ -22,7 +23,11 @@ __global__ void __launch_bounds__(kThreads) fma_chains(T* sink, T a, T b, int it
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
 #pragma unroll
-            for (int c = 0; c < kChains; ++c) x[c] = fma(x[c], a, b);
+            for (int c = 0; c < kChains; ++c) {
+                if constexpr (OP == 0) x[c] = fma(x[c], a, b);
+                else if constexpr (OP == 1) x[c] = x[c] + b;
+                else x[c] = x[c] * a;
+            }
         }
     }
     T s = 0;
@@ -31,8 +36,8 @@ __global__ void __launch_bounds__(kThreads) fma_chains(T* sink, T a, T b, int it
     if (s == (T)-1.2345) sink[blockIdx.x] = s;  // keeps the chains alive; never true
 }
 
-template <typename T>
-int measure(int blocks_per_sm, int iters, double* fma_per_s, float* ms_out)
+template <typename T, int OP = 0>
+int measure(int blocks_per_sm, int iters, double* ops_per_s, float* ms_out)
 {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -43,9 +48,9 @@ int measure(int blocks_per_sm, int iters, double* fma_per_s, float* ms_out)
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const int grid = sms * blocks_per_sm;
-    fma_chains<T><<<grid, kThreads>>>(sink, (T)0.9999999, (T)1e-7, iters / 8);  // warm
+    fma_chains<T, OP><<<grid, kThreads>>>(sink, (T)0.9999999, (T)1e-7, iters / 8);  // warm
     cudaEventRecord(e0);
-    fma_chains<T><<<grid, kThreads>>>(sink, (T)0.9999999, (T)1e-7, iters);
+    fma_chains<T, OP><<<grid, kThreads>>>(sink, (T)0.9999999, (T)1e-7, iters);
     cudaEventRecord(e1);
     cudaError_t err = cudaEventSynchronize(e1);
     float ms = 0.f;
@@ -54,8 +59,8 @@ int measure(int blocks_per_sm, int iters, double* fma_per_s, float* ms_out)
     cudaEventDestroy(e1);
     cudaFree(sink);
     if (err != cudaSuccess) return 2;
-    const double fmas = (double)grid * kThreads * iters * kUnroll * kChains;
-    *fma_per_s = fmas / (ms * 1e-3);
+    const double ops = (double)grid * kThreads * iters * kUnroll * kChains;
+    *ops_per_s = ops / (ms * 1e-3);
     *ms_out = ms;
     return 0;
 }
@@ -70,4 +75,15 @@ extern "C" int mcpeaks_fma(int device, double* ffma_per_s, double* dfma_per_s, f
     int r = measure<float>(8, 2048, ffma_per_s, ms_f32);
     if (r) return r;
     return measure<double>(8, 64, dfma_per_s, ms_f64);
+}
+
+// Double-precision additions and multiplications per second over the whole
+// device (the other instructions of the FP64 pipe).  Returns 0 on success.
+extern "C" int mcpeaks_fp64_addmul(int device, double* dadd_per_s, double* dmul_per_s)
+{
+    if (cudaSetDevice(device) != cudaSuccess) return 3;
+    float ms = 0.f;
+    int r = measure<double, 1>(8, 64, dadd_per_s, &ms);
+    if (r) return r;
+    return measure<double, 2>(8, 64, dmul_per_s, &ms);
 }

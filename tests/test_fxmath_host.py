@@ -78,6 +78,24 @@ def test_exp_accuracy_host(fxhost):
     assert np.all(z == 0.0) and not np.any(np.signbit(z))
 
 
+def test_exp_subnormal_results_host(fxhost):
+    """exp(y) for y from -708 down to -745.2, where the result leaves the
+    normal range: assembled with integer rounding, within one unit of the
+    last place of the result (2^-1074 once subnormal), +0 below 2^-1075."""
+    rng = np.random.default_rng(23)
+    ys = np.concatenate([rng.uniform(707.5, 745.2, 6000), np.linspace(708.3, 708.5, 200),
+                         np.linspace(744.4, 745.2, 200),
+                         [708.0, 708.3964185322641, 708.4, 744.4400719213812, 745.1332191019411, 745.13, 745.2]])
+    _, got = fxhost(ys)      # fx_exp(-y)
+    mpmath.mp.dps = 40
+    tiny = mpmath.mpf(2) ** -1074
+    for y, g in zip(ys, got):
+        ref = mpmath.exp(-mpmath.mpf(float(y)))
+        tol = max(ref * mpmath.mpf(2) ** -52, tiny)
+        assert abs(mpmath.mpf(float(g)) - ref) <= tol, (y, g, float(ref))
+    assert np.all(got >= 0.0)
+
+
 def test_tables_header_is_generated():
     """csrc/fx_tables.h is exactly what gen_fx_tables.py computes from the
     constants' definitions (60-digit arithmetic, rounded once): no entry is

@@ -42,13 +42,14 @@ def _solo(make_ctx, w, precision):
     return r
 
 
-# Batch against solo, about ten times the differences observed on GB300
-# (estimate relative to max(|I|, sigma), sigma relative): FP64 3.6e-16 and
-# 4.3e-15 on the mix, 7.2e-15 and 9.0e-15 over every class; mixed 2.6e-8 and
-# 9.2e-8 on the mix, 1.4e-7 and 3.3e-6 over every class (single-precision
-# histogram sums grouped by segment instead of by block: the grids differ
-# by their rounding, and each rebin carries it into the next iteration).
-@pytest.mark.parametrize("precision,rtol,stol", [("fp64", 1e-13, 1e-13), ("mixed", 3e-7, 1e-6)])
+# Batch against solo, about ten times the largest differences observed on
+# GB300 in three runs (estimate relative to max(|I|, sigma), sigma
+# relative): FP64 4.1e-16 and 6.5e-15 on the mix, 7.2e-15 and 1.1e-14 over
+# every class; mixed 3.9e-8 and 3.8e-7 on the mix, 1.4e-7 and 3.3e-6 over
+# every class (single-precision histogram sums grouped by segment instead
+# of by block: the grids differ by their rounding, and each rebin carries
+# it into the next iteration).
+@pytest.mark.parametrize("precision,rtol,stol", [("fp64", 1e-13, 1e-13), ("mixed", 3e-7, 4e-6)])
 def test_batch_matches_solo(gpu_ctx_factory, precision, rtol, stol):
     ws = _mix(40, seed=11)
     ctx = gpu_ctx_factory(precision=precision)
@@ -112,9 +113,12 @@ def test_batch_fp64_traces_match_oracle(gpu_ctx_factory):
     path's tolerances (test_gpu_parity): each iteration's estimate within
     1e-12 of its conditioning scale and its variance within 1e-12 (1e-10 for
     the oscillatory family), the final grid within 1e-12, chi^2 within
-    1e-9, and the last histogram within 1e-12 of each axis's largest bin
-    (per bin, a few bins far below an axis's largest differ by up to 3e-12
-    relative: observed on corner9, the bins of 5e-14 next to 2e-13).  The batch draws each
+    1e-9, and the last histogram within 1e-11 of each axis's largest bin.
+    The histogram sums F^2, whose relative error is the mapped points'
+    last-bit differences (grids equal to ~1e-16, not bit for bit) times the
+    integrand's sensitivity: f6's F^2 = exp(2 sum c_i x_i) multiplies them
+    by 2 sum c_i ~ 70 (observed 3.1e-12 of the axis's largest bin; corner9's
+    bins 3e-12 relative to themselves).  The batch draws each
     integral's own samples; only the grouping of the partial sums into
     segments differs from the oracle's compensated sums."""
     from test_gpu_parity import cond_scale
@@ -131,7 +135,9 @@ def test_batch_fp64_traces_match_oracle(gpu_ctx_factory):
         np.testing.assert_allclose(I, o["trace_I"], rtol=0, atol=1e-12 * scale, err_msg=w.name)
         np.testing.assert_allclose(V, o["trace_var"], rtol=vtol, atol=0, err_msg=w.name)
         np.testing.assert_allclose(B, o["grid"], rtol=0, atol=1e-12, err_msg=w.name)
-        assert np.all(np.abs(C - o["hist"]) <= 1e-12 * np.abs(o["hist"]).max(axis=1, keepdims=True)), w.name
+        rowmax = np.abs(o["hist"]).max(axis=1, keepdims=True)
+        worst = float(np.max(np.abs(C - o["hist"]) / rowmax))
+        assert worst <= 1e-11, (w.name, worst, np.unravel_index(np.argmax(np.abs(C - o["hist"]) / rowmax), C.shape))
         assert b["estimate"] == pytest.approx(o["estimate"], abs=1e-12 * scale), w.name
         assert b["sigma"] == pytest.approx(o["sigma"], rel=vtol), w.name
         assert b["chi2_dof"] == pytest.approx(o["chi2_dof"], rel=1e-9, abs=1e-12), w.name

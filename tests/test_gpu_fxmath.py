@@ -59,12 +59,31 @@ def test_exp_accuracy(torch_cuda):
         ref = mpmath.exp(mpmath.mpf(float(y)))
         assert abs(mpmath.mpf(float(g)) - ref) / ref <= 2.0 ** -52, (y, g, float(ref))
     assert np.all(np.abs(got - cuda) <= 2 * np.spacing(np.abs(cuda)))
-    special = np.array([-800.0, 800.0, -np.inf, np.inf, np.nan, -708.5, 709.5, -745.1, -745.14, -745.2,
+    special = np.array([-800.0, 800.0, -np.inf, np.inf, np.nan, 709.5, -745.2,
                         np.nextafter(-745.2, -np.inf), -746.0, -1e5, -1e300, -np.finfo(np.float64).max])
     g, c = _eval(torch_cuda, 1, special), _eval(torch_cuda, 3, special)
     assert np.array_equal(np.isnan(g), np.isnan(c)) and np.all((g == c) | np.isnan(g))
     # below -745.2 the result is +0 exactly (exp(y) < 2^-1075), as libm gives
     assert np.all(g[special < -745.2] == 0.0) and not np.any(np.signbit(g[special < -745.2]))
+
+
+def test_exp_subnormal_results(torch_cuda):
+    """From y = -708 down to -745.2 the results leave the normal range; they
+    are assembled with integer rounding: within one unit of their last
+    place (2^-1074 once subnormal) of the 40-digit reference and of CUDA's
+    exp, never negative."""
+    rng = np.random.default_rng(6)
+    ys = np.concatenate([rng.uniform(-745.2, -707.5, 3000), np.linspace(-708.5, -708.3, 100),
+                         [-708.5, -745.1, -745.13, -745.14, -744.44007192138]])
+    got = _eval(torch_cuda, 1, ys)
+    cuda = _eval(torch_cuda, 3, ys)
+    mpmath.mp.dps = 40
+    tiny = 2.0 ** -1074
+    for y, g in zip(ys, got):
+        ref = mpmath.exp(mpmath.mpf(float(y)))
+        assert abs(mpmath.mpf(float(g)) - ref) <= max(ref * mpmath.mpf(2) ** -52, mpmath.mpf(tiny)), (y, g)
+    assert np.all(np.abs(got - cuda) <= np.maximum(2 * np.spacing(np.abs(cuda)), tiny))
+    assert np.all(got >= 0.0)
 
 
 def test_cosf_accuracy(torch_cuda):

@@ -212,7 +212,7 @@ def test_cube_split_mode(gpu_ctx_factory, d, ncall, g, ita):
     assert_parity(w, o, g_)
     gm = gpu_run(gpu_ctx_factory, w, precision="mixed")
     err = np.max(np.abs(gm["I"] - o["trace_I"])) / cond_scale(w, o)
-    assert err < MIXED_BOUND, err
+    assert err < MIXED_SPLIT_BOUND, err
 
 
 def test_no_adjust_iterations_keep_grid(gpu_ctx_factory):
@@ -340,12 +340,17 @@ def test_empty_and_single_cube_ranges(gpu_ctx_factory):
 # times the error observed on GB300 (single-precision map and integrand; the
 # grids then differ by the single-precision histogram sums, whose atomic
 # order varies from run to run).  Iteration estimates relative to their
-# conditioning scale, variances relative.  Observed (I, var): corner8 2.7e-9,
-# 8.2e-7; osc10 9.2e-8, 3.7e-8; gauss3 1.3e-8, 7.1e-8.
+# conditioning scale, variances relative.  Largest observed in three runs
+# (I, var): corner8 2.8e-9, 8.2e-7; osc10 9.2e-8, 4.0e-8; gauss3 1.3e-8,
+# 8.4e-8.
 MIXED_BOUND = {"corner8": (3e-8, 1e-5), "osc10": (1e-6, 5e-7), "gauss3": (1.5e-7, 1e-6)}
 # full-size corner8 geometry on sampled ranges: observed 4.7e-8 (sum of cube
 # means relative to the sum of |means|), 1.9e-6 per histogram bin
 MIXED_FULL_SIZE = (5e-7, 2e-5)
+# Gaussians in cube-split mode (few cubes of many samples, each thread's
+# single-precision shifted sums over hundreds of samples): observed 1.9e-8,
+# 6.8e-8 and 7.5e-9 for the three cases below
+MIXED_SPLIT_BOUND = 7e-7
 
 
 @pytest.mark.parametrize("make,ncall", [(W.corner8, 400_000), (W.osc10, 400_000), (W.gauss3, 2 ** 18)])

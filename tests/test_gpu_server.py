@@ -13,13 +13,15 @@ from paper_2202_01753_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 # Served against solo, estimate relative to max(|I|, sigma) and sigma
-# relative: about ten times the differences observed on GB300 -- FP64 at
-# rounding level; mixed 1.1e-5 and 7.0e-4: the single-precision histogram
-# sums are grouped by the step's segments, which depend on which requests
-# share the step, and the rebinning carries their rounding from iteration to
-# iteration, most on the narrow high-dimensional peaks.
-RTOL = {"fp64": 1e-13, "mixed": 1e-4}
-STOL = {"fp64": 1e-13, "mixed": 7e-3}
+# relative: about ten times the largest differences observed on GB300 in
+# two runs -- FP64 5.0e-14 and 5.3e-11 (the oscillatory requests' variances
+# are differences of nearly equal sums, as in the parity tests); mixed
+# 1.2e-5 and 9.8e-4: the single-precision histogram sums are grouped by the
+# step's segments, which depend on which requests share the step, and the
+# rebinning carries their rounding from iteration to iteration, most on the
+# narrow high-dimensional peaks.
+RTOL = {"fp64": 1e-12, "mixed": 1e-4}
+STOL = {"fp64": 1e-9, "mixed": 1e-2}
 
 
 def _reqs(n, seed, itmax=8, rel=True):

@@ -58,11 +58,16 @@ def assert_ranks_identical(outs):
 
 @pytest.mark.parametrize("world", [2, 3])
 def test_cosmo6_shards_match_whole_iteration_oracle(torch_cuda, world):
+    # histogram bins within 2e-12 (the whole-run test holds 1e-12): the ridge
+    # exp(-(x1 + x2 - r)^2 / (2 0.01^2)) turns the last-bit differences of the
+    # mapped x (grid edges rounded differently by the kernels and the oracle)
+    # into ~1e3 times larger relative changes of F^2, and the ranks' partial
+    # histograms add one more grouping of the bin sums (observed 1.005e-12)
     w = W.cosmo6().scaled(400_000, itmax=5)
     outs = sharded_run(torch_cuda, w, world)
     assert_ranks_identical(outs)
     o = oracle_run(w)
-    assert_parity(w, o, outs[0])
+    assert_parity(w, o, outs[0], hist_tol=2e-12 * np.abs(o["hist"]) + 1e-300)
 
 
 def test_suite_shards_with_plain_iterations_and_early_stop(torch_cuda):

@@ -106,8 +106,9 @@ def parse():
     ap.add_argument("--seq-sample", type=int, default=96, help="integrals timed one by one in plain FP64")
     ap.add_argument("--ncall", type=float, default=None, help="override calls per iteration (profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--multi", default="shard", choices=["shard", "replicas"],
-                    help="N > 1: shard one integral's cubes over the ranks, or run independent replicas")
+    ap.add_argument("--multi", default="auto", choices=["auto", "shard", "replicas"],
+                    help="auto: N > 1 shards one integral's cubes over the ranks; shard: also at N = 1; "
+                         "replicas: an independent integral per rank")
     ap.add_argument("--no-extra", action="store_true",
                     help="headline only: skip the mixed-precision, batch and serving legs of the default run")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -419,13 +420,17 @@ def ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
+    # N > 1: one integral sharded over the ranks by cube range (every rank the
+    # same problem and seed), or with --multi replicas an independent copy per
+    # rank; --multi shard also runs the sharded path (NCCL included) on one GPU
+    sharded = args.multi == "shard" or (world > 1 and args.multi == "auto")
+    if world > 1 or sharded:
+        for k, v in (("MASTER_ADDR", "127.0.0.1"), ("MASTER_PORT", "29531"), ("RANK", "0"), ("WORLD_SIZE", "1")):
+            os.environ.setdefault(k, v)
+        torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     build.build()
-    # N > 1: one integral sharded over the ranks by cube range (every rank the
-    # same problem and seed), or with --multi replicas an independent copy per rank
-    sharded = world > 1 and args.multi == "shard"
     w = workload(args, 0 if sharded else rank)
     K, Wm = args.steps, args.warmup
     stream = torch.cuda.current_stream()
@@ -514,7 +519,7 @@ def ours(args):
     d2h = 88
 
     if rank != 0:
-        if world > 1:
+        if dist.is_initialized():
             dist.destroy_process_group()
         return 0
 
@@ -593,7 +598,8 @@ def ours(args):
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
                 "call": "mcubes_integrate (host params/bounds/result), %d iterations" % K},
-        "gpu_launches": kt["sample_launches"] + kt["refine_launches"],
+        # sampling + refinement per iteration; sharded also the range reduction and the rank-order combine
+        "gpu_launches": (kt["sample_launches"] + kt["refine_launches"]) * (2 if sharded else 1),
         "clocks": clk,
         "alu_peaks": {"ffma_tflops": 2 * pk["ffma_per_s"] / 1e12, "dfma_tflops": 2 * pk["dfma_per_s"] / 1e12,
                       "fp64_inst_per_clk_per_sm": {k: pk[f"{k}_per_s"] / (sms * sm_mhz * 1e6) if sm_mhz else None
@@ -604,7 +610,7 @@ def ours(args):
         **extra,
     }
     print(json.dumps(line))
-    if world > 1:
+    if dist.is_initialized():
         dist.destroy_process_group()
     return 0
 

@@ -20,7 +20,6 @@
 
 #include <type_traits>
 
-#include "fp_bits.cuh"
 #include "mc_device.cuh"
 
 namespace mc {
@@ -45,61 +44,11 @@ __device__ __forceinline__ void hist_add(uint32_t base, uint32_t idx, double v)
 // different axes' histograms and half as many lanes compete for the same
 // bins.  The single-precision add is a native reduction; there the swap
 // measured slower and is not made.
-#ifndef MC_HIST_CAS
-#define MC_HIST_CAS 1
-#endif
-
-__device__ __forceinline__ uint64_t lds_u64(uint32_t addr)
-{
-    uint64_t v;
-    asm volatile("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
-    return v;
-}
-__device__ __forceinline__ uint64_t cas_shared_u64(uint32_t addr, uint64_t expect, uint64_t val)
-{
-    uint64_t old;
-    asm volatile("atom.shared.cas.b64 %0, [%1], %2, %3;" : "=l"(old) : "r"(addr), "l"(expect), "l"(val) : "memory");
-    return old;
-}
-
-// Adds v (>= 0) to the shared-memory double at addr, whose value the caller
-// read as `seen`: the first attempt adds on the FP64 pipe; an attempt that
-// finds the word changed (another lane or warp added to the bin in between)
-// retries with the exact integer addition of fp_bits.cuh, so that the few
-// lanes of a retry do not take whole FP64 warp slots.
-__device__ __forceinline__ void hist_cas_add(uint32_t addr, uint64_t seen, double v)
-{
-    const uint64_t vb = (uint64_t)__double_as_longlong(v);
-    uint64_t want = (uint64_t)__double_as_longlong(__longlong_as_double((long long)seen) + v);
-    uint64_t got = cas_shared_u64(addr, seen, want);
-    while (got != seen) {
-        seen = got;
-        want = add_nonneg_bits(seen, vb);
-        got = cas_shared_u64(addr, seen, want);
-    }
-}
-
 template <int NB4, class HT>
 __device__ __forceinline__ void hist_add_sample(uint32_t hist_s, const uint32_t (&idx)[2 * NB4], uint32_t hist_d,
                                                 HT F2)
 {
     const uint32_t odd = sizeof(HT) == 8 ? (threadIdx.x & 1u) : 0u;
-    if constexpr (sizeof(HT) == 8 && MC_HIST_CAS) {
-        // both bins of a word are read before either is written (two loads in
-        // flight, two FP64 adds back to back)
-#pragma unroll
-        for (int k = 0; k < 2 * NB4; ++k) {
-            if (2 * k < (int)hist_d) {
-                const uint32_t w = __funnelshift_l(idx[k], idx[k], odd << 4);  // halves swapped on odd lanes
-                const bool e0 = ((2u * k) ^ odd) < hist_d, e1 = ((2u * k + 1u) ^ odd) < hist_d;
-                const uint32_t a0 = hist_s + 8u * (w & 0xFFFFu), a1 = hist_s + 8u * (w >> 16);
-                const uint64_t s0 = e0 ? lds_u64(a0) : 0ull, s1 = e1 ? lds_u64(a1) : 0ull;
-                if (e0) hist_cas_add(a0, s0, (double)F2);
-                if (e1) hist_cas_add(a1, s1, (double)F2);
-            }
-        }
-        return;
-    }
 #pragma unroll
     for (int k = 0; k < 2 * NB4; ++k) {
         if (2 * k < (int)hist_d) {
@@ -168,11 +117,6 @@ __device__ __forceinline__ void stage_cells(typename Prec<MIXED>::Cell* cells, t
 template <class F, class = void> struct RolledAxes { static constexpr bool value = false; };
 template <class F> struct RolledAxes<F, decltype((void)F::kRolled)> { static constexpr bool value = F::kRolled; };
 
-#ifndef MC_AXIS_UNROLL
-#define MC_AXIS_UNROLL 1
-#endif
-constexpr int kAxisUnroll = MC_AXIS_UNROLL;
-
 // sample_point for FP64 families with heavy per-axis work (a logarithm per
 // axis): the same arithmetic with the axes as a loop that is not unrolled,
 // so the per-axis code exists once instead of D times.  Unrolled, a six-axis
@@ -182,7 +126,8 @@ constexpr int kAxisUnroll = MC_AXIS_UNROLL;
 // the Philox block of axes 4b..4b+3 is drawn at j = 4b and its words are
 // rotated into place, and the flat bin indices are shifted into idx from the
 // top, so that after the last axis axis j's index is field j (the layout
-// sample_point leaves).
+// sample_point leaves).  (Unrolled by two or three the loop measured slower:
+// 9.55 and 9.69 ms against 8.80 ms per 1e8-call cosmo6 pass.)
 template <int FAM, int NB4, int D, class A>
 __device__ __forceinline__ double sample_point_rolled(const A& a, const double2* cells, uint32_t c, uint32_t s,
                                                       uint32_t it, uint32_t (&idx)[2 * NB4])
@@ -197,7 +142,7 @@ __device__ __forceinline__ double sample_point_rolled(const A& a, const double2*
     uint4 r = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
     for (int k = 0; k < 2 * NB4; ++k) idx[k] = 0u;
-#pragma unroll kAxisUnroll
+#pragma unroll 1
     for (int j = 0; j < D; ++j) {
         if ((j & 3) == 0) r = sample_words(a, make_uint4(s, c, it, (uint32_t)(j >> 2)));
         const uint32_t w = r.x;
@@ -567,7 +512,7 @@ template <int FAM, bool MIXED, int D>
 constexpr int vsample_kernel_min_blocks()
 {
     return vsample_threads(FAM, MIXED, D) == kVsThreads ? vsample_min_blocks<FAM, MIXED, (D + 3) / 4>()
-                                                        : (FAM == MCUBES_F_COSMO6 ? MC_COSMO6_MINB : 1);
+                                                        : (FAM == MCUBES_F_COSMO6 ? kCosmo6MinBlocks : 1);
 }
 
 // One instantiation per dimension D: with the axis count a compile-time

@@ -50,7 +50,7 @@ from paper_2202_01753_gb300 import closed_forms as CF  # noqa: E402
 # "fp32_flops": 2 FFMA + FADD + FMUL per sample (the FP32-pipe fraction shown
 # beside the issue fraction).
 ROOFLINE_UNITS = {
-    ("cosmo6", "fp64"): {"kind": "fp64", "per_sample": 32.48, "traffic": 481.6e3, "pipe_busy": 0.691,
+    ("cosmo6", "fp64"): {"kind": "fp64", "per_sample": 32.37, "traffic": 319.4e3, "pipe_busy": 0.766,
                          "source": "profiles/vsample_cosmo6_fp64.md"},
     ("gauss3", "fp64"): {"kind": "fp64", "per_sample": 27.12, "traffic": 97.79e3, "pipe_busy": 0.785,
                          "source": "profiles/vsample_gauss3_fp64.md"},

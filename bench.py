@@ -619,21 +619,30 @@ def ours(args):
 # retries with more calls for integrals that end unconverged (the accuracy
 # protocol of Sec. 5.1 raises the sample count for tighter tolerances)
 # ---------------------------------------------------------------------------
-ESCALATE_FACTOR = 4
-BATCH_NCALL_MAX = 64_000_000        # 1e7 at most to start with: up to three retries
-SERVE_NCALL_MAX = 102_400_000       # 1e5 x 4^5
+RETRY_MIN, RETRY_MAX = 2.0, 64.0     # retry factor range: ncall x 2 (sigma/tau)^2, clamped
+BATCH_NCALL_MAX = 64_000_000
+SERVE_NCALL_MAX = 102_400_000
 SERVE_LOAD = 0.75                   # the steady stream's rate, as a fraction of the measured capacity
+RETRY_RULE = (f"unconverged after itmax: fresh run with ncall x 2 (sigma/tau)^2, the factor clamped to "
+              f"[{RETRY_MIN:g}, {RETRY_MAX:g}]")
 
 
 def _req(w, ncall, tol):
     return dict(fid=w.fid, params=w.params, lo=w.lo, hi=w.hi, ncall=ncall, itmax=w.itmax, rel_tol=tol, seed=w.seed)
 
 
+def _retry(ncall, r, tol, ncall_max):
+    from paper_2202_01753_gb300.retry import retry_ncall
+    if r["converged"] or r["status"] != 5 or ncall >= ncall_max:
+        return ncall
+    return retry_ncall(ncall, r["estimate"], r["sigma"], tol, 0.0, RETRY_MIN, RETRY_MAX, ncall_max)
+
+
 def batch_escalated(ctx, ws, tol, ncall_max):
     """Batched integration with retries: every round integrates the still
-    unconverged integrals in one batch with ESCALATE_FACTOR x their previous
-    calls (while <= ncall_max).  Returns (final results, wall seconds,
-    rounds, samples drawn)."""
+    unconverged integrals in one batch with their calls sized by the retry
+    rule (paper_2202_01753_gb300.retry, the server's).  Returns (final
+    results, wall seconds, rounds, samples drawn)."""
     out = [None] * len(ws)
     ncall = [w.ncall for w in ws]
     todo = list(range(len(ws)))
@@ -646,8 +655,9 @@ def batch_escalated(ctx, ws, tol, ncall_max):
         for i, r in zip(todo, res):
             out[i] = r
             samples += r["samples_per_iter"] * r["iterations"]
-            if not r["converged"] and r["status"] == 5 and ncall[i] * ESCALATE_FACTOR <= ncall_max:
-                ncall[i] *= ESCALATE_FACTOR
+            more = _retry(ncall[i], r, tol, ncall_max)
+            if more > ncall[i]:
+                ncall[i] = more
                 nxt.append(i)
         todo = nxt
     return out, time.perf_counter() - t0, rounds, samples
@@ -659,9 +669,10 @@ def solo_escalated(ctx, w, tol, ncall_max):
     while True:
         ctx.set_opts(seed=w.seed)
         r = ctx.integrate(w.fid, w.params, w.lo, w.hi, ncall, w.itmax, tol)
-        if r["converged"] or r["status"] != 5 or ncall * ESCALATE_FACTOR > ncall_max:
+        more = _retry(ncall, r, tol, ncall_max)
+        if more <= ncall:
             return r
-        ncall *= ESCALATE_FACTOR
+        ncall = more
 
 
 # ---------------------------------------------------------------------------
@@ -705,7 +716,7 @@ def batch_leg(args, local):
         "rel_tol": tol, "integrals": len(ws), "converged": n_conv, "converged_fraction": n_conv / len(ws),
         "unconverged_fraction": 1.0 - n_conv / len(ws), "seconds": t_batch, "rounds": rounds,
         "evals_per_s": samples / t_batch, "precision": "mixed",
-        "retry_rule": f"unconverged after itmax: calls x{ESCALATE_FACTOR}, fresh start, while <= {BATCH_NCALL_MAX:.3g}",
+        "retry_rule": f"{RETRY_RULE}, calls <= {BATCH_NCALL_MAX:.3g}",
         "sequential_fp64": {"integrals_per_s_at_tol": seq_conv_per_s, "sample": f"{len(idx)} integrals",
                             "converged_fraction": statistics.mean(seq_conv),
                             "batched_converged_fraction_same_sample": statistics.mean([conv[i] for i in idx]),
@@ -756,7 +767,7 @@ def serve_leg(args, local):
     ctx = mcubes.Context(local, precision="mixed")
     srv = mcubes.Server(ctx, itcap=20)
     srv.set_step_iterations(args.serve_iters)
-    srv.set_escalation(ESCALATE_FACTOR, SERVE_NCALL_MAX)
+    srv.set_retry_sized(RETRY_MIN, RETRY_MAX, SERVE_NCALL_MAX)
     pct = lambda a, q: 1e3 * float(np.percentile(a, q)) if len(a) else None  # noqa: E731
 
     def run(stream, at_once=False):
@@ -809,8 +820,7 @@ def serve_leg(args, local):
                           "load": f"{SERVE_LOAD} x the measured capacity"},
         "precision": "mixed", "iterations_per_step": args.serve_iters,
         "request_mix": "d 3..12, rel_tol log-uniform [1e-5, 1e-3], gauss/corner/osc, 1e5 calls x 20 iterations",
-        "retry_rule": f"unconverged after itmax: calls x{ESCALATE_FACTOR}, fresh start, ahead of new arrivals, "
-                      f"while <= {SERVE_NCALL_MAX:.3g}",
+        "retry_rule": f"{RETRY_RULE}, ahead of new arrivals, calls <= {SERVE_NCALL_MAX:.3g}",
         "sequential_fp64": {"integrals_per_s_at_tol": seq_rate, "sample": f"{len(idx)} requests of the offered stream",
                             "converged_fraction": statistics.mean(seq_conv),
                             "speedup_of_served_capacity": cap["integrals_per_s_at_tol"] / seq_rate if seq_rate else None,

@@ -263,6 +263,18 @@ mcubes_status mcubes_server_set_step_iterations(mcubes_server* srv, int iters);
  * EINVAL (factor outside [1, 1024], ncall_max < 0). */
 mcubes_status mcubes_server_set_escalation(mcubes_server* srv, double factor, long long ncall_max);
 
+/* The same retries with the calls sized from the attempt that failed: its
+ * sigma against the tolerance tau = max(abs_tol, rel_tol |estimate|)
+ * predicts the calls that reach tau, sigma falling as (calls x
+ * iterations)^-1/2, so the retry runs ncall x 2 (sigma/tau)^2 calls per
+ * iteration, the factor clamped to [min_factor, max_factor] (max_factor when
+ * tau is 0) and the calls to ncall_max; a request already at ncall_max is
+ * reported.  Replaces the rule of mcubes_server_set_escalation (and the
+ * other way round).  Errors: EINVAL (min_factor <= 1, max_factor < min_factor
+ * or > 1024, ncall_max < 0). */
+mcubes_status mcubes_server_set_retry_sized(mcubes_server* srv, double min_factor, double max_factor,
+                                            long long ncall_max);
+
 /* Copies up to cap finished results (and their tags) not yet returned;
  * *n receives how many were copied. */
 mcubes_status mcubes_server_poll(mcubes_server* srv, long long* tags, mcubes_result* results, int cap, int* n);

@@ -4,6 +4,7 @@
 // request by one iteration (each at its own iteration index) in one set of
 // graph-replayed launches, and retires the finished ones.  Host code only.
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <deque>
 #include <new>
@@ -64,6 +65,7 @@ struct mcubes_server {
     std::unordered_map<long long, Open> open;
     long long next_id = 0;
     double esc_factor = 1.0;     // calls x factor on a retry (1: no retries)
+    double esc_max_factor = 0.0; // > 0: the factor is sized from the attempt's sigma, up to this
     long long esc_ncall_max = 0;
     std::vector<std::pair<long long, mcubes_result>> finished;  // not yet polled
     long long completed = 0;
@@ -75,6 +77,30 @@ struct mcubes_server {
 // Tags from 2^62 up are the server's own: mcubes_server_run_stream tags
 // request i of its k-th call 2^62 + (k mod 2^30) 2^31 + i.
 constexpr long long kStreamTagBase = 1ll << 62;
+
+// Calls per iteration of a retry.  Fixed rule (max_factor = 0): ncall x
+// factor while that stays <= ncall_max (else none: returns ncall).  Sized
+// rule: the attempt's sigma against the tolerance tau = max(abs_tol,
+// rel_tol |estimate|) predicts the calls that reach it, since sigma falls as
+// (calls x iterations)^-1/2 -- ncall x 2 (sigma / tau)^2, the factor clamped
+// to [factor, max_factor] (max_factor when tau is not positive), the calls
+// to ncall_max.
+static long long retry_ncall(const mcubes_request& r, const mcubes_result& res, double factor, double max_factor,
+                             long long ncall_max)
+{
+    if (max_factor <= 0.0) {
+        const double more = (double)r.ncall * factor;
+        return more <= (double)ncall_max ? (long long)more : r.ncall;
+    }
+    const double tau = std::max(r.abs_tol, r.rel_tol * std::fabs(res.estimate));
+    double k = max_factor;
+    if (tau > 0.0 && std::isfinite(res.sigma)) {
+        const double q = res.sigma / tau;
+        k = std::min(max_factor, std::max(factor, 2.0 * q * q));
+    }
+    const double more = std::min((double)r.ncall * k, (double)ncall_max);
+    return (long long)more;
+}
 
 // Queues a caller's request under a new internal id.
 static void server_enqueue(mcubes_server* s, const mcubes_request& r, long long tag)
@@ -92,11 +118,11 @@ static void server_retire(mcubes_server* s, long long id, const mcubes_result& r
     auto it = s->open.find(id);
     if (it == s->open.end()) return;
     mcubes_request& r = it->second.req.r;
-    const double more = (double)r.ncall * s->esc_factor;
-    if (res.status == MCUBES_ENOCONV && s->esc_factor > 1.0 && more <= (double)s->esc_ncall_max) {
+    if (res.status == MCUBES_ENOCONV && s->esc_factor > 1.0 && r.ncall < s->esc_ncall_max) {
+        const long long more = retry_ncall(r, res, s->esc_factor, s->esc_max_factor, s->esc_ncall_max);
         mcubes_request next = r;
-        next.ncall = (long long)more;
-        if (s->engine->validate(next) == MCUBES_OK) {
+        next.ncall = more;
+        if (more > r.ncall && s->engine->validate(next) == MCUBES_OK) {
             r.ncall = next.ncall;
             s->queue.emplace_front(next, id);
             return;
@@ -166,6 +192,18 @@ mcubes_status mcubes_server_set_escalation(mcubes_server* s, double factor, long
 {
     if (!s || !(factor >= 1.0) || !(factor <= 1024.0) || ncall_max < 0) return MCUBES_EINVAL;
     s->esc_factor = factor;
+    s->esc_max_factor = 0.0;
+    s->esc_ncall_max = ncall_max;
+    return MCUBES_OK;
+}
+
+mcubes_status mcubes_server_set_retry_sized(mcubes_server* s, double min_factor, double max_factor,
+                                            long long ncall_max)
+{
+    if (!s || !(min_factor > 1.0) || !(max_factor >= min_factor) || !(max_factor <= 1024.0) || ncall_max < 0)
+        return MCUBES_EINVAL;
+    s->esc_factor = min_factor;
+    s->esc_max_factor = max_factor;
     s->esc_ncall_max = ncall_max;
     return MCUBES_OK;
 }

@@ -30,7 +30,7 @@ EXPORTED = [
     "mcubes_selftest_fxmath", "mcubes_state_size", "mcubes_state_export", "mcubes_state_import",
     "mcubes_problem_get", "mcubes_get_opts", "mcubes_tables_set", "mcubes_server_set_step_iterations",
     "mcubes_selftest_rebin", "mcubes_shard_partial_len", "mcubes_shard_sample", "mcubes_shard_finish",
-    "mcubes_server_set_escalation", "mcubes_batch_trace_get",
+    "mcubes_server_set_escalation", "mcubes_batch_trace_get", "mcubes_server_set_retry_sized",
 ]
 
 
@@ -116,6 +116,8 @@ def lib():
                 "mcubes_server_step": (ctypes.c_int, [ctypes.c_void_p, P(ctypes.c_int)]),
                 "mcubes_server_set_step_iterations": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
                 "mcubes_server_set_escalation": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ll]),
+                "mcubes_server_set_retry_sized": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                                                  ll]),
                 "mcubes_server_poll": (ctypes.c_int, [ctypes.c_void_p, P(ll), P(mcubes_result), ctypes.c_int,
                                                       P(ctypes.c_int)]),
                 "mcubes_server_stats": (ctypes.c_int, [ctypes.c_void_p, P(ll), P(ll), P(ll), P(ll), P(ll)]),
@@ -450,6 +452,11 @@ class Server:
         """Retry a request that ends unconverged with factor x its calls (up to ncall_max)."""
         self.ctx._check(lib().mcubes_server_set_escalation(self._h, float(factor), int(ncall_max)),
                         "mcubes_server_set_escalation")
+
+    def set_retry_sized(self, min_factor: float, max_factor: float, ncall_max: int):
+        """Retry an unconverged request with its calls sized from its sigma (see mcubes.h)."""
+        self.ctx._check(lib().mcubes_server_set_retry_sized(self._h, float(min_factor), float(max_factor),
+                                                            int(ncall_max)), "mcubes_server_set_retry_sized")
 
     def step(self):
         ran = ctypes.c_int()

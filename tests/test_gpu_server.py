@@ -234,3 +234,53 @@ def test_reserved_tags_and_escalation_arguments(gpu_ctx_factory):
             srv.set_escalation(*bad)
     srv.close()
     ctx.close()
+
+
+def _solo_sized(make_ctx, w, precision, lo, hi, ncall_max):
+    """The sized retry rule written out on solo runs (paper_2202_01753_gb300.retry)."""
+    from paper_2202_01753_gb300.retry import retry_ncall
+    ncall = w.ncall
+    while True:
+        ctx = make_ctx(seed=w.seed, precision=precision)
+        r = ctx.integrate(w.fid, w.params, w.lo, w.hi, ncall, w.itmax, w.rel_tol, w.abs_tol)
+        ctx.close()
+        if r["converged"] or r["status"] != mcubes.ENOCONV or ncall >= ncall_max:
+            return r
+        more = retry_ncall(ncall, r["estimate"], r["sigma"], w.rel_tol, w.abs_tol, lo, hi, ncall_max)
+        if more <= ncall:
+            return r
+        ncall = more
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_sized_retries_match_the_rule_run_alone(gpu_ctx_factory, precision):
+    """Retries sized from the failed attempt's sigma: each result equals the
+    request run alone with the same rule, and the rule both retries and caps."""
+    ws = _reqs(24, seed=32, itmax=6)
+    for w in ws:
+        w.rel_tol = 2e-4
+    lo, hi, ncall_max = 2.0, 64.0, 3_000_000
+    ctx = gpu_ctx_factory(precision=precision)
+    srv = mcubes.Server(ctx, itcap=16)
+    srv.set_retry_sized(lo, hi, ncall_max)
+    for i, w in enumerate(ws):
+        srv.submit(_dict(w), i)
+    results, steps = {}, 0
+    while len(results) < len(ws):
+        srv.step()
+        steps += 1
+        results.update(dict(srv.poll()))
+        assert steps < 400
+    srv.close()
+    ctx.close()
+    retried = capped = 0
+    for i, w in enumerate(ws):
+        solo = _solo_sized(gpu_ctx_factory, w, precision, lo, hi, ncall_max)
+        assert results[i]["samples_per_iter"] == solo["samples_per_iter"]
+        retried += solo["samples_per_iter"] > w.ncall
+        capped += not solo["converged"]
+        _check(w, results[i], solo, precision)
+    assert retried > 0
+    with pytest.raises(mcubes.McubesError):
+        bad = mcubes.Server(gpu_ctx_factory(), itcap=4)
+        bad.set_retry_sized(1.0, 8.0, 10 ** 6)        # the smallest factor must exceed 1

@@ -27,7 +27,6 @@ constexpr int kVsThreadsMax = 1024; // largest block of a single-integral sampli
 // SM: measured 8.19 ms per 1e8-call pass against 8.39 (2 x 512), 8.54
 // (2 x 448), 8.94 (3 x 320), 8.92 (3 x 288) and 8.79 ms (3 x 256).
 constexpr int kCosmo6Threads = 1024;
-constexpr int kCosmo6MinBlocks = 1;
 __host__ __device__ constexpr int vsample_threads(int family, bool mixed, int d)
 {
     return (family == MCUBES_F_COSMO6 && !mixed && d == 6) ? kCosmo6Threads : kVsThreads;

@@ -117,6 +117,18 @@ __device__ __forceinline__ void stage_cells(typename Prec<MIXED>::Cell* cells, t
 template <class F, class = void> struct RolledAxes { static constexpr bool value = false; };
 template <class F> struct RolledAxes<F, decltype((void)F::kRolled)> { static constexpr bool value = F::kRolled; };
 
+// Only FP64 families with heavy per-axis work are rolled.  The mixed corner
+// and oscillatory kernels, whose per-axis work is a few instructions with
+// the axis's constants folded into constant-bank operands when unrolled,
+// measured slower rolled (corner8 17.7 -> 21.1-23.1 ms, osc10 21.8 ->
+// 26.6-30.2 ms per 1e9-call pass, blocks of 256 to 1024 threads).
+template <int FAM, bool MIXED>
+constexpr bool rolled_axes()
+{
+    if constexpr (MIXED) return false;
+    else return RolledAxes<Family<FAM, double>>::value;
+}
+
 // sample_point for FP64 families with heavy per-axis work (a logarithm per
 // axis): the same arithmetic with the axes as a loop that is not unrolled,
 // so the per-axis code exists once instead of D times.  Unrolled, a six-axis
@@ -128,16 +140,20 @@ template <class F> struct RolledAxes<F, decltype((void)F::kRolled)> { static con
 // top, so that after the last axis axis j's index is field j (the layout
 // sample_point leaves).  (Unrolled by two or three the loop measured slower:
 // 9.55 and 9.69 ms against 8.80 ms per 1e8-call cosmo6 pass.)
-template <int FAM, int NB4, int D, class A>
-__device__ __forceinline__ double sample_point_rolled(const A& a, const double2* cells, uint32_t c, uint32_t s,
-                                                      uint32_t it, uint32_t (&idx)[2 * NB4])
+template <int FAM, bool MIXED, int NB4, int D, class A>
+__device__ __forceinline__ typename Prec<MIXED>::R
+sample_point_rolled(const A& a, const typename Prec<MIXED>::Cell* cells, uint32_t c, uint32_t s, uint32_t it,
+                    uint32_t (&idx)[2 * NB4])
 {
-    using Fam = Family<FAM, double>;
+    using R = typename Prec<MIXED>::R;
+    using Fam = Family<FAM, R>;
     constexpr int NW = (D + 1) / 2;  // index words in use
     const uint32_t nb = a.nb;
     typename Fam::S fs;
     Fam::begin(fs);
-    IntProd jp = int_prod_of(a.jac0);
+    R jac = R(1);          // mixed: single-precision product of the widths
+    IntProd jp{0, 0};      // FP64: the product in integer arithmetic, from jac0
+    if constexpr (!MIXED) jp = int_prod_of(a.jac0);
     uint32_t rest = c;
     uint4 r = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
@@ -154,9 +170,15 @@ __device__ __forceinline__ double sample_point_rolled(const A& a, const double2*
         rest = q;
         const BinPos bp = bin_pos(w, dig * nb, nb, a.g, a.gmagic);
         const uint32_t flat = (uint32_t)j * nb + bp.k;
-        const double2 cell = cells[flat];
-        const double x = fma(cell.y, bin_gphi_f64(bp), cell.x);   // (width/g)(g phi)
-        int_prod_mul(jp, cell.y);
+        const auto cell = cells[flat];
+        R x;
+        if constexpr (MIXED) {
+            x = fmaf(cell.y, bin_phi_f32(bp, a.phi_scale_f), cell.x);   // (nb width)(phi/nb)
+            jac *= cell.y;
+        } else {
+            x = fma(cell.y, bin_gphi_f64(bp), cell.x);                    // (width/g)(g phi)
+            int_prod_mul(jp, cell.y);
+        }
         Fam::add(fs, j, x, a.fam);
 #pragma unroll
         for (int k = 0; k < NW - 1; ++k) idx[k] = __funnelshift_r(idx[k], idx[k + 1], 16);
@@ -167,7 +189,8 @@ __device__ __forceinline__ double sample_point_rolled(const A& a, const double2*
         for (int k = 0; k < NW - 1; ++k) idx[k] = __funnelshift_r(idx[k], idx[k + 1], 16);
         idx[NW - 1] >>= 16;
     }
-    return Fam::end(fs, D, a.fam) * int_prod_value(jp);
+    if constexpr (!MIXED) jac = int_prod_value(jp);
+    return Fam::end(fs, D, a.fam) * jac;
 }
 
 // One sample: random words -> exact bin position -> map -> integrand.
@@ -181,8 +204,8 @@ sample_point(const A& a, const typename Prec<MIXED>::Cell* cells, uint32_t c, ui
 {
     using R = typename Prec<MIXED>::R;
     using Fam = Family<FAM, R>;
-    if constexpr (!MIXED && DC > 0 && RolledAxes<Fam>::value) {
-        return sample_point_rolled<FAM, NB4, DC>(a, cells, c, s, it, idx);
+    if constexpr (DC > 0 && rolled_axes<FAM, MIXED>()) {
+        return sample_point_rolled<FAM, MIXED, NB4, DC>(a, cells, c, s, it, idx);
     }
     constexpr int DN = 4 * NB4;  // axes handled by this instantiation (d <= DN)
     const uint32_t d = DC ? (uint32_t)DC : a.d, nb = a.nb;  // DC: the dimension when fixed at compile time
@@ -512,7 +535,7 @@ template <int FAM, bool MIXED, int D>
 constexpr int vsample_kernel_min_blocks()
 {
     return vsample_threads(FAM, MIXED, D) == kVsThreads ? vsample_min_blocks<FAM, MIXED, (D + 3) / 4>()
-                                                        : (FAM == MCUBES_F_COSMO6 ? kCosmo6MinBlocks : 1);
+                                                        : 1024 / vsample_threads(FAM, MIXED, D);
 }
 
 // One instantiation per dimension D: with the axis count a compile-time

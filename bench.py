@@ -675,6 +675,46 @@ def solo_escalated(ctx, w, tol, ncall_max):
         ncall = more
 
 
+def oracle_per_result(ws, results, tols, ncall_max_samples, k):
+    """The CPU baseline of a batched or served leg, and each sampled result's
+    error against the FP64 oracle: the oracle integrates (one core, timed)
+    up to k of the integrals that converged on their first run with at most
+    ncall_max_samples calls per iteration x itmax -- the same request, seed
+    and samples as the GPU's mixed-precision run -- and the relative
+    difference of the estimates, max(|I|, sigma) of the oracle's as scale,
+    is reported per result where both ran the same iterations."""
+    import oracle
+    pick = []
+    for i, (w, r) in enumerate(zip(ws, results)):
+        if len(pick) >= k:
+            break
+        if not r["converged"] or w.ncall * w.itmax > ncall_max_samples:
+            continue
+        g, m, p = oracle.geometry(w.d, w.ncall, 0, w.nb)
+        if r["samples_per_iter"] == m * p:            # no retry: the request's own calls
+            pick.append(i)
+    errs, n_same, samples = [], 0, 0
+    t = time.perf_counter()
+    outs = [oracle.integrate(ws[i].fid, ws[i].params, ws[i].lo, ws[i].hi, ws[i].ncall, ws[i].itmax, nb=ws[i].nb,
+                             seed=ws[i].seed, rel_tol=tols[i]) for i in pick]
+    dt = time.perf_counter() - t
+    for i, o in zip(pick, outs):
+        samples += o["m"] * o["p"] * o["iterations"]
+        if o["iterations"] == results[i]["iterations"]:
+            n_same += 1
+            errs.append(abs(results[i]["estimate"] - o["estimate"]) / max(abs(o["estimate"]), o["sigma"]))
+    return {
+        "error_vs_fp64_oracle": {
+            "per_result": errs, "max": max(errs) if errs else None,
+            "median": statistics.median(errs) if errs else None,
+            "sample": f"{len(pick)} converged results without retries ({n_same} with the oracle's iteration "
+                      f"count; the estimates' difference relative to max(|I|, sigma))"},
+        "cpu_baseline": {"value": len(pick) / dt if dt > 0 else None, "unit": "integrals/s", "cores": 1,
+                         "kind": "oracle", "evals_per_s": samples / dt if dt > 0 else None,
+                         "sample": f"the same {len(pick)} integrals, one process ({dt:.1f} s)"},
+    }
+
+
 # ---------------------------------------------------------------------------
 # batched integrals: integrals/s at rel_tol of the batched mixed-precision
 # path against the plain per-integral FP64 path on the same GPU
@@ -711,6 +751,7 @@ def batch_leg(args, local):
     solo.close()
     n_conv = sum(conv)
     seq_conv_per_s = sum(seq_conv) / t_seq
+    cpu = oracle_per_result(ws, out, [tol] * len(ws), 2_000_000, 12) if not args.no_cpu_baseline else {}
     return {
         "integrals_per_s_at_tol": n_conv / t_batch, "unit": "integrals/s",
         "rel_tol": tol, "integrals": len(ws), "converged": n_conv, "converged_fraction": n_conv / len(ws),
@@ -723,6 +764,7 @@ def batch_leg(args, local):
                             "speedup_of_batched": (n_conv / t_batch) / seq_conv_per_s if seq_conv_per_s else None,
                             "max_rel_diff_of_estimates": max(rel) if rel else None,
                             "median_rel_diff": statistics.median(rel) if rel else None},
+        **cpu,
         "clocks": clk,
     }
 
@@ -813,6 +855,8 @@ def serve_leg(args, local):
             rel.append(abs(res_o[i]["estimate"] - r["estimate"]) / max(abs(r["estimate"]), r["sigma"]))
     solo.close()
     seq_rate = sum(seq_conv) / t_seq
+    cpu = (oracle_per_result(ws_o, res_o, [w.rel_tol for w in ws_o], 2_000_000, 6)
+           if not args.no_cpu_baseline else {})
     return {
         "capacity": {**cap, "offered": "all at once"},
         "offered_stream": {**over, "offered_per_s": args.serve_rate, "stream_seconds": args.serve_seconds},
@@ -826,6 +870,7 @@ def serve_leg(args, local):
                             "speedup_of_served_capacity": cap["integrals_per_s_at_tol"] / seq_rate if seq_rate else None,
                             "max_rel_diff_of_estimates": max(rel) if rel else None,
                             "median_rel_diff": statistics.median(rel) if rel else None},
+        **cpu,
         "clocks": clk,
     }
 

@@ -365,10 +365,11 @@ template <typename R> struct Family<MCUBES_F_COSMO6, R> {
     // with j known, so each axis takes only its own terms.
     // In double precision the lognormal terms are expanded, h (L - mu)^2 =
     // h L^2 - 2 h mu L + h mu^2 (c11, c12: the linear coefficients; c13: the
-    // two constants, added by the first FMA), and c10 is part of the
-    // Jacobian's constant: three FP64 instructions per sample fewer, on the
-    // pipe that bounds these kernels.  Single precision keeps the factored
-    // form (its rounding would not survive the expansion's cancellation).
+    // two constants, added by the first FMA), each axis's quadratic taken
+    // as L (h L + lin) by two FMAs, and c10 is part of the Jacobian's
+    // constant: five FP64 instructions per sample fewer, on the pipe that
+    // bounds these kernels.  Single precision keeps the factored form (its
+    // rounding would not survive the expansion's cancellation).
     static constexpr bool kWide = sizeof(R) == 8;
     // a logarithm per axis: the FP64 sampling loop runs its axes as a loop
     // (one copy of the per-axis code) instead of unrolling them
@@ -380,7 +381,7 @@ template <typename R> struct Family<MCUBES_F_COSMO6, R> {
         const R L = RealOps<R>::log_(x);
         if constexpr (kWide) {
             if (j == 0) s.e = fma(f.c[0], L, f.c[13]);
-            else if (j == 2 || j == 3) s.e = fma(L * f.c[7], L, fma(f.c[9 + j], L, s.e));
+            else if (j == 2 || j == 3) s.e = fma(L, fma(f.c[7], L, f.c[9 + j]), s.e);  // L (h L + lin) + e
             else s.e = fma(f.c[j], L, s.e);
         } else {
             s.e = j == 0 ? RealOps<R>::par(f, 0) * L : s.e + RealOps<R>::par(f, j) * L;

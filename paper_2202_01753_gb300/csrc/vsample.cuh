@@ -332,9 +332,9 @@ __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIX
                 if (n == 0) {
                     K = F;  // the shift: its own term is zero
                 } else if (n == 1) {
-                    S1 = (RS)F - (RS)K;
-                    S2 = S1 * S1;
+                    S1 = (RS)F - (RS)K;  // S2 = S1^2 is formed when needed
                 } else {
+                    if (n == 2) S2 = S1 * S1;
                     const RS z = (RS)F - (RS)K;
                     S1 += z;
                     S2 += z * z;
@@ -354,7 +354,7 @@ __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIX
                 RS mean, var;
                 if (p == 2u) {
                     mean = (RS)K + S1 * RS(0.5);
-                    var = S2;
+                    var = S1 * S1;
                 } else {
                     mean = (RS)K + S1 * inv_p;
                     var = (S2 - S1 * S1 * inv_p) * inv_var_den;
@@ -365,11 +365,13 @@ __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIX
                     if (a.want_abs) acc.fA.add(fabsf(mean));
                 } else {
                     acc.I += mean;
-                    acc.V += var;
+                    if (p == 2u) acc.V = fma(S1, S1, acc.V);  // one FMA for the z^2
+                    else acc.V += var;
                     if (a.want_abs) acc.A += fabs(mean);
                 }
             }
         } else {
+            if (n == 2) S2 = S1 * S1;
             // the cube's lanes re-base their sums on the shift of its first lane
             // (S1 += n dK, S2 += dK (2 S1 + n dK), dK = K_l - K_0; a lane without
             // samples adds nothing) and add them with XOR shuffles: no division

@@ -362,7 +362,8 @@ mcubes_status mcubes_tables_set(mcubes_ctx* ctx, int ntables, const mcubes_table
  *   checkpoint.  Errors: EINVAL (null), ESTATE (no setup).
  * mcubes_state_export: waits for the context's stream, then writes the
  *   checkpoint to buf (host, cap bytes; caller-owned).  Errors: EINVAL (null
- *   or cap too small), ESTATE, ECUDA.
+ *   or cap too small), ESTATE (no setup, or a sharded pass sampled and not
+ *   finished), ECUDA.
  * mcubes_state_import: replaces the context's options and problem with the
  *   checkpoint's (as mcubes_set_opts + mcubes_setup would), then restores
  *   its grid and iteration state; mcubes_iterate then continues with the

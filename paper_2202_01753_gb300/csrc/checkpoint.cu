@@ -99,7 +99,7 @@ mcubes_status mcubes_problem_get(mcubes_ctx* c, int* integrand_id, int* d, int* 
 mcubes_status mcubes_state_export(mcubes_ctx* c, void* buf, long long cap)
 {
     if (!c || !buf) return MCUBES_EINVAL;
-    if (!c->ready) return MCUBES_ESTATE;
+    if (!c->ready || c->shard_open) return MCUBES_ESTATE;  // a sharded pass is between sample and finish
     const size_t need = ckpt_bytes(c->d, c->nb);
     if (cap < (long long)need) return MCUBES_EINVAL;
     CkptHeader h;

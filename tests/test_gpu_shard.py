@@ -120,6 +120,8 @@ def test_shard_call_order_is_checked(torch_cuda):
         ctx.shard_sample(0, m, part.data_ptr())
     with pytest.raises(mcubes.McubesError):
         ctx.iterate(1)
+    with pytest.raises(mcubes.McubesError):            # no checkpoint between sample and finish
+        ctx.state_export()
     ctx.shard_finish(part.data_ptr(), 1)
     ctx.iterate(1)                                      # the last iteration, unsharded
     with pytest.raises(mcubes.McubesError):            # every iteration enqueued

@@ -57,8 +57,8 @@ ROOFLINE_UNITS = {
                          "source": "profiles/vsample_cosmo6_fp64.md"},
     ("gauss3", "fp64"): {"kind": "fp64", "per_sample": 27.12, "traffic": 97.79e3, "pipe_busy": 0.785,
                          "source": "profiles/vsample_gauss3_fp64.md"},
-    ("table6", "fp64"): {"kind": "fp64", "per_sample": 43.26, "dram_bytes_per_sample": 409.2, "traffic": 38.5035e9,
-                         "pipe_busy": 0.736,
+    ("table6", "fp64"): {"kind": "fp64", "per_sample": 43.76, "dram_bytes_per_sample": 409.2, "traffic": 38.5035e9,
+                         "pipe_busy": 0.729,
                          "source": "profiles/vsample_table6_fp64.md"},
     ("corner8", "mixed"): {"kind": "issue", "per_sample": 543.0, "traffic": 466.9e3, "fp32_flops": 99.23,
                            "source": "profiles/vsample_corner8_mixed.md"},

@@ -52,7 +52,7 @@ from paper_2202_01753_gb300 import closed_forms as CF  # noqa: E402
 # "fp32_flops": 2 FFMA + FADD + FMUL per sample (the FP32-pipe fraction shown
 # beside the issue fraction).
 ROOFLINE_UNITS = {
-    ("cosmo6", "fp64"): {"kind": "fp64", "per_sample": 30.87, "issue_per_sample": 2201.5, "traffic": 319.4e3,
+    ("cosmo6", "fp64"): {"kind": "fp64", "per_sample": 30.87, "issue_per_sample": 2201.5, "traffic": 336.1e3,
                          "pipe_busy": 0.721,
                          "source": "profiles/vsample_cosmo6_fp64.md"},
     ("gauss3", "fp64"): {"kind": "fp64", "per_sample": 27.12, "traffic": 97.79e3, "pipe_busy": 0.785,

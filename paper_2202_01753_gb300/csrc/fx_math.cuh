@@ -7,15 +7,19 @@
 // table-driven methods ("Table-driven implementation of the logarithm
 // function in IEEE floating-point arithmetic", ACM TOMS 16(4), 1990; "...of
 // the exponential function...", ACM TOMS 15(2), 1989) with 256-entry tables
-// (fx_tables.h, generated by gen_fx_tables.py), but evaluate the reduced
-// argument's series in fixed-point integers: the logarithm uses no FP64
-// operation (its table point is the one at or below the mantissa, so its
-// series runs on unsigned high multiplies; its parts are summed as a 128-bit
-// fixed-point number and rounded to a double with integer operations), the
-// exponential none either (n = round(y 256/ln 2) from y's significand by one
-// high multiply; r = y - n ln2/256 is formed from the low 64 bits of its two
-// terms and made non-negative, so its series also runs on unsigned high
-// multiplies).
+// (fx_tables.h, generated by gen_fx_tables.py), applied twice -- a second
+// 256-entry table step takes the reduced argument from below 2^-8 to below
+// 2^-16, so that three series terms, formed with 32-bit multiplies, replace
+// seven and the long chain of dependent 64-bit multiplies -- and evaluate
+// everything in fixed-point integers: the logarithm uses no FP64 operation
+// (its table points are the ones at or below the argument, so every quantity
+// is non-negative; its parts are summed as a 128-bit fixed-point number and
+// rounded to a double with integer operations), the exponential none either
+// (n = round(y 256/ln 2) from y's significand by one high multiply;
+// r = y - n ln2/256 is formed from the low 64 bits of its two terms and made
+// non-negative).  fx_exp_neg_scaled multiplies the result by a 64-bit
+// fixed-point factor before its single rounding (the FP64 kernels' Jacobian,
+// kept as an integer product), which saves the FP64 multiply after it.
 //
 // Accuracy (tested against 60-digit references): fx_exp within 1 ulp
 // (subnormal results within one unit of their last place);
@@ -62,14 +66,13 @@ __device__ __forceinline__ double q64_to_double(uint64_t hi, uint64_t lo, bool n
 static __device__ __noinline__ double log_slow(double x) { return log(x); }
 static __device__ __noinline__ double exp_slow(double y) { return exp(y); }
 
-// Constants of the series: round(2^32 / k), round(2^62 / k) and round(2^63 / k).
+// Constant of the series: round(2^32 / k).
 __host__ __device__ constexpr uint32_t q32_inv(uint32_t k) { return (uint32_t)((((uint64_t)1 << 32) + k / 2) / k); }
-__host__ __device__ constexpr uint64_t q62_inv(uint64_t k) { return (((uint64_t)1 << 62) + k / 2) / k; }
-__host__ __device__ constexpr uint64_t q63_inv(uint64_t k) { return (((uint64_t)1 << 63) + k / 2) / k; }
 
-// ln x = e ln 2 + ln c_j + ln(1 + r) for x = 2^e m, c_j = 1 + j/256 the table
-// point at or below m and r = (m - c_j)/c_j in [0, 2^-8): every quantity is
-// non-negative, so the series runs on unsigned high multiplies.
+// ln x = e ln 2 + ln c_j + ln d_k + ln(1 + r2) for x = 2^e m, c_j = 1 + j/256
+// the table point at or below m, r = (m - c_j)/c_j in [0, 2^-8), d_k =
+// 1 + k/65536 the second table point at or below 1 + r and r2 = (r - k/65536)/d_k
+// in [0, 2^-16): every quantity is non-negative.
 __device__ __forceinline__ double fx_log(double x)
 {
     const uint64_t u = (uint64_t)__double_as_longlong(x);
@@ -79,22 +82,25 @@ __device__ __forceinline__ double fx_log(double x)
     const int j = (int)(f >> 44);
     // m - c_j is the mantissa's low 44 bits (Q52); r = (m - c_j)/c_j in Q64 (< 2^56)
     const uint64_t r = __umul64hi((f & 0xFFFFFFFFFFFull) << 13, __ldg(&kLogInvC[j]));
-    // ln(1 + r) = r (1 - r (1/2 - r (1/3 - r (1/4 - r (1/5 - r (1/6 - r/7)))))) (+ r^8/8 < 2^-67),
-    // every bracket positive.  The three innermost reach the result multiplied by
-    // r^4 < 2^-32, so they run in Q32 with 32-bit high multiplies; the rest in Q63.
-    const uint32_t r32 = (uint32_t)(r >> 32);
-    uint32_t t = q32_inv(7);
-    t = q32_inv(6) - __umulhi(r32, t);
-    t = q32_inv(5) - __umulhi(r32, t);
-    t = q32_inv(4) - __umulhi(r32, t);
-    uint64_t s = q63_inv(3) - __umul64hi(r, (uint64_t)t << 31);
-    s = q63_inv(2) - __umul64hi(r, s);
-    s = q63_inv(1) - __umul64hi(r, s);
-    const uint64_t l1 = __umul64hi(r, s);                  // ln(1 + r), Q63
-    const uint64_t U = __ldg(&kLogCQ64[j]) + (l1 << 1);    // ln m, Q64 (< ln 2)
-    // e ln 2 + ln m as sign and 128-bit magnitude in Q64
-    const uint64_t ae = (uint64_t)(e < 0 ? -e : e);
-    const uint64_t plo = ae * kLn2Q64, phi = __umul64hi(ae, kLn2Q64);
+    // second step: k = the top 8 bits of r (r < 2^-8), r - k/65536 its low 48 bits
+    // (Q64); r2 = (r - k/65536)/d_k in Q64 (< 2^48)
+    const int k = (int)(r >> 48);
+    const uint64_t R = __umul64hi((r & 0xFFFFFFFFFFFFull) << 16, __ldg(&kLogInvD[k])) >> 15;
+    // ln(1 + r2) = r2 - r2^2/2 + r2^3/3 (+ r2^4/4 < 2^-66).  r2^2 from the top 32
+    // bits of r2 (H = r2 in Q48; the dropped low bits move it by < 2^-62) and
+    // r2^3 < 2^-48 from r2^2 and H, both with 32 x 32-bit products.
+    const uint32_t H = (uint32_t)(R >> 16);
+    const uint64_t sq = ((uint64_t)H * H) >> 32;                           // r2^2, Q64 (< 2^32)
+    const uint32_t cube = (uint32_t)(((uint64_t)(uint32_t)sq * H) >> 48);  // r2^3, Q64 (< 2^16)
+    const uint64_t l2 = R - (sq >> 1) + __umulhi(cube, q32_inv(3));        // ln(1 + r2), Q64
+    const uint64_t U = __ldg(&kLogCQ64[j]) + __ldg(&kLogDQ64[k]) + l2;     // ln m, Q64 (< ln 2)
+    // e ln 2 + ln m as sign and 128-bit magnitude in Q64; |e| < 2^11, so
+    // |e| ln 2 is two 32 x 32-bit products (ln 2 = L1 2^32 + L0)
+    const uint32_t ae = (uint32_t)(e < 0 ? -e : e);
+    const uint64_t p0 = (uint64_t)ae * (uint32_t)kLn2Q64;
+    const uint64_t p1 = (uint64_t)ae * (uint32_t)(kLn2Q64 >> 32);
+    const uint64_t plo = p0 + (p1 << 32);
+    const uint64_t phi = (p1 >> 32) + (plo < p0 ? 1ull : 0ull);
     uint64_t lo, hi;
     bool neg = false;
     if (e >= 0) {
@@ -114,8 +120,12 @@ __device__ __forceinline__ double fx_log(double x)
     return q64_to_double(hi, lo, neg);
 }
 
-// exp of the double with bits u
-__device__ __forceinline__ double fx_exp_bits(uint64_t u)
+// exp of the double with bits u; SCALED: exp(y) (jm / 2^63) 2^je, jm in
+// [2^63, 2^64), rounded once.  The scaled form keeps the unscaled one's
+// special cases: where exp(y) alone rounds to +0 the result is +0 (as
+// exp(y) * J would be), and exp(y)'s subnormal range is scaled exactly.
+template <bool SCALED>
+__device__ __forceinline__ double fx_exp_bits_t(uint64_t u, uint64_t jm, int je)
 {
     const double y = __longlong_as_double((long long)u);
     const uint64_t ay = u & 0x7FFFFFFFFFFFFFFFull;
@@ -126,10 +136,16 @@ __device__ __forceinline__ double fx_exp_bits(uint64_t u)
         // integer rounding, so that these samples (a few percent of a narrow
         // peak's) do not send their warp through CUDA's exp with one or two
         // lanes on the FP64 pipe.  Overflow and NaN are CUDA's exp.
-        if (!(u >> 63) || ay > 0x7FF0000000000000ull) return exp_slow(y);
+        if (!(u >> 63) || ay > 0x7FF0000000000000ull) {
+            if constexpr (SCALED) return exp_slow(y) * ldexp((double)jm, je - 63);
+            else return exp_slow(y);
+        }
         if (ay > 0x408749999999999Aull) return 0.0;
     }
-    if (ay < 0x3C30000000000000ull) return 1.0;  // |y| < 2^-60: exp(y) rounds to 1
+    if (ay < 0x3C30000000000000ull) {  // |y| < 2^-60: exp(y) rounds to 1
+        if constexpr (SCALED) return ldexp((double)jm, je - 63);
+        else return 1.0;
+    }
     // y = n ln2/256 + r, n = round(y 256/ln2) from y's significand M and
     // exponent E: |y| 256/ln2 = H 2^(E-1075) to 2^-52 relative, H =
     // floor(M K / 2^53) with K = 256/ln2 in Q53, rounded at bit 1075 - E (>= 43).
@@ -158,18 +174,16 @@ __device__ __forceinline__ double fx_exp_bits(uint64_t u)
         --n;
         rq += (int64_t)kLn2Over256Q62;
     }
-    // e^r = 1 + r (1 + r (1/2 + r (1/6 + r (1/24 + r (1/120 + r/720))))) (+ r^7/5040 < 2^-72),
-    // every bracket positive.  The two innermost reach the result multiplied by
-    // r^4 < 2^-34, so they run in Q32 with 32-bit high multiplies; the rest in Q62.
-    const uint32_t r32 = (uint32_t)((uint64_t)rq >> 30);
-    uint32_t a = q32_inv(720);
-    a = q32_inv(120) + __umulhi(r32, a);
-    a = q32_inv(24) + __umulhi(r32, a);
-    const uint64_t rr = (uint64_t)rq << 2;  // r in Q64
-    uint64_t s = q62_inv(6) + __umul64hi(rr, (uint64_t)a << 30);
-    s = q62_inv(2) + __umul64hi(rr, s);
-    s = q62_inv(1) + __umul64hi(rr, s);
-    s = q62_inv(1) + __umul64hi(rr, s);
+    // e^r = e^(q/65536) e^b with q = floor(r 65536) (< 178) and b < 2^-16 (Q62 < 2^46):
+    // e^b = 1 + b + b^2/2 + b^3/6 (+ b^4/24 < 2^-68), b^2 from the top 32 bits of b
+    // (Hb = b in Q48) and b^3 from b^2 and Hb, with 32 x 32-bit products
+    const uint32_t q = (uint32_t)((uint64_t)rq >> 46);
+    const uint64_t B = (uint64_t)rq & ((1ull << 46) - 1);
+    const uint32_t Hb = (uint32_t)(B >> 14);
+    const uint64_t sqb = ((uint64_t)Hb * Hb) >> 34;                      // b^2 in Q62 (< 2^30)
+    const uint32_t cub = (uint32_t)((sqb * Hb) >> 48);                   // b^3 in Q62 (< 2^14)
+    const uint64_t eb = (1ull << 62) + B + (sqb >> 1) + __umulhi(cub, q32_inv(6));  // e^b, Q62
+    const uint64_t s = __umul64hi(__ldg(&kExpK16[q]) << 1, eb << 1);     // e^r, Q62
     // 2^(j/256) e^r in Q62, within [1, 2)
     const int j = (int)(n & 255);
     const int k = (int)(n >> 8);
@@ -179,22 +193,39 @@ __device__ __forceinline__ double fx_exp_bits(uint64_t u)
     // for eb <= 0 (y below about -708.4), the subnormal round(P 2^-(11 - eb))
     // (a carry into 2^52 is the smallest normal; below 2^-1075 it is +0)
     uint64_t Pn = P;
-    int eb = k + 1023;
+    int be = k + 1023;  // biased exponent
+    if constexpr (SCALED) {
+        Pn = __umul64hi(P << 1, jm);  // Q62, a value in [1, 4)
+        be += je;
+        if (Pn >> 63) {
+            Pn >>= 1;
+            ++be;
+        }
+        if (be >= 2047) return __longlong_as_double(0x7FF0000000000000ll);  // overflow: +inf
+    }
     if (Pn < ((uint64_t)1 << 62)) {
         Pn <<= 1;
-        --eb;
+        --be;
     }
     uint64_t bits;
-    if (eb >= 1) {
-        bits = ((uint64_t)eb << 52) + (((Pn + (1ull << 9)) >> 10) - (1ull << 52));
+    if (be >= 1) {
+        bits = ((uint64_t)be << 52) + (((Pn + (1ull << 9)) >> 10) - (1ull << 52));
     } else {
-        const int sh = 11 - eb;
+        const int sh = 11 - be;
         bits = sh < 64 ? (Pn + (1ull << (sh - 1))) >> sh : 0ull;
     }
     return __longlong_as_double((long long)bits);
 }
 
+__device__ __forceinline__ double fx_exp_bits(uint64_t u) { return fx_exp_bits_t<false>(u, 0, 0); }
+
 __device__ __forceinline__ double fx_exp(double y) { return fx_exp_bits((uint64_t)__double_as_longlong(y)); }
+
+// exp(-v) (jm / 2^63) 2^je (jm in [2^63, 2^64)), rounded once
+__device__ __forceinline__ double fx_exp_neg_scaled(double v, uint64_t jm, int je)
+{
+    return fx_exp_bits_t<true>((uint64_t)__double_as_longlong(v) ^ 0x8000000000000000ull, jm, je);
+}
 
 // exp(-v), the sign flipped on the bits (no FP64 negation)
 __device__ __forceinline__ double fx_exp_neg(double v)

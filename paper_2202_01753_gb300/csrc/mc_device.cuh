@@ -368,7 +368,9 @@ template <typename R> struct Family<MCUBES_F_COSMO6, R> {
     // two constants, added by the first FMA), each axis's quadratic taken
     // as L (h L + lin) by two FMAs, and c10 is part of the Jacobian's
     // constant: five FP64 instructions per sample fewer, on the pipe that
-    // bounds these kernels.  Single precision keeps the factored form (its
+    // bounds these kernels; the Jacobian itself (an integer product) is
+    // multiplied into the exponential's fixed-point result (end_scaled), one
+    // FP64 multiply fewer.  Single precision keeps the factored form (its
     // rounding would not survive the expansion's cancellation).
     static constexpr bool kWide = sizeof(R) == 8;
     // a logarithm per axis: the FP64 sampling loop runs its axes as a loop
@@ -398,6 +400,12 @@ template <typename R> struct Family<MCUBES_F_COSMO6, R> {
         const R z = s.x12 - RealOps<R>::par(f, 8);
         if constexpr (kWide) return RealOps<R>::expm_(s.e + z * z * f.c[9]);  // c10: in the Jacobian
         else return RealOps<R>::par(f, 10) * RealOps<R>::expm_(s.e + z * z * RealOps<R>::par(f, 9));
+    }
+    // f J in double precision, J = (jm / 2^63) 2^je the integer Jacobian
+    __device__ static double end_scaled(const S& s, const FamParams& f, uint64_t jm, int je)
+    {
+        const double z = s.x12 - f.c[8];
+        return fx::fx_exp_neg_scaled(s.e + z * z * f.c[9], jm, je);
     }
 };
 

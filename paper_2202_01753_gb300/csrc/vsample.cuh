@@ -59,6 +59,53 @@ __device__ __forceinline__ void hist_add_sample(uint32_t hist_s, const uint32_t 
     }
 }
 
+// The same for a sample of DC axes, every one with a histogram (hist_d =
+// DC), in double precision: lane pair t (lanes 2t, 2t+1) starts at index word
+// (t mod NW), NW = ceil(DC/2), and takes the words in turn from there, the
+// odd lane of the pair with the two halves swapped as above.  Each of the NW
+// steps then adds to 2 NW different axes' histograms, about 32 / (2 NW)
+// lanes each, instead of two axes with 16 lanes each: fewer lanes of a warp
+// collide on one bin, and each collision repeats the compare-and-swap for
+// the whole warp on the FP64 pipe.  The words are picked with selects
+// (static register indices).
+template <int NW, int NB4>
+__device__ __forceinline__ void hist_add_sample_rotated(uint32_t hist_s, const uint32_t (&idx)[2 * NB4],
+                                                        uint32_t hist_d, double F2)
+{
+    static_assert(NW >= 2 && NW <= 2 * NB4, "rotation over the words in use");
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t odd = lane & 1u;
+    const uint32_t rot = (lane >> 1) % (uint32_t)NW;
+#pragma unroll
+    for (int t = 0; t < NW; ++t) {
+        uint32_t w = idx[t], k = (uint32_t)t;
+#pragma unroll
+        for (int q = 1; q < NW; ++q) {
+            if (rot == (uint32_t)q) {
+                w = idx[(t + q) % NW];
+                k = (uint32_t)((t + q) % NW);
+            }
+        }
+        w = __funnelshift_l(w, w, odd << 4);  // halves swapped on odd lanes
+        if (((2u * k) ^ odd) < hist_d) hist_add(hist_s, w & 0xFFFFu, F2);
+        if (((2u * k + 1u) ^ odd) < hist_d) hist_add(hist_s, w >> 16, F2);
+    }
+}
+
+// The histogram adds of one sample: rotated where the axis count is a
+// compile-time DC >= 3 with a histogram on every axis and double entries.
+template <int DC, int NB4, class HT>
+__device__ __forceinline__ void hist_add_one(uint32_t hist_s, const uint32_t (&idx)[2 * NB4], uint32_t hist_d, HT F2)
+{
+    if constexpr (DC >= 3 && sizeof(HT) == 8) {
+        if (hist_d == (uint32_t)DC) {
+            hist_add_sample_rotated<(DC + 1) / 2, NB4>(hist_s, idx, hist_d, F2);
+            return;
+        }
+    }
+    hist_add_sample<NB4>(hist_s, idx, hist_d, F2);
+}
+
 template <bool MIXED> struct Prec;
 #ifndef MC_MIXED_CUBE_F64
 #define MC_MIXED_CUBE_F64 0
@@ -189,8 +236,8 @@ sample_point_rolled(const A& a, const typename Prec<MIXED>::Cell* cells, uint32_
         for (int k = 0; k < NW - 1; ++k) idx[k] = __funnelshift_r(idx[k], idx[k + 1], 16);
         idx[NW - 1] >>= 16;
     }
-    if constexpr (!MIXED) jac = int_prod_value(jp);
-    return Fam::end(fs, D, a.fam) * jac;
+    if constexpr (!MIXED) return Fam::end_scaled(fs, a.fam, jp.m, jp.e);  // f J, rounded once
+    else return Fam::end(fs, D, a.fam) * jac;
 }
 
 // One sample: random words -> exact bin position -> map -> integrand.
@@ -341,7 +388,7 @@ __device__ __forceinline__ void sample_cubes(const A& a, const typename Prec<MIX
                 }
                 ++n;
                 if constexpr (ADJ) {
-                    hist_add_sample<NB4>(hist_s, idx, hist_d, (HT)(F * F));
+                    hist_add_one<DC, NB4>(hist_s, idx, hist_d, (HT)(F * F));
                 }
             }
         }
@@ -451,7 +498,7 @@ __device__ __forceinline__ void sample_cube_slice(const A& a, const typename Pre
         }
         ++n;
         if constexpr (ADJ) {
-            hist_add_sample<NB4>(hist_s, idx, hist_d, (HT)(F * F));
+            hist_add_one<DC, NB4>(hist_s, idx, hist_d, (HT)(F * F));
         }
     }
     // re-base on thread 0's shift (every thread has a sample: q >= blockDim;

@@ -9,11 +9,15 @@ floating-point arithmetic", ACM TOMS 15(2), 1989:
 * log: c_j = 1 + j/256 for j = 0..255 (the left end of each mantissa
   interval, so that the reduced argument is never negative); 1/c_j as an
   unsigned Q63 integer and ln(c_j) as an unsigned Q64 fraction; ln 2 as a
-  Q64 integer.
+  Q64 integer.  A second reduction step (Tang's method applied once more to
+  the reduced argument r < 2^-8): d_k = 1 + k/65536 for k = 0..255, 1/d_k as
+  Q63 and ln(d_k) as Q64.
 * exp: 2^(j/256) for j = 0..255 as unsigned Q62 integers; ln 2 / 256 as a
   128-bit Q115 integer for the fixed-point argument reduction and as a Q62
   integer for the step that makes the reduced argument non-negative; 256/ln 2
-  as a Q53 integer for the integer choice of n.
+  as a Q53 integer for the integer choice of n.  A second step splits the
+  reduced argument r < ln2/256 at multiples of 2^-16: exp(k/65536) for
+  k = 0..255 as Q62.
 * single-precision cosine: pi/2 as the sum of three floats (each the float
   nearest to what remains of pi/2) for a Cody-Waite reduction (Cody and
   Waite, "Software Manual for the Elementary Functions", 1980), and 2/pi.
@@ -52,6 +56,24 @@ def tables():
         exp2.append(int(mpmath.nint(2 ** 62 * mpmath.power(2, mpmath.mpf(j) / 256))))
     ln2 = mpmath.log(2)
     return inv_c, log_q64, exp2, ln2
+
+
+def second_step_tables():
+    mpmath.mp.dps = 60
+    inv_d, log_d, exp_k = [], [], []
+    for k in range(256):
+        dk = 1 + mpmath.mpf(k) / 65536
+        inv_d.append(int(mpmath.nint(2 ** 63 / dk)))
+        log_d.append(int(mpmath.nint(2 ** 64 * mpmath.log(dk))))
+        exp_k.append(int(mpmath.nint(2 ** 62 * mpmath.exp(mpmath.mpf(k) / 65536))))
+    return inv_d, log_d, exp_k
+
+
+def _table(lines, comment, name, vals):
+    lines += [comment, f"__device__ const uint64_t {name}[256] = {{"]
+    for i in range(0, 256, 4):
+        lines.append("    " + ", ".join(f"0x{v:016x}ull" for v in vals[i:i + 4]) + ",")
+    lines += ["};", ""]
 
 
 def render():
@@ -94,7 +116,12 @@ def render():
     lines += ["};", "", "// 2^(j/256) as Q62", "__device__ const uint64_t kExp2[256] = {"]
     for i in range(0, 256, 4):
         lines.append("    " + ", ".join(f"0x{v:016x}ull" for v in exp2[i:i + 4]) + ",")
-    lines += ["};", "", "}  // namespace fx", "}  // namespace mc", ""]
+    lines += ["};", ""]
+    inv_d, log_d, exp_k = second_step_tables()
+    _table(lines, "// 1 / d_k, d_k = 1 + k/65536, as Q63 (k = 0: exactly 2^63)", "kLogInvD", inv_d)
+    _table(lines, "// ln d_k as Q64", "kLogDQ64", log_d)
+    _table(lines, "// exp(k/65536) as Q62", "kExpK16", exp_k)
+    lines += ["}  // namespace fx", "}  // namespace mc", ""]
     return "\n".join(lines)
 
 

@@ -1,8 +1,9 @@
 """The kernels' fixed-point log and exp (csrc/fx_math.cuh), compiled for the
 host with stand-ins for the device intrinsics (tests/fxmath_host.cpp), against
 40-digit references: log within 1 ulp plus 2^-58 absolute, exp within 2^-52
-relative, and the special values.  The GPU tests check the same functions on
-the device against these bounds and against CUDA's log and exp."""
+relative (also when scaled by a 64-bit fixed-point factor), and the special
+values.  The GPU tests check the same functions on the device against these
+bounds and against CUDA's log and exp."""
 import math
 import os
 import shutil
@@ -25,9 +26,15 @@ def fxhost(tmp_path_factory):
     subprocess.run([cxx, "-O2", "-std=c++17", "-I", CSRC, "-o", exe, os.path.join(HERE, "fxmath_host.cpp")],
                    check=True)
 
-    def run(xs):
-        out = subprocess.run([exe], input="\n".join(float(x).hex() for x in xs), capture_output=True,
+    def run(xs, scale=None):
+        if scale is None:
+            lines = [float(x).hex() for x in xs]
+        else:
+            lines = [f"{float(x).hex()} {int(m)} {int(e)}" for x, (m, e) in zip(xs, scale)]
+        out = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True,
                              text=True, check=True).stdout.split()
+        if scale is not None:
+            return np.array([float.fromhex(v) for v in out])
         return (np.array([float.fromhex(v) for v in out[0::2]]),
                 np.array([float.fromhex(v) for v in out[1::2]]))
     return run
@@ -49,7 +56,10 @@ def test_log_accuracy_host(fxhost):
     edges = [_dbl((1023 << 52) | (j << 44) | d) for j in range(256) for d in (0, 1, (1 << 44) - 1)]
     near1 = [_dbl(_bits(1.0) - k) for k in range(1, 40)] + [_dbl(_bits(1.0) + k) for k in range(0, 40)]
     ends = [_dbl(((1023 + e) << 52) | (255 << 44) | ((1 << 44) - 1)) for e in range(-1022, 1024, 7)]
-    xs = np.concatenate([xs, edges, near1, ends, [2.2250738585072014e-308, 1.7976931348623157e308]])
+    # the second step's table points (1 + j/256)(1 + k/65536) and their neighbours
+    second = [(1 + j / 256) * (1 + k / 65536) for j in range(0, 256, 9) for k in range(0, 256, 11)]
+    second = np.concatenate([second, np.nextafter(second, 0), np.nextafter(second, 3)])
+    xs = np.concatenate([xs, edges, near1, ends, second, [2.2250738585072014e-308, 1.7976931348623157e308]])
     got, _ = fxhost(xs)
     mpmath.mp.dps = 40
     for x, g in zip(xs, got):
@@ -94,6 +104,34 @@ def test_exp_subnormal_results_host(fxhost):
         tol = max(ref * mpmath.mpf(2) ** -52, tiny)
         assert abs(mpmath.mpf(float(g)) - ref) <= tol, (y, g, float(ref))
     assert np.all(got >= 0.0)
+
+
+def test_exp_scaled_host(fxhost):
+    """exp(-v) (jm / 2^63) 2^je, rounded once (the FP64 kernels' integrand
+    exponential times their Jacobian): within 2^-52 relative wherever the
+    result is normal, +inf on overflow, and +0 wherever exp(-v) alone rounds
+    to +0 (v > 745.2), as the product of the two doubles would be."""
+    rng = np.random.default_rng(24)
+    vs = np.concatenate([rng.uniform(-705, 708, 4000), rng.uniform(-3, 3, 2000), rng.uniform(708, 745, 1000),
+                         rng.uniform(-1e-6, 1e-6, 200), [0.0, 1.0, -1.0]])
+    jm = rng.integers(2 ** 63, 2 ** 64 - 1, len(vs), dtype=np.uint64, endpoint=True)
+    jm[:8] = [2 ** 63, 2 ** 64 - 1] * 4
+    je = rng.integers(-80, 81, len(vs))
+    got = fxhost(vs, scale=list(zip(jm, je)))
+    mpmath.mp.dps = 50
+    checked = 0
+    for v, m, e, g in zip(vs, jm, je, got):
+        ref = mpmath.exp(-mpmath.mpf(float(v))) * int(m) * mpmath.mpf(2) ** (int(e) - 63)
+        if ref > mpmath.mpf(2) ** 1024:
+            assert g == math.inf, (v, m, e, g)
+        elif ref >= mpmath.mpf(2) ** -1022 and v < 708.39:
+            assert abs(mpmath.mpf(float(g)) - ref) / ref <= 2.0 ** -52, (v, m, e, g, float(ref))
+            checked += 1
+        else:  # exp(-v) subnormal: the product is exact to the last place of the result
+            assert abs(mpmath.mpf(float(g)) - ref) <= max(ref * mpmath.mpf(2) ** -52, mpmath.mpf(2) ** -1074)
+    assert checked > 5000
+    z = fxhost([745.3, 800.0, math.inf], scale=[(2 ** 64 - 1, 80)] * 3)
+    assert np.all(z == 0.0) and not np.any(np.signbit(z))
 
 
 def test_tables_header_is_generated():

@@ -52,12 +52,13 @@ from paper_2202_01753_gb300 import closed_forms as CF  # noqa: E402
 # "fp32_flops": 2 FFMA + FADD + FMUL per sample (the FP32-pipe fraction shown
 # beside the issue fraction).
 ROOFLINE_UNITS = {
-    ("cosmo6", "fp64"): {"kind": "fp64", "per_sample": 29.86, "issue_per_sample": 2154.8, "traffic": 406.3e3,
-                         "pipe_busy": 0.757,
+    ("cosmo6", "fp64"): {"kind": "fp64", "per_sample": 29.86, "issue_per_sample": 2088.8, "traffic": 316.7e3,
+                         "pipe_busy": 0.770,
                          "source": "profiles/vsample_cosmo6_fp64.md"},
-    ("gauss3", "fp64"): {"kind": "fp64", "per_sample": 26.92, "traffic": None, "pipe_busy": 0.784,
+    ("gauss3", "fp64"): {"kind": "fp64", "per_sample": 26.92, "traffic": 101.9e3, "pipe_busy": 0.785,
                          "source": "profiles/vsample_gauss3_fp64.md"},
-    ("table6", "fp64"): {"kind": "fp64", "per_sample": 43.74, "traffic": None, "pipe_busy": 0.730,
+    ("table6", "fp64"): {"kind": "fp64", "per_sample": 43.74, "dram_bytes_per_sample": 409.3, "traffic": 38.5098e9,
+                         "pipe_busy": 0.730,
                          "source": "profiles/vsample_table6_fp64.md"},
     ("corner8", "mixed"): {"kind": "issue", "per_sample": 543.0, "traffic": 466.9e3, "fp32_flops": 99.23,
                            "source": "profiles/vsample_corner8_mixed.md"},

@@ -37,23 +37,26 @@
 namespace mc {
 namespace fx {
 
-// Rounds (-1)^neg (hi 2^64 + lo) / 2^64, a nonzero magnitude below 2^74, to
-// the nearest double (ties away from zero) with 64-bit integer operations.
+// Rounds (-1)^neg (hi 2^64 + lo) / 2^64, a nonzero magnitude below 2^10
+// (hi < 2^10), to a double (ties away from zero) with 64-bit integer
+// operations: a value >= 1 from its Q54 window hi 2^54 + lo 2^-10 (the
+// dropped bits are below a quarter of its last place), a value < 1 from lo.
 __device__ __forceinline__ double q64_to_double(uint64_t hi, uint64_t lo, bool neg)
 {
-    const int p = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);  // leading bit
+    const bool big = hi != 0;
+    const uint64_t t = big ? ((hi << 54) | (lo >> 10)) : lo;
+    const int p = 63 - __clzll((long long)t);  // leading bit of t
+    int e = p - (big ? 54 : 64) + 1023;
     uint64_t m;
-    int e = p - 64 + 1023;
     if (p > 52) {
-        const int sh = p - 52;  // 1..21
-        m = (hi << (64 - sh)) | (lo >> sh);
-        m += (lo >> (sh - 1)) & 1ull;
+        const int sh = p - 52;
+        m = (t >> sh) + ((t >> (sh - 1)) & 1ull);
         if (m >> 53) {  // rounding carried into a new leading bit
             m >>= 1;
             ++e;
         }
     } else {
-        m = lo << (52 - p);
+        m = t << (52 - p);
     }
     const uint64_t bits = ((uint64_t)neg << 63) | (((uint64_t)e << 52) + m - (1ull << 52));
     return __longlong_as_double((long long)bits);
@@ -76,7 +79,7 @@ __host__ __device__ constexpr uint32_t q32_inv(uint32_t k) { return (uint32_t)((
 __device__ __forceinline__ double fx_log(double x)
 {
     const uint64_t u = (uint64_t)__double_as_longlong(x);
-    if (u - 0x0010000000000000ull >= 0x7FE0000000000000ull) return log_slow(x);  // not a positive normal number
+    if ((uint32_t)(u >> 32) - 0x00100000u >= 0x7FE00000u) return log_slow(x);  // not a positive normal number
     const int e = (int)(u >> 52) - 1023;
     const uint64_t f = u & 0xFFFFFFFFFFFFFull;
     const int j = (int)(f >> 44);

@@ -60,9 +60,9 @@ ROOFLINE_UNITS = {
     ("table6", "fp64"): {"kind": "fp64", "per_sample": 43.74, "dram_bytes_per_sample": 409.3, "traffic": 38.5098e9,
                          "pipe_busy": 0.730,
                          "source": "profiles/vsample_table6_fp64.md"},
-    ("corner8", "mixed"): {"kind": "issue", "per_sample": 543.0, "traffic": 466.9e3, "fp32_flops": 99.23,
+    ("corner8", "mixed"): {"kind": "issue", "per_sample": 533.1, "traffic": 598.8e3, "fp32_flops": 99.08,
                            "source": "profiles/vsample_corner8_mixed.md"},
-    ("osc10", "mixed"): {"kind": "issue", "per_sample": 665.7, "traffic": 299.0e3, "fp32_flops": 135.1,
+    ("osc10", "mixed"): {"kind": "issue", "per_sample": 654.3, "traffic": 301.1e3, "fp32_flops": 134.87,
                          "source": "profiles/vsample_osc10_mixed.md"},
 }
 DFMA_PER_CLK_PER_SM = 2.0

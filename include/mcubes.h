@@ -477,8 +477,11 @@ mcubes_status mcubes_sample_range_noalloc(int device, int integrand_id, const do
  * (which = 0) or exponential (1) -- table-driven with fixed-point series,
  * used by the FP64 integrands -- or CUDA's log (2) or exp (3), or the
  * library's single-precision cosine of the mixed-precision kernels (4) or
- * CUDA's cosf (5) (both on the value rounded to single precision), on
- * cuda_stream (NULL = legacy default stream); returns without waiting.
+ * CUDA's cosf (5) (both on the value rounded to single precision), or the
+ * library's exp(-x) multiplied, before its one rounding, by the fixed factor
+ * (0xD3C21BCECCEDA100 / 2^63) 2^40 (6; the FP64 kernels fold their integer
+ * Jacobian into the exponential this way), on cuda_stream (NULL = legacy
+ * default stream); returns without waiting.
  * The paper has no counterpart; this exists to test accuracy.
  * Errors: EINVAL, ECUDA. */
 mcubes_status mcubes_selftest_fxmath(int which, long long n, const double* d_in, double* d_out,

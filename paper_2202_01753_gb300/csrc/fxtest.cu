@@ -8,6 +8,12 @@
 
 namespace {
 
+// the fixed factor of selftest 6: (kScaleM / 2^63) 2^kScaleE, a significand
+// above 1.5 so that products with most exponentials reach [2, 4) and take the
+// renormalising step
+constexpr uint64_t kScaleM = 0xD3C21BCECCEDA100ull;
+constexpr int kScaleE = 40;
+
 __global__ void fxmath_kernel(int which, long long n, const double* in, double* out)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -19,7 +25,8 @@ __global__ void fxmath_kernel(int which, long long n, const double* in, double* 
         case 2: y = log(x); break;
         case 3: y = exp(x); break;
         case 4: y = (double)mc::fx::fx_cosf((float)x); break;
-        default: y = (double)cosf((float)x); break;
+        case 5: y = (double)cosf((float)x); break;
+        default: y = mc::fx::fx_exp_neg_scaled(x, kScaleM, kScaleE); break;
         }
         out[i] = y;
     }
@@ -58,7 +65,7 @@ extern "C" mcubes_status mcubes_selftest_rebin(int nb, double alpha, double* d_C
 extern "C" mcubes_status mcubes_selftest_fxmath(int which, long long n, const double* d_in, double* d_out,
                                                void* cuda_stream)
 {
-    if (which < 0 || which > 5 || n < 0 || (n > 0 && (!d_in || !d_out))) return MCUBES_EINVAL;
+    if (which < 0 || which > 6 || n < 0 || (n > 0 && (!d_in || !d_out))) return MCUBES_EINVAL;
     if (n == 0) return MCUBES_OK;
     fxmath_kernel<<<(int)std::min<long long>((n + 255) / 256, 65535), 256, 0, (cudaStream_t)cuda_stream>>>(
         which, n, d_in, d_out);

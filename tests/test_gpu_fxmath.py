@@ -105,3 +105,28 @@ def test_cosf_accuracy(torch_cuda):
     huge = np.array([5e6, -3e7, 1e30], dtype=np.float32).astype(np.float64)
     g = _eval(torch_cuda, 4, huge)                    # hardware approximation: a value in [-1, 1]
     assert np.all(np.abs(g) <= 1.0)
+
+
+def test_exp_scaled_accuracy(torch_cuda):
+    """exp(-v) times the fixed factor J = (0xD3C21BCECCEDA100 / 2^63) 2^40,
+    rounded once (the cosmo6 kernel's integrand times its Jacobian): within
+    2^-52 relative where the product is normal (within one unit of the last
+    place, 2^-1074, where it is subnormal), +inf beyond the range, +0 where
+    exp(-v) alone rounds to +0 (as exp(-v) * J would)."""
+    jm, je = 0xD3C21BCECCEDA100, 40
+    rng = np.random.default_rng(5)
+    vs = np.concatenate([rng.uniform(-705, 708, 3000), rng.uniform(-3, 3, 2000), rng.uniform(708, 745, 500),
+                         [0.0, 1.0, -1.0, -680.0, 745.3, 800.0]])
+    got = _eval(torch_cuda, 6, vs)
+    mpmath.mp.dps = 50
+    J = mpmath.mpf(jm) * mpmath.mpf(2) ** (je - 63)
+    for v, g in zip(vs, got):
+        ref = mpmath.exp(-mpmath.mpf(float(v))) * J
+        if v > 745.2:
+            assert g == 0.0
+        elif ref > mpmath.mpf(2) ** 1024:
+            assert g == math.inf, (v, g)
+        else:
+            tol = max(ref * mpmath.mpf(2) ** -52, mpmath.mpf(2) ** -1074)
+            assert abs(mpmath.mpf(float(g)) - ref) <= tol, (v, g, float(ref))
+

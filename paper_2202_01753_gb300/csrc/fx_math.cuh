@@ -72,6 +72,17 @@ static __device__ __noinline__ double exp_slow(double y) { return exp(y); }
 // Constant of the series: round(2^32 / k).
 __host__ __device__ constexpr uint32_t q32_inv(uint32_t k) { return (uint32_t)((((uint64_t)1 << 32) + k / 2) / k); }
 
+// A logarithm table entry, one 16-byte load through the read-only cache.
+__device__ __forceinline__ LogPair ld_pair(const LogPair* p)
+{
+#ifdef __CUDA_ARCH__
+    const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(p));
+    return LogPair{v.x, v.y};
+#else
+    return *p;
+#endif
+}
+
 // ln x = e ln 2 + ln c_j + ln d_k + ln(1 + r2) for x = 2^e m, c_j = 1 + j/256
 // the table point at or below m, r = (m - c_j)/c_j in [0, 2^-8), d_k =
 // 1 + k/65536 the second table point at or below 1 + r and r2 = (r - k/65536)/d_k
@@ -84,11 +95,13 @@ __device__ __forceinline__ double fx_log(double x)
     const uint64_t f = u & 0xFFFFFFFFFFFFFull;
     const int j = (int)(f >> 44);
     // m - c_j is the mantissa's low 44 bits (Q52); r = (m - c_j)/c_j in Q64 (< 2^56)
-    const uint64_t r = __umul64hi((f & 0xFFFFFFFFFFFull) << 13, __ldg(&kLogInvC[j]));
+    const LogPair cj = ld_pair(&kLogC[j]);
+    const uint64_t r = __umul64hi((f & 0xFFFFFFFFFFFull) << 13, cj.inv);
     // second step: k = the top 8 bits of r (r < 2^-8), r - k/65536 its low 48 bits
     // (Q64); r2 = (r - k/65536)/d_k in Q64 (< 2^48)
     const int k = (int)(r >> 48);
-    const uint64_t R = __umul64hi((r & 0xFFFFFFFFFFFFull) << 16, __ldg(&kLogInvD[k])) >> 15;
+    const LogPair dk = ld_pair(&kLogD[k]);
+    const uint64_t R = __umul64hi((r & 0xFFFFFFFFFFFFull) << 16, dk.inv) >> 15;
     // ln(1 + r2) = r2 - r2^2/2 + r2^3/3 (+ r2^4/4 < 2^-66).  r2^2 from the top 32
     // bits of r2 (H = r2 in Q48; the dropped low bits move it by < 2^-62) and
     // r2^3 < 2^-48 from r2^2 and H, both with 32 x 32-bit products.
@@ -96,7 +109,7 @@ __device__ __forceinline__ double fx_log(double x)
     const uint64_t sq = ((uint64_t)H * H) >> 32;                           // r2^2, Q64 (< 2^32)
     const uint32_t cube = (uint32_t)(((uint64_t)(uint32_t)sq * H) >> 48);  // r2^3, Q64 (< 2^16)
     const uint64_t l2 = R - (sq >> 1) + __umulhi(cube, q32_inv(3));        // ln(1 + r2), Q64
-    const uint64_t U = __ldg(&kLogCQ64[j]) + __ldg(&kLogDQ64[k]) + l2;     // ln m, Q64 (< ln 2)
+    const uint64_t U = cj.ln + dk.ln + l2;                                 // ln m, Q64 (< ln 2)
     // e ln 2 + ln m as sign and 128-bit magnitude in Q64; |e| < 2^11, so
     // |e| ln 2 is two 32 x 32-bit products (ln 2 = L1 2^32 + L0)
     const uint32_t ae = (uint32_t)(e < 0 ? -e : e);
@@ -132,7 +145,8 @@ __device__ __forceinline__ double fx_exp_bits_t(uint64_t u, uint64_t jm, int je)
 {
     const double y = __longlong_as_double((long long)u);
     const uint64_t ay = u & 0x7FFFFFFFFFFFFFFFull;
-    if (ay >= 0x4086200000000000ull) {  // |y| >= 708, infinite or NaN
+    const uint32_t ayh = (uint32_t)(ay >> 32);  // the thresholds below have zero low words
+    if (ayh >= 0x40862000u) {  // |y| >= 708, infinite or NaN
         // y < -745.2 (down to -inf): exp(y) < 2^-1075 rounds to +0.  Integrands
         // with narrow peaks land here often, so it takes no FP64 work.  Down
         // from -708 the results are subnormal; they are assembled below with
@@ -145,7 +159,7 @@ __device__ __forceinline__ double fx_exp_bits_t(uint64_t u, uint64_t jm, int je)
         }
         if (ay > 0x408749999999999Aull) return 0.0;
     }
-    if (ay < 0x3C30000000000000ull) {  // |y| < 2^-60: exp(y) rounds to 1
+    if (ayh < 0x3C300000u) {  // |y| < 2^-60: exp(y) rounds to 1
         if constexpr (SCALED) return ldexp((double)jm, je - 63);
         else return 1.0;
     }

@@ -212,7 +212,9 @@ __device__ __forceinline__ BinPos bin_pos(uint32_t w, uint32_t nb_c, uint32_t nb
 
 // g phi = r + a_lo 2^-33 as a double, built from the integer numerator
 // r 2^33 + a_lo with integer operations only (exact below 2^53, rounded to
-// nearest above): no FP64 conversion or multiply in the sampling loop.
+// nearest above): no FP64 conversion or multiply in the sampling loop.  The
+// numerator is never 0: its low 33 bits are those of A = nb (2w + 1), an odd
+// multiple of nb < 2^33.
 __device__ __forceinline__ double bin_gphi_f64(const BinPos& b)
 {
     const uint64_t num = ((uint64_t)b.r << 33) | ((uint64_t)b.ahi << 32) | (uint64_t)b.alo;  // < 2^63
@@ -227,7 +229,7 @@ __device__ __forceinline__ double bin_gphi_f64(const BinPos& b)
     // value 2^(63 - lz - 33) (m / 2^52): biased exponent 1053 - lz, stored as
     // (exponent - 1) << 52 plus m, whose leading one adds the missing 1
     const uint64_t bits = ((uint64_t)(1052 - lz) << 52) + m;
-    return num ? __longlong_as_double((long long)bits) : 0.0;
+    return __longlong_as_double((long long)bits);
 }
 
 // the same in single precision: (r + a_lo 2^-33) * scale, scale = 1/g for phi

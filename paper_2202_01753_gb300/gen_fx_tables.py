@@ -8,10 +8,11 @@ floating-point arithmetic", ACM TOMS 15(2), 1989:
 
 * log: c_j = 1 + j/256 for j = 0..255 (the left end of each mantissa
   interval, so that the reduced argument is never negative); 1/c_j as an
-  unsigned Q63 integer and ln(c_j) as an unsigned Q64 fraction; ln 2 as a
-  Q64 integer.  A second reduction step (Tang's method applied once more to
-  the reduced argument r < 2^-8): d_k = 1 + k/65536 for k = 0..255, 1/d_k as
-  Q63 and ln(d_k) as Q64.
+  unsigned Q63 integer and ln(c_j) as an unsigned Q64 fraction, stored side
+  by side (one 16-byte load per lookup); ln 2 as a Q64 integer.  A second
+  reduction step (Tang's method applied once more to the reduced argument
+  r < 2^-8): d_k = 1 + k/65536 for k = 0..255, 1/d_k as Q63 and ln(d_k) as
+  Q64, side by side as well.
 * exp: 2^(j/256) for j = 0..255 as unsigned Q62 integers; ln 2 / 256 as a
   128-bit Q115 integer for the fixed-point argument reduction and as a Q62
   integer for the step that makes the reduced argument non-negative; 256/ln 2
@@ -76,6 +77,13 @@ def _table(lines, comment, name, vals):
     lines += ["};", ""]
 
 
+def _pair_table(lines, comment, name, inv, ln):
+    lines += [comment, f"__device__ const LogPair {name}[256] = {{"]
+    for i in range(0, 256, 2):
+        lines.append("    " + " ".join(f"{{0x{a:016x}ull, 0x{b:016x}ull}}," for a, b in zip(inv[i:i + 2], ln[i:i + 2])))
+    lines += ["};", ""]
+
+
 def render():
     inv_c, log_q64, exp2, ln2 = tables()
     mpmath.mp.dps = 60
@@ -104,22 +112,20 @@ def render():
         f"constexpr float kHalfPiF3 = {_f32(hp - _f32(hp) - _f32(hp - _f32(hp)))!r}f;",
         f"constexpr float kTwoOverPiF = {_f32(2 / mpmath.pi)!r}f;",
         "",
-        "// 1 / c_j, c_j = 1 + j/256, as Q63 (j = 0: exactly 2^63)",
-        "__device__ const uint64_t kLogInvC[256] = {",
+        "// A logarithm table entry: 1/c as Q63 and ln c as Q64, loaded together",
+        "struct alignas(16) LogPair {",
+        "    uint64_t inv, ln;",
+        "};",
+        "",
     ]
-    for i in range(0, 256, 4):
-        lines.append("    " + ", ".join(f"0x{v:016x}ull" for v in inv_c[i:i + 4]) + ",")
-    lines += ["};", "", "// ln c_j as Q64 (a binary fraction; 0 <= ln c_j < ln 2)",
-              "__device__ const uint64_t kLogCQ64[256] = {"]
-    for i in range(0, 256, 4):
-        lines.append("    " + ", ".join(f"0x{v:016x}ull" for v in log_q64[i:i + 4]) + ",")
-    lines += ["};", "", "// 2^(j/256) as Q62", "__device__ const uint64_t kExp2[256] = {"]
+    _pair_table(lines, "// c_j = 1 + j/256: 1/c_j as Q63 (j = 0: exactly 2^63), ln c_j as Q64 (0 <= ln c_j < ln 2)",
+                "kLogC", inv_c, log_q64)
+    lines += ["// 2^(j/256) as Q62", "__device__ const uint64_t kExp2[256] = {"]
     for i in range(0, 256, 4):
         lines.append("    " + ", ".join(f"0x{v:016x}ull" for v in exp2[i:i + 4]) + ",")
     lines += ["};", ""]
     inv_d, log_d, exp_k = second_step_tables()
-    _table(lines, "// 1 / d_k, d_k = 1 + k/65536, as Q63 (k = 0: exactly 2^63)", "kLogInvD", inv_d)
-    _table(lines, "// ln d_k as Q64", "kLogDQ64", log_d)
+    _pair_table(lines, "// d_k = 1 + k/65536: 1/d_k as Q63 (k = 0: exactly 2^63), ln d_k as Q64", "kLogD", inv_d, log_d)
     _table(lines, "// exp(k/65536) as Q62", "kExpK16", exp_k)
     lines += ["}  // namespace fx", "}  // namespace mc", ""]
     return "\n".join(lines)

@@ -156,7 +156,9 @@ def test_batch_early_convergence_per_integral(gpu_ctx_factory):
         s = _solo(gpu_ctx_factory, w, "fp64")
         assert b["iterations"] == s["iterations"]
         assert b["converged"] == s["converged"]
-        assert b["estimate"] == pytest.approx(s["estimate"], rel=1e-10)
+        # the FP64 batch-against-solo bound of test_batch_matches_solo
+        scale = max(abs(s["estimate"]), s["sigma"], 1e-9)
+        assert abs(b["estimate"] - s["estimate"]) <= 1e-13 * scale, (w.name, b["estimate"], s["estimate"])
         its.add(b["iterations"])
         if b["converged"]:
             assert b["sigma"] <= w.rel_tol * abs(b["estimate"])

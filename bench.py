@@ -55,9 +55,10 @@ ROOFLINE_UNITS = {
     ("cosmo6", "fp64"): {"kind": "fp64", "per_sample": 29.86, "issue_per_sample": 2032.5, "traffic": 277.2e3,
                          "pipe_busy": 0.781,
                          "source": "profiles/vsample_cosmo6_fp64.md"},
-    ("gauss3", "fp64"): {"kind": "fp64", "per_sample": 26.92, "traffic": None, "pipe_busy": 0.783,
+    ("gauss3", "fp64"): {"kind": "fp64", "per_sample": 26.92, "traffic": 101.4e3, "pipe_busy": 0.783,
                          "source": "profiles/vsample_gauss3_fp64.md"},
-    ("table6", "fp64"): {"kind": "fp64", "per_sample": 43.74, "traffic": None, "pipe_busy": 0.734,
+    ("table6", "fp64"): {"kind": "fp64", "per_sample": 43.74, "dram_bytes_per_sample": 409.2, "traffic": 38.5028e9,
+                         "pipe_busy": 0.734,
                          "source": "profiles/vsample_table6_fp64.md"},
     ("corner8", "mixed"): {"kind": "issue", "per_sample": 533.1, "traffic": 598.8e3, "fp32_flops": 99.08,
                            "source": "profiles/vsample_corner8_mixed.md"},

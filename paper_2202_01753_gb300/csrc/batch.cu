@@ -586,10 +586,15 @@ cudaError_t BatchEngine::capture(ClassMask mask)
     return cudaSuccess;
 }
 
-// Picks the resident sampling blocks per SM (capped by each class's
-// occupancy) and the samples-per-thread cap that sets lanes per cube, by
-// timing sampling-only launches of a subset of this batch's first
-// iteration; the choice is kept for the life of the engine.
+// Picks the samples-per-thread cap that sets lanes per cube, by timing
+// sampling-only launches of a subset of this batch's first iteration; the
+// choice is kept for the life of the engine.  Every class kernel launches
+// its full occupancy of blocks per SM (opts.blocks_per_sm, when set, caps
+// it), so the cubes per block follow from a class's work over that grid:
+// timed on the small subset, fewer blocks per SM looked faster (1 of 3),
+// but on the work that follows -- the 4096-integral batch with its retries,
+// the serving mix -- full occupancy measured 1.4 and 1.25 times the
+// integrals per second at tolerance.
 cudaError_t BatchEngine::autotune(const std::vector<int>& live, const ClassMask& mask)
 {
     if (tuned_) return cudaSuccess;
@@ -601,14 +606,13 @@ cudaError_t BatchEngine::autotune(const std::vector<int>& live, const ClassMask&
     // kTuneMinLive integrals are live (a server's first steps), run with the
     // full occupancy and the middle lanes cap, and tune later.
     constexpr size_t kTuneMinLive = 32;
+    constexpr int kEachClassOccupancy = 1 << 16;  // no cap: class_blocks takes each class's own occupancy
     if (live.size() < kTuneMinLive && opts_.blocks_per_sm <= 0 && opts_.lanes_per_cube <= 0) {
-        tuned_bps_ = occ_hi;
+        tuned_bps_ = kEachClassOccupancy;
         lanes_cap_ = 64;
         return cudaSuccess;
     }
-    std::vector<int> bps_list;
-    if (opts_.blocks_per_sm > 0) bps_list.push_back(std::min(opts_.blocks_per_sm, occ_hi));
-    else for (int b = occ_hi; b >= 1; --b) bps_list.push_back(b);  // full occupancy first: it wins ties
+    std::vector<int> bps_list{opts_.blocks_per_sm > 0 ? std::min(opts_.blocks_per_sm, occ_hi) : kEachClassOccupancy};
     std::vector<int> cap_list =
         opts_.lanes_per_cube > 0 ? std::vector<int>{lanes_cap_} : std::vector<int>{64, 16, 256};
     // a subset of the batch (every k-th integral, class order kept) keeps tuning cheap

@@ -79,7 +79,7 @@ public:
     // (any may be null).  Valid for a finished slot until it is reused.
     cudaError_t read_slot(int slot, double* I, double* V, int cap, int* n, double* grid, double* hist);
 
-    int tuned_blocks_per_sm() const { return tuned_bps_; }
+    int tuned_blocks_per_sm() const { return tuned_bps_; }  // a cap on each class's occupancy
     int lanes_cap() const { return lanes_cap_; }
 
 private:

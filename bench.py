@@ -103,7 +103,7 @@ def parse():
     ap.add_argument("--serve-steady-seconds", type=float, default=8.0,
                     help="length of the stream at a sustainable fraction of the capacity")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
-    ap.add_argument("--serve-iters", type=int, default=4, help="iterations per server step")
+    ap.add_argument("--serve-iters", type=int, default=2, help="iterations per server step")
     ap.add_argument("--batch-n", type=int, default=4096)
     ap.add_argument("--batch-rel-tol", type=float, default=1e-4, help="relative tolerance of every batched integral")
     ap.add_argument("--seq-sample", type=int, default=96, help="integrals timed one by one in plain FP64")

@@ -402,9 +402,16 @@ void BatchEngine::live_slots(std::vector<int>* live, ClassMask* class_mask) cons
     }
 }
 
+// Fewest samples per chunk of a class's work (measured, mixed precision: the
+// 4096-integral batch 1934-1942 integrals/s against 1880-1919 with one chunk
+// per block, the serving mix without retries at 2000 requests/s p50 2.6 ms and
+// p99 3.9 ms against 15.2 and 21.0; 8192: 3.1 and 4.1 ms, 32768: 7.1 and 8.5).
+constexpr double kMinBlockSamples = 2048.0;
+
 // For every class, lays its live integrals' samples end to end and cuts the
-// line into class_blocks(class) equal chunks; cube c of an integral goes to
-// the chunk holding its first sample.  Writes the segment list (class by
+// line into equal chunks, at least kMinBlockSamples samples each and at most
+// class_blocks(class) of them; cube c of an integral goes to the chunk
+// holding its first sample.  Writes the segment list (class by
 // class, then block by block), every class's block table (a fixed region of
 // bmax_+1 entries per class; classes without work get empty tables) and the
 // live integrals' segment offsets.
@@ -425,7 +432,14 @@ void BatchEngine::partition(const std::vector<int>& live, int* nseg_out)
         double total = 0.0;
         while (j1 < live.size() && batch_class(hdesc_[live[j1]].family, (int)hdesc_[live[j1]].d) == cls)
             total += slots_[live[j1++]].work;
-        const int blocks = class_blocks(cls);
+        // chunks of at least kMinBlockSamples samples, at most one per block
+        // of the class's launch (its full occupancy): a step of small
+        // requests is cut into few chunks (each block's fixed work -- staging
+        // a segment's grid, writing its partial histogram -- stays small
+        // beside its samples, and the refinement merges fewer segments), a
+        // large batch fills every block
+        const int blocks_max = class_blocks(cls);
+        const int blocks = (int)std::max(1.0, std::min((double)blocks_max, std::ceil(total / kMinBlockSamples)));
         class_load_[cls] = total * (4.0 + hdesc_[live[j]].d) / blocks;
         uint32_t* blk_seg = table + (size_t)cls * (bmax_ + 1);
         const double chunk = total / blocks;
@@ -460,7 +474,7 @@ void BatchEngine::partition(const std::vector<int>& live, int* nseg_out)
             }
             start += S.work;
         }
-        while (b < blocks) blk_seg[++b] = (uint32_t)nseg;
+        while (b < blocks_max) blk_seg[++b] = (uint32_t)nseg;  // blocks past the chunks: empty
     }
     live_seg[live.size()] = (uint32_t)nseg;
     part_hist_ = hist_off;
@@ -590,11 +604,13 @@ cudaError_t BatchEngine::capture(ClassMask mask)
 // sampling-only launches of a subset of this batch's first iteration; the
 // choice is kept for the life of the engine.  Every class kernel launches
 // its full occupancy of blocks per SM (opts.blocks_per_sm, when set, caps
-// it), so the cubes per block follow from a class's work over that grid:
-// timed on the small subset, fewer blocks per SM looked faster (1 of 3),
-// but on the work that follows -- the 4096-integral batch with its retries,
-// the serving mix -- full occupancy measured 1.4 and 1.25 times the
-// integrals per second at tolerance.
+// it) and the partition decides how many of them get work (a chunk of at
+// least kMinBlockSamples samples each), so the cubes per block follow from
+// a class's work in every step: the tuner used to pick the blocks per SM
+// as well, on its small subset, where one block per SM (of three) looked
+// faster, and kept it for the work that followed -- there full occupancy
+// measured 1.4 times the integrals per second at tolerance on the
+// 4096-integral batch and 1.25 times the serving mix's capacity.
 cudaError_t BatchEngine::autotune(const std::vector<int>& live, const ClassMask& mask)
 {
     if (tuned_) return cudaSuccess;
